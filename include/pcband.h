@@ -1,0 +1,220 @@
+/*
+ * pcband.h -- C ABI of the GB300 parity-blocked band solver.
+ *
+ * The library computes, for a Bloch vector kappa, the discrete elastic pencil
+ *     A_h(kappa) v = omega^2 M_h v,   A_h = B_h C_h B_h^H
+ * of the rotated staggered discretisation (Sec. 3, Eq. discrete_GEP) restricted
+ * to one of the four parity blocks of even grids (Sec. 4, Theorem 4.1,
+ * Cor. 4.2), and drives it with a shift-invert Krylov-Schur eigensolver whose
+ * inner linear solves are preconditioned CG (Sec. 6, Eq.
+ * shift_invert_system_unified).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid:      N x N x N nodes, N even and >= 4; node (i, j, k) sits at reduced
+ *            coordinate (i, j, k)/N; full-grid order l = i + N (j + N k)
+ *            (Eq. H_def: i fastest).
+ * Blocks:    block b = 2 p12 + p13 holds the nodes with (i+j) mod 2 = p12 and
+ *            (i+k) mod 2 = p13, i.e. the common eigenspace of Gamma_12,
+ *            Gamma_13 with signs ((-1)^p12, (-1)^p13) (Eqs. V_sigma_main,
+ *            Proj_sigma_main).  b = 0,1,2,3 <-> V_{++}, V_{+-}, V_{-+}, V_{--}.
+ *            Block b has n_b = N^3/4 nodes; its canonical order t lists them by
+ *            ascending full index l, which is t = i' + (N/2)(j'' + (N/2) k) with
+ *            i = 2 i' + ((k + p13) mod 2), j = 2 j'' + ((k + p12 + p13) mod 2).
+ *            block = -1 selects the full space (all n = N^3 nodes, order l).
+ * Vectors:   complex, component-major: x[alpha * m + t], alpha = 0,1,2 the
+ *            Cartesian velocity component, m = n_b (block) or n (full space).
+ *            PC_C64 = interleaved float (re, im); PC_C128 = interleaved double.
+ *            Vector arguments are DEVICE pointers owned by the caller; the
+ *            library never frees them.
+ * Units:     the library non-dimensionalises (Sec. 7.1, "after
+ *            nondimensionalization"): stiffness C/C0 with C0 = 1e9 Pa, density
+ *            rho/rho0 with rho0 = 1e3 kg/m^3, lengths /L with
+ *            L = |det A_lat|^(1/3).  Operators applied through this ABI are
+ *            A_hat = A_h L^2 / C0 and M_hat = M_h / rho0; eigenvalues of the
+ *            hat pencil relate to SI as lambda_SI = lambda_hat C0 / (rho0 L^2).
+ *            pc_eigs returns SI values (rad^2/s^2).
+ * Streams:   `stream` is a cudaStream_t (0 = legacy default stream).  Calls
+ *            that take a stream only enqueue work on it; they do not
+ *            synchronise unless stated.
+ * Errors:    every function returns PC_OK (0) or a negative PC_E* code; the
+ *            message of the last failure on the calling thread is returned by
+ *            pc_last_error().  No call aborts the process or traps the GPU:
+ *            device loops carry iteration caps and report through status codes.
+ * Threads:   a pc_grid handle must not be used by two threads at once; any
+ *            number of handles may coexist.
+ */
+#ifndef PCBAND_H
+#define PCBAND_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PC_OK 0
+#define PC_EINVAL (-1)      /* bad argument: odd/small N, block, dtype, null pointer */
+#define PC_ENOMEM (-2)      /* device or host allocation failed */
+#define PC_ECUDA (-3)       /* a CUDA / cuFFT / cuBLAS call failed */
+#define PC_ENOCONV (-4)     /* iteration cap reached; outputs hold the best iterate */
+#define PC_EBREAKDOWN (-5)  /* PCG found p^H (A - sigma M) p <= 0: shifted operator not SPD */
+#define PC_ENAN (-6)        /* NaN or Inf met in a reduction */
+#define PC_ESTATE (-7)      /* call out of order (e.g. apply before pc_set_k) */
+
+/* ---- element types ----------------------------------------------------- */
+#define PC_C64 1   /* complex64: FP32 storage and FP32 arithmetic */
+#define PC_C128 2  /* complex128: FP64 storage and FP64 arithmetic */
+
+/* ---- precision of pc_eigs ---------------------------------------------- */
+#define PC_PREC_FP64 0   /* every step in FP64 (plain method) */
+#define PC_PREC_MIXED 1  /* complex64 inner PCG, FP64 outer Krylov + residual refinement */
+
+typedef struct pc_grid pc_grid; /* opaque, owned by the library */
+
+/* Two-phase material, copied at pc_grid_create (caller keeps ownership). */
+typedef struct {
+    double rho[2];         /* density of phase 0 (matrix) and phase 1 (inclusion), kg/m^3 */
+    double C[2][36];       /* 6x6 Voigt stiffness per phase, row-major, order [11,22,33,23,13,12],
+                              engineering shear (Sec. 2, Eq. constitutive_voigt_main), Pa; symmetric */
+    const uint8_t* phase;  /* host, N^3 phase ids (0/1) in full order, or NULL */
+    const float* theta;    /* host, N^3 inclusion fractions in [0,1] (Eq. subpixel_material_average),
+                              or NULL; at most one of phase/theta non-NULL; both NULL = phase 0 */
+    double a_lat[9];       /* lattice basis A_lat = [a1 a2 a3], column-major: a_lat[3*l + r] = (a_l)_r, m */
+} pc_material;
+
+/* Outcome of one PCG solve. */
+typedef struct {
+    int iters;          /* iterations taken */
+    int status;         /* PC_OK, PC_ENOCONV, PC_EBREAKDOWN or PC_ENAN */
+    double rel_resid;   /* final ||r|| / ||rhs|| (recurrence residual) */
+} pc_pcg_info;
+
+/* Options of pc_eigs; fill with pc_options_default first. */
+typedef struct {
+    double tol;          /* converged when the true relative residual
+                            ||A x - lambda M x|| / (|lambda| ||M x||) <= tol (FP64); default 1e-8 */
+    double inner_tol;    /* relative residual of each shift-invert solve; default 1e-10 */
+    int precision;       /* PC_PREC_FP64 or PC_PREC_MIXED */
+    int full_space;      /* 0: four parity blocks merged (default); 1: one full-space solve */
+    int block_size;      /* Krylov block width per parity block; default 4 */
+    int max_basis;       /* Krylov-Schur basis size before restart; default 32 */
+    int max_restarts;    /* outer iteration cap; default 60 */
+    int inner_maxit;     /* PCG iteration cap per solve; default 400 */
+    int guard;           /* extra Ritz pairs carried per block beyond its share; default 3 */
+    int verbose;         /* 0 = silent */
+} pc_options;
+
+/* Statistics of one pc_eigs call. */
+typedef struct {
+    int status;              /* PC_OK or PC_ENOCONV */
+    int outer_iters;         /* Krylov-Schur expansions, summed over blocks */
+    int inner_solves;        /* shift-invert solves, summed over blocks */
+    long long pcg_iters;     /* PCG iterations summed over all solves (and right-hand sides) */
+    int max_pcg_iters;       /* longest single solve */
+    int zero_modes;          /* zero-derivative modes deflated (12 full / 3 per block at Gamma) */
+    double max_rel_resid;    /* largest true relative residual among returned pairs */
+    double seconds;          /* wall time of the call */
+} pc_eigs_info;
+
+/* ---- lifecycle --------------------------------------------------------- */
+
+/* Create a grid: copies the material to the device (phase ids or fractions in
+ * full order and in the four block orders).  N even, >= 4.  *out receives the
+ * handle.  Allocates device memory with cudaMalloc on the current device. */
+int pc_grid_create(int N, const pc_material* m, pc_grid** out);
+
+/* Release every device and host resource of the grid.  NULL is accepted. */
+int pc_grid_destroy(pc_grid* g);
+
+/* Scales of the non-dimensional units used by apply/PCG (see Units above). */
+int pc_grid_units(const pc_grid* g, double* C0, double* rho0, double* L);
+
+/* Set the Bloch vector: kappa in reduced reciprocal coordinates, phase
+ * phi_l = 2 pi kappa_l across the l-th lattice translation (Eqs.
+ * reduced_bloch_coordinate, phi_def).  Rebuilds the per-k Fourier symbol
+ * tables of the preconditioner (Sec. 5.3, Eq. Bhat_xi_m_def). Synchronous. */
+int pc_set_k(pc_grid* g, const double kappa[3]);
+
+/* Host-only index map (no GPU needed): full_node_of_t[t] = full index l of
+ * position t of block b, for t < N^3/4 (ascending l; Sec. 4, Eq. V_sigma_main).
+ * full_node_of_t is caller-owned host memory of N^3/4 entries. */
+int pc_block_index(int N, int block, int64_t* full_node_of_t);
+
+/* ---- operator ---------------------------------------------------------- */
+
+/* y = (A_hat - shift M_hat) x on block b (0..3) or the full space (b = -1):
+ * the matrix-free chain x -> B^H x -> C B^H x -> B C B^H x of Sec. 6.1 with
+ * Bloch-phased body-diagonal differences (Eqs. Sd_def, Dd_def,
+ * Dtilde_recon_main, Dcal_cartesian_transform_main, B_discrete_main).
+ * x, y: device, 3*m elements of `dtype`, must not overlap.  Enqueued on stream. */
+int pc_block_apply(pc_grid* g, int block, int dtype, const void* x, void* y, double shift,
+                   void* stream);
+
+/* Same as pc_block_apply for `count` vectors of one block at once:
+ * x and y hold `count` consecutive vectors of 3*m elements each. */
+int pc_block_apply_many(pc_grid* g, int block, int dtype, int count, const void* x, void* y,
+                        double shift, void* stream);
+
+/* Apply M_hat (nodewise density, Eq. discrete_GEP) to a block vector. */
+int pc_block_mass(pc_grid* g, int block, int dtype, const void* x, void* y, void* stream);
+
+/* Gather block b of a full-space vector (Q_sigma^T x, Eq. Asigma_main) or
+ * scatter a block vector into a full-space vector (Q_sigma y; other blocks'
+ * entries untouched).  direction 0 = full->block, 1 = block->full. */
+int pc_block_transfer(pc_grid* g, int block, int dtype, int direction, const void* src, void* dst,
+                      void* stream);
+
+/* Block Bloch Fourier transform (Sec. 5.2, Eq. Tsigma_unified): forward
+ * (inverse = 0) computes what = T_sigma^H w, inverse computes w = T_sigma what.
+ * Mode order (p fastest, then q, then r) with p, q < N/2, r < N.  dtype PC_C128
+ * or PC_C64.  Requires pc_set_k. */
+int pc_block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* w, void* what,
+                     void* stream);
+
+/* ---- solvers ----------------------------------------------------------- */
+
+/* Solve (A_hat - sigma M_hat) x = rhs on block b by PCG with the block Fourier
+ * reference-medium preconditioner (Sec. 5.4, Sec. 6.1): x starts at zero and
+ * stops at ||r|| <= tol ||rhs|| or maxit.  sigma must lie below the block's
+ * lowest eigenvalue (the paper's sigma = -delta < 0); otherwise PCG may report
+ * PC_EBREAKDOWN.  At Gamma the zero-derivative modes are not touched.
+ * Synchronises the stream to fill `info` (may be NULL). */
+int pc_shift_invert_pcg(pc_grid* g, int block, int dtype, double sigma, const void* rhs, void* x,
+                        double tol, int maxit, pc_pcg_info* info, void* stream);
+
+/* Fill `opt` with the defaults listed in pc_options. */
+int pc_options_default(pc_options* opt);
+
+/* Default shift sigma = -delta with delta = 0.30 C_max / rho_max in the hat
+ * units (Eq. num_shift_delta_rule, with density normalised by its maximum). */
+double pc_default_sigma(const pc_grid* g);
+
+/* Lowest `nev` non-zero eigenvalues of (A_h(kappa), M_h) (Sec. 6): sets kappa,
+ * solves the four parity blocks with shift-invert Krylov-Schur and merges
+ * their spectra (Eq. block_gep_impl_unified), or solves the full space when
+ * opt->full_space.  At kappa = 0 (mod 1) the zero-derivative modes found by
+ * the Fourier SVD of the symbol blocks (Sec. 6.2, Eq. gamma_null_space_main)
+ * are M-orthogonally projected out and not reported.  sigma: shift-invert
+ * target in hat units (pass NaN for pc_default_sigma).
+ * evals: host, nev doubles, ascending, SI (rad^2/s^2).
+ * evecs: NULL or device [nev][3][N^3] complex128, full-space layout, M_h-normalised.
+ * block_of: NULL or host int[nev], source block of each value (-1 for full space).
+ * info: NULL or statistics.  Synchronous. */
+int pc_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_options* opt,
+            double* evals, void* evecs, int* block_of, pc_eigs_info* info);
+
+/* ---- diagnostics ------------------------------------------------------- */
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* pc_last_error(void);
+
+/* Library version string. */
+const char* pc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCBAND_H */

@@ -1,0 +1,272 @@
+"""ctypes binding of ``libpcband.so``: argument marshalling only.
+
+Every function mirrors the C entry point of the same name declared in
+``include/pcband.h``; status codes become exceptions.  Device vectors are
+passed as torch CUDA tensors (or raw integer device addresses); nothing here
+computes any part of the method.  A missing library raises at import.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpcband.so")
+
+PC_OK, PC_EINVAL, PC_ENOMEM, PC_ECUDA, PC_ENOCONV, PC_EBREAKDOWN, PC_ENAN, PC_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+PC_C64, PC_C128 = 1, 2
+PC_PREC_FP64, PC_PREC_MIXED = 0, 1
+
+EXPORTED = [
+    "pc_grid_create", "pc_grid_destroy", "pc_grid_units", "pc_set_k", "pc_block_index",
+    "pc_block_apply", "pc_block_apply_many", "pc_block_mass", "pc_block_transfer",
+    "pc_block_fourier", "pc_shift_invert_pcg", "pc_options_default", "pc_default_sigma",
+    "pc_eigs", "pc_last_error", "pc_version",
+]
+
+
+class PcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (status %d)" % (msg, code))
+        self.code = code
+
+
+class PcNoConvergence(PcError):
+    pass
+
+
+class PcBreakdown(PcError):
+    pass
+
+
+class c_material(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double * 2), ("C", (ctypes.c_double * 36) * 2),
+                ("phase", ctypes.POINTER(ctypes.c_uint8)), ("theta", ctypes.POINTER(ctypes.c_float)),
+                ("a_lat", ctypes.c_double * 9)]
+
+
+class c_pcg_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("rel_resid", ctypes.c_double)]
+
+
+class c_options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("precision", ctypes.c_int),
+                ("full_space", ctypes.c_int), ("block_size", ctypes.c_int), ("max_basis", ctypes.c_int),
+                ("max_restarts", ctypes.c_int), ("inner_maxit", ctypes.c_int), ("guard", ctypes.c_int),
+                ("verbose", ctypes.c_int)]
+
+
+class c_eigs_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iters", ctypes.c_int), ("inner_solves", ctypes.c_int),
+                ("pcg_iters", ctypes.c_longlong), ("max_pcg_iters", ctypes.c_int),
+                ("zero_modes", ctypes.c_int), ("max_rel_resid", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libpcband.so is not built: run __graft_entry__.build() "
+                          "(or python -m paper_2606_03599_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "pc_grid_create": ([ci, ctypes.POINTER(c_material), ctypes.POINTER(vp)], ci),
+        "pc_grid_destroy": ([vp], ci),
+        "pc_grid_units": ([vp, dp, dp, dp], ci),
+        "pc_set_k": ([vp, dp], ci),
+        "pc_block_index": ([ci, ci, ctypes.POINTER(ctypes.c_int64)], ci),
+        "pc_block_apply": ([vp, ci, ci, vp, vp, cd, vp], ci),
+        "pc_block_apply_many": ([vp, ci, ci, ci, vp, vp, cd, vp], ci),
+        "pc_block_mass": ([vp, ci, ci, vp, vp, vp], ci),
+        "pc_block_transfer": ([vp, ci, ci, ci, vp, vp, vp], ci),
+        "pc_block_fourier": ([vp, ci, ci, ci, vp, vp, vp], ci),
+        "pc_shift_invert_pcg": ([vp, ci, ci, cd, vp, vp, cd, ci, ctypes.POINTER(c_pcg_info), vp], ci),
+        "pc_options_default": ([ctypes.POINTER(c_options)], ci),
+        "pc_default_sigma": ([vp], cd),
+        "pc_eigs": ([vp, dp, ci, cd, ctypes.POINTER(c_options), dp, vp, ctypes.POINTER(ci),
+                     ctypes.POINTER(c_eigs_info)], ci),
+        "pc_last_error": ([], ctypes.c_char_p),
+        "pc_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc):
+    if rc == PC_OK:
+        return
+    msg = lib.pc_last_error().decode()
+    if rc == PC_ENOCONV:
+        raise PcNoConvergence(rc, msg)
+    if rc == PC_EBREAKDOWN:
+        raise PcBreakdown(rc, msg)
+    raise PcError(rc, msg)
+
+
+def _ptr(t):
+    """Device address of a torch tensor (or an int address)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_contiguous():
+        raise ValueError("vector arguments must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.complex64:
+        return PC_C64
+    if t.dtype == torch.complex128:
+        return PC_C128
+    raise TypeError("vectors must be complex64 or complex128")
+
+
+def make_material(C, rho, phase=None, theta=None, a_lat=None):
+    """pc_material from per-phase stiffness (2,6,6) Pa, densities (2,), optional phase/theta arrays.
+
+    Returns (struct, keepalive) -- keep ``keepalive`` referenced until the create call returns.
+    """
+    m = c_material()
+    C = np.asarray(C, dtype=np.float64).reshape(2, 36)
+    for p in range(2):
+        m.rho[p] = float(rho[p])
+        for e in range(36):
+            m.C[p][e] = float(C[p, e])
+    keep = []
+    if phase is not None:
+        ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint8))
+        keep.append(ph)
+        m.phase = ph.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    if theta is not None:
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+        keep.append(th)
+        m.theta = th.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    A = np.eye(3) if a_lat is None else np.asarray(a_lat, dtype=np.float64)
+    for l in range(3):
+        for r in range(3):
+            m.a_lat[3 * l + r] = float(A[r, l])
+    return m, keep
+
+
+def pc_grid_create(N, C, rho, phase=None, theta=None, a_lat=None):
+    m, keep = make_material(C, rho, phase, theta, a_lat)
+    h = ctypes.c_void_p()
+    _check(lib.pc_grid_create(int(N), ctypes.byref(m), ctypes.byref(h)))
+    del keep
+    return h.value
+
+
+def pc_grid_destroy(g):
+    _check(lib.pc_grid_destroy(g))
+
+
+def pc_grid_units(g):
+    c0, r0, L = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib.pc_grid_units(g, ctypes.byref(c0), ctypes.byref(r0), ctypes.byref(L)))
+    return c0.value, r0.value, L.value
+
+
+def pc_set_k(g, kappa):
+    k = (ctypes.c_double * 3)(*[float(v) for v in kappa])
+    _check(lib.pc_set_k(g, k))
+
+
+def pc_block_index(N, block):
+    out = np.empty(int(N) ** 3 // 4, dtype=np.int64)
+    _check(lib.pc_block_index(int(N), int(block), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return out
+
+
+def pc_block_apply(g, block, x, y, shift=0.0, stream=None):
+    _check(lib.pc_block_apply(g, int(block), _dtype_code(x), _ptr(x), _ptr(y), float(shift),
+                              _stream(stream)))
+
+
+def pc_block_apply_many(g, block, count, x, y, shift=0.0, stream=None):
+    _check(lib.pc_block_apply_many(g, int(block), _dtype_code(x), int(count), _ptr(x), _ptr(y),
+                                   float(shift), _stream(stream)))
+
+
+def pc_block_mass(g, block, x, y, stream=None):
+    _check(lib.pc_block_mass(g, int(block), _dtype_code(x), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def pc_block_transfer(g, block, direction, src, dst, stream=None):
+    _check(lib.pc_block_transfer(g, int(block), _dtype_code(src), int(direction), _ptr(src), _ptr(dst),
+                                 _stream(stream)))
+
+
+def pc_block_fourier(g, block, inverse, w, what, stream=None):
+    _check(lib.pc_block_fourier(g, int(block), _dtype_code(w), int(inverse), _ptr(w), _ptr(what),
+                                _stream(stream)))
+
+
+def pc_shift_invert_pcg(g, block, sigma, rhs, x, tol=1e-10, maxit=400, stream=None, raise_on_fail=True):
+    info = c_pcg_info()
+    rc = lib.pc_shift_invert_pcg(g, int(block), _dtype_code(rhs), float(sigma), _ptr(rhs), _ptr(x),
+                                 float(tol), int(maxit), ctypes.byref(info), _stream(stream))
+    if raise_on_fail:
+        _check(rc)
+    return {"rc": rc, "iters": info.iters, "status": info.status, "rel_resid": info.rel_resid}
+
+
+def pc_options_default(**overrides):
+    o = c_options()
+    _check(lib.pc_options_default(ctypes.byref(o)))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def pc_default_sigma(g):
+    return float(lib.pc_default_sigma(g))
+
+
+def pc_eigs(g, kappa, nev, sigma=float("nan"), opt=None, evecs=None, raise_on_fail=True):
+    """Returns (evals SI ascending, block_of, info dict)."""
+    opt = opt if opt is not None else pc_options_default()
+    k = (ctypes.c_double * 3)(*[float(v) for v in kappa])
+    ev = np.empty(int(nev), dtype=np.float64)
+    bo = (ctypes.c_int * int(nev))()
+    info = c_eigs_info()
+    rc = lib.pc_eigs(g, k, int(nev), float(sigma), ctypes.byref(opt),
+                     ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(evecs), bo,
+                     ctypes.byref(info))
+    if raise_on_fail:
+        _check(rc)
+    d = {f: getattr(info, f) for f, _ in c_eigs_info._fields_}
+    d["rc"] = rc
+    return ev, np.array(list(bo)), d
+
+
+def pc_version():
+    return lib.pc_version().decode()
+
+
+def nan():
+    return math.nan

@@ -1,0 +1,312 @@
+// C ABI: grid lifecycle, Bloch vector, index maps, operator entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pc_internal.h"
+
+namespace pc {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA;
+}
+
+int launch_mass(int dtype, const void* x, void* y, const void* mat, int matkind, double rho0,
+                double rho1, int64_t m, cudaStream_t s);
+int launch_transfer(int dtype, const void* src, void* dst, int N, int b, int dir, cudaStream_t s);
+
+int tile_tx(int shape) { return shape == 0 ? 32 : shape == 1 ? 16 : shape == 2 ? 8 : 4; }
+int tile_ty(int shape) { return shape <= 2 ? 8 : 4; }
+
+ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype) {
+    ApplyConfig c;
+    // widest tile whose a-extent divides X (no ragged tiles in a); FP64 capped at 16x8
+    c.shape = 3;
+    const int first = (dtype == PC_C128) ? 1 : 0;
+    for (int s = first; s <= 2; ++s) {
+        if (X % tile_tx(s) == 0 && X >= tile_tx(s) && Y >= tile_ty(s)) {
+            c.shape = s;
+            break;
+        }
+    }
+    const int tiles = ((X + tile_tx(c.shape) - 1) / tile_tx(c.shape)) *
+                      ((Y + tile_ty(c.shape) - 1) / tile_ty(c.shape));
+    const long target = 152L * 4;  // about four resident CTAs per SM
+    long nch = (target + (long)tiles * nitems - 1) / ((long)tiles * nitems);
+    const long maxch = Z / 4 > 0 ? Z / 4 : 1;
+    if (nch > maxch) nch = maxch;
+    if (nch < 1) nch = 1;
+    c.tz = (int)((Z + nch - 1) / nch);
+    c.ctas = tiles * ((Z + c.tz - 1) / c.tz);
+    return c;
+}
+
+static bool finite_all(const double* v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+static void fill_params(pc_grid* g) {
+    make_stencil_params(g->P64, g->Chat, g->rhohat, g->Ainv, g->cubic, g->N, g->k.phi, g->X, g->Y, g->Z);
+    make_stencil_params(g->P32, g->Chat, g->rhohat, g->Ainv, g->cubic, g->N, g->k.phi, g->X, g->Y, g->Z);
+}
+
+extern "C" {
+
+const char* pc_last_error(void) { return g_last_error.c_str(); }
+
+const char* pc_version(void) { return "pcband 0.1 (sm_103a)"; }
+
+int pc_block_index(int N, int block, int64_t* out) {
+    if (N < 4 || (N & 1)) return fail(PC_EINVAL, "pc_block_index: N must be even and >= 4");
+    if (block < 0 || block > 3) return fail(PC_EINVAL, "pc_block_index: block must be 0..3");
+    if (!out) return fail(PC_EINVAL, "pc_block_index: null output");
+    const int X = N / 2;
+    const int p12 = block >> 1, p13 = block & 1;
+    int64_t t = 0;
+    for (int k = 0; k < N; ++k)
+        for (int b = 0; b < X; ++b)
+            for (int a = 0; a < X; ++a, ++t) {
+                int64_t i = 2 * a + ((k + p13) & 1);
+                int64_t j = 2 * b + ((k + p12 + p13) & 1);
+                out[t] = i + (int64_t)N * (j + (int64_t)N * k);
+            }
+    return PC_OK;
+}
+
+int pc_grid_units(const pc_grid* g, double* C0, double* rho0, double* L) {
+    if (!g) return fail(PC_EINVAL, "pc_grid_units: null grid");
+    if (C0) *C0 = g->C0;
+    if (rho0) *rho0 = g->rho0;
+    if (L) *L = g->L;
+    return PC_OK;
+}
+
+int pc_grid_destroy(pc_grid* g) {
+    if (!g) return PC_OK;
+    release_solver_state(g);
+    cudaFree(g->d_mat_full);
+    for (int b = 0; b < 4; ++b) cudaFree(g->d_mat_blk[b]);
+    cudaFree(g->d_dot);
+    delete g;
+    return PC_OK;
+}
+
+int pc_grid_create(int N, const pc_material* m, pc_grid** out) {
+    if (!out) return fail(PC_EINVAL, "pc_grid_create: null output");
+    *out = nullptr;
+    if (N < 4 || (N & 1)) return fail(PC_EINVAL, "pc_grid_create: N must be even and >= 4 (parity blocks need even grids)");
+    if (N > 1024) return fail(PC_EINVAL, "pc_grid_create: N > 1024 not supported");
+    if (!m) return fail(PC_EINVAL, "pc_grid_create: null material");
+    if (m->phase && m->theta) return fail(PC_EINVAL, "pc_grid_create: give phase or theta, not both");
+    if (!finite_all(&m->C[0][0], 72) || !finite_all(m->rho, 2) || !finite_all(m->a_lat, 9))
+        return fail(PC_EINVAL, "pc_grid_create: non-finite material constants");
+    for (int p = 0; p < 2; ++p) {
+        if (!(m->rho[p] > 0)) return fail(PC_EINVAL, "pc_grid_create: densities must be positive");
+        double scale = 0;
+        for (int e = 0; e < 36; ++e) scale = std::fmax(scale, std::fabs(m->C[p][e]));
+        for (int a = 0; a < 6; ++a)
+            for (int b = a + 1; b < 6; ++b)
+                if (std::fabs(m->C[p][a * 6 + b] - m->C[p][b * 6 + a]) > 1e-12 * scale)
+                    return fail(PC_EINVAL, "pc_grid_create: stiffness must be symmetric");
+    }
+    // A_lat (column-major input) and its determinant
+    double A[3][3];
+    for (int l = 0; l < 3; ++l)
+        for (int r = 0; r < 3; ++r) A[r][l] = m->a_lat[3 * l + r];
+    double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                 A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                 A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    if (!(std::fabs(det) > 0)) return fail(PC_EINVAL, "pc_grid_create: singular lattice basis");
+
+    pc_grid* g = new pc_grid();
+    g->N = N;
+    g->X = N / 2;
+    g->Y = N / 2;
+    g->Z = N;
+    g->n = (int64_t)N * N * N;
+    g->nb = g->n / 4;
+    g->L = std::cbrt(std::fabs(det));
+    cudaGetDevice(&g->device);
+    for (int p = 0; p < 2; ++p) {
+        for (int e = 0; e < 36; ++e) g->Chat[p][e] = m->C[p][e] / g->C0;
+        g->rhohat[p] = m->rho[p] / g->rho0;
+    }
+    // inverse of A_hat = A_lat / L, row-major (A^-1)_{s m}
+    double Ah[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int l = 0; l < 3; ++l) Ah[r][l] = A[r][l] / g->L;
+    double dh = det / (g->L * g->L * g->L);
+    double inv[3][3];
+    inv[0][0] = (Ah[1][1] * Ah[2][2] - Ah[1][2] * Ah[2][1]) / dh;
+    inv[0][1] = (Ah[0][2] * Ah[2][1] - Ah[0][1] * Ah[2][2]) / dh;
+    inv[0][2] = (Ah[0][1] * Ah[1][2] - Ah[0][2] * Ah[1][1]) / dh;
+    inv[1][0] = (Ah[1][2] * Ah[2][0] - Ah[1][0] * Ah[2][2]) / dh;
+    inv[1][1] = (Ah[0][0] * Ah[2][2] - Ah[0][2] * Ah[2][0]) / dh;
+    inv[1][2] = (Ah[0][2] * Ah[1][0] - Ah[0][0] * Ah[1][2]) / dh;
+    inv[2][0] = (Ah[1][0] * Ah[2][1] - Ah[1][1] * Ah[2][0]) / dh;
+    inv[2][1] = (Ah[0][1] * Ah[2][0] - Ah[0][0] * Ah[2][1]) / dh;
+    inv[2][2] = (Ah[0][0] * Ah[1][1] - Ah[0][1] * Ah[1][0]) / dh;
+    double dev = 0;
+    for (int s = 0; s < 3; ++s)
+        for (int mm = 0; mm < 3; ++mm) {
+            g->Ainv[s * 3 + mm] = inv[s][mm];
+            dev = std::fmax(dev, std::fabs(inv[s][mm] - (s == mm ? 1.0 : 0.0)));
+        }
+    g->cubic = dev < 1e-12;
+
+    // material: full order and the four block orders
+    g->matkind = m->theta ? 1 : 0;
+    const size_t esz = g->matkind ? sizeof(float) : sizeof(uint8_t);
+    std::vector<unsigned char> full(g->n * esz, 0);
+    if (m->phase) {
+        for (int64_t l = 0; l < g->n; ++l) {
+            if (m->phase[l] > 1) {
+                delete g;
+                return fail(PC_EINVAL, "pc_grid_create: phase ids must be 0 or 1");
+            }
+            full[l] = m->phase[l];
+        }
+    } else if (m->theta) {
+        for (int64_t l = 0; l < g->n; ++l)
+            if (!(m->theta[l] >= 0.f && m->theta[l] <= 1.f)) {
+                delete g;
+                return fail(PC_EINVAL, "pc_grid_create: theta must lie in [0,1]");
+            }
+        std::memcpy(full.data(), m->theta, g->n * esz);
+    }
+    cudaError_t e = cudaMalloc(&g->d_mat_full, g->n * esz);
+    if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMalloc(material)"); }
+    e = cudaMemcpy(g->d_mat_full, full.data(), g->n * esz, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMemcpy(material)"); }
+    std::vector<int64_t> idx(g->nb);
+    std::vector<unsigned char> blk(g->nb * esz);
+    for (int b = 0; b < 4; ++b) {
+        pc_block_index(N, b, idx.data());
+        for (int64_t t = 0; t < g->nb; ++t) std::memcpy(&blk[t * esz], &full[idx[t] * esz], esz);
+        e = cudaMalloc(&g->d_mat_blk[b], g->nb * esz);
+        if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMalloc(block material)"); }
+        e = cudaMemcpy(g->d_mat_blk[b], blk.data(), g->nb * esz, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMemcpy(block material)"); }
+    }
+    fill_params(g);
+    *out = g;
+    return PC_OK;
+}
+
+int pc_set_k(pc_grid* g, const double kappa[3]) {
+    if (!g || !kappa) return fail(PC_EINVAL, "pc_set_k: null argument");
+    if (!finite_all(kappa, 3)) return fail(PC_EINVAL, "pc_set_k: non-finite kappa");
+    bool gamma = true;
+    for (int l = 0; l < 3; ++l) {
+        g->k.kappa[l] = kappa[l];
+        // phase of kappa mod 1, reduced first so that exact lattice vectors give phase 0
+        double frac = kappa[l] - std::floor(kappa[l]);
+        g->k.phi[l] = 2.0 * M_PI * frac;
+        if (frac != 0.0) gamma = false;
+    }
+    g->k.gamma = gamma;
+    g->k.set = true;
+    fill_params(g);
+    return precond_set_k(g);
+}
+
+}  // extern "C"
+
+namespace pc {
+
+// Launch one batch of stencil applies on grid g (items share the layout kind).
+int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nitems, double* dot_partials,
+               int dot_stride, cudaStream_t s, const ApplyConfig* cfg_in) {
+    const int X = full ? g->N : g->X, Y = full ? g->N : g->Y, Z = g->Z;
+    ApplyConfig cfg = cfg_in ? *cfg_in : choose_apply_config(X, Y, Z, nitems, dtype);
+    if (dtype == PC_C64) {
+        StencilParams<float> P = g->P32;
+        P.X = X;
+        P.Y = Y;
+        P.Z = Z;
+        return launch_apply_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
+                                dot_stride, s);
+    }
+    StencilParams<double> P = g->P64;
+    P.X = X;
+    P.Y = Y;
+    P.Z = Z;
+    return launch_apply_f64(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
+                            dot_stride, s);
+}
+
+const void* grid_mat(const pc_grid* g, int block) { return block < 0 ? g->d_mat_full : g->d_mat_blk[block]; }
+
+}  // namespace pc
+
+extern "C" {
+
+int pc_block_apply_many(pc_grid* g, int block, int dtype, int count, const void* x, void* y, double shift,
+                        void* stream) {
+    if (!g) return fail(PC_EINVAL, "pc_block_apply: null grid");
+    if (block < -1 || block > 3) return fail(PC_EINVAL, "pc_block_apply: block must be -1..3");
+    if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_block_apply: dtype must be PC_C64 or PC_C128");
+    if (!x || !y) return fail(PC_EINVAL, "pc_block_apply: null vector");
+    if (count < 0) return fail(PC_EINVAL, "pc_block_apply: negative count");
+    if (!std::isfinite(shift)) return fail(PC_EINVAL, "pc_block_apply: non-finite shift");
+    if (!g->k.set) return fail(PC_ESTATE, "pc_block_apply: call pc_set_k first");
+    if (count == 0) return PC_OK;
+    const int64_t m = block < 0 ? g->n : g->nb;
+    const size_t vbytes = 3 * m * (dtype == PC_C64 ? 8 : 16);
+    const char* xb = static_cast<const char*>(x);
+    char* yb = static_cast<char*>(y);
+    if (xb < yb + vbytes * count && yb < xb + vbytes * count)
+        return fail(PC_EINVAL, "pc_block_apply: x and y overlap");
+    std::vector<ApplyItem> items(count);
+    for (int i = 0; i < count; ++i) {
+        items[i].x = xb + vbytes * i;
+        items[i].y = yb + vbytes * i;
+        items[i].mat = grid_mat(g, block);
+        items[i].shift = shift;
+        items[i].block = block;
+        items[i].dot_slot = -1;
+    }
+    return grid_apply(g, dtype, block < 0, items.data(), count, nullptr, 0, (cudaStream_t)stream, nullptr);
+}
+
+int pc_block_apply(pc_grid* g, int block, int dtype, const void* x, void* y, double shift, void* stream) {
+    return pc_block_apply_many(g, block, dtype, 1, x, y, shift, stream);
+}
+
+int pc_block_mass(pc_grid* g, int block, int dtype, const void* x, void* y, void* stream) {
+    if (!g || !x || !y) return fail(PC_EINVAL, "pc_block_mass: null argument");
+    if (block < -1 || block > 3) return fail(PC_EINVAL, "pc_block_mass: block must be -1..3");
+    if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_block_mass: bad dtype");
+    const int64_t m = block < 0 ? g->n : g->nb;
+    return launch_mass(dtype, x, y, grid_mat(g, block), g->matkind, g->rhohat[0], g->rhohat[1], m,
+                       (cudaStream_t)stream);
+}
+
+int pc_block_transfer(pc_grid* g, int block, int dtype, int direction, const void* src, void* dst,
+                      void* stream) {
+    if (!g || !src || !dst) return fail(PC_EINVAL, "pc_block_transfer: null argument");
+    if (block < 0 || block > 3) return fail(PC_EINVAL, "pc_block_transfer: block must be 0..3");
+    if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_block_transfer: bad dtype");
+    if (direction != 0 && direction != 1) return fail(PC_EINVAL, "pc_block_transfer: direction must be 0 or 1");
+    return launch_transfer(dtype, src, dst, g->N, block, direction, (cudaStream_t)stream);
+}
+
+}  // extern "C"

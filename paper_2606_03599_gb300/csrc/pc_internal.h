@@ -1,0 +1,135 @@
+// Internal declarations of the pcband library (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <cublas_v2.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pcband.h"
+
+namespace pc {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define PC_CUDA_TRY(expr)                                      \
+    do {                                                       \
+        cudaError_t _e = (expr);                               \
+        if (_e != cudaSuccess) return ::pc::cuda_fail(_e, #expr); \
+    } while (0)
+
+#define PC_TRY(expr)                \
+    do {                            \
+        int _rc = (expr);           \
+        if (_rc != PC_OK) return _rc; \
+    } while (0)
+
+// ---------------------------------------------------------------- device parameters
+// Everything a stencil launch needs about one grid at one Bloch vector, passed
+// by value (kernel parameter space).  R = float (complex64 path) or double.
+template <typename R>
+struct StencilParams {
+    R C[2][36];   // stiffness per phase in hat units, times (N/4)^2 when the lattice is cubic
+    R rho[2];     // density per phase in hat units
+    R Mmix[9];    // Mmix[s*3+m] = (A_hat^-1)_{s m} / (4 h_s); unused when cubic
+    R ph[3][2];   // (cos phi_l, sin phi_l)
+    int N;        // grid size
+    int X, Y, Z;  // lattice extents of the vector layout (N/2, N/2, N) or (N, N, N)
+};
+
+// One vector to process in a batched stencil launch.
+struct ApplyItem {
+    const void* x;
+    void* y;
+    const void* mat;  // material of this layout (uint8 phase ids or float theta)
+    double shift;     // y = (A - shift M) x
+    int block;        // 0..3 or -1 (full)
+    int dot_slot;     // >= 0: write <x, y> partials to dot scratch slot, else -1
+};
+
+// ---------------------------------------------------------------- kernels (launch wrappers)
+// Fused stencil apply over a batch of items sharing params and layout kind.
+// shape: tile code (0 = 32x8, 1 = 16x8, 2 = 8x8, 3 = 4x4); tz: k-planes per CTA.
+// dp: per-CTA partial sums of Re<x, y> (slot-major, stride ds) or nullptr.
+int launch_apply_f32(bool full, bool cubic, int matkind, int shape, const StencilParams<float>& P,
+                     const ApplyItem* items, int nitems, int tz, double* dp, int ds, cudaStream_t s);
+int launch_apply_f64(bool full, bool cubic, int matkind, int shape, const StencilParams<double>& P,
+                     const ApplyItem* items, int nitems, int tz, double* dp, int ds, cudaStream_t s);
+
+struct ApplyConfig {
+    int shape;  // tile code
+    int tz;     // planes per CTA
+    int ctas;   // CTAs per item
+};
+ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype);
+int tile_tx(int shape);
+int tile_ty(int shape);
+
+// Stencil parameters from hat-unit material tables (Chat[2][36], rhohat[2]),
+// (A_hat^-1)_{s m} row-major, grid size N and Bloch phases phi[3].  For a cubic
+// lattice the factor (N/4)^2 of the two reconstructed derivatives is folded
+// into C; otherwise Mmix = (A_hat^-1)_{s m} / (4 h_s) with h_s = 1/N.
+template <typename R>
+inline void make_stencil_params(StencilParams<R>& P, const double Chat[2][36], const double rhohat[2],
+                                const double Ainv[9], bool cubic, int N, const double phi[3], int X,
+                                int Y, int Z) {
+    const double q = N / 4.0;
+    for (int p = 0; p < 2; ++p)
+        for (int e = 0; e < 36; ++e) P.C[p][e] = (R)(Chat[p][e] * (cubic ? q * q : 1.0));
+    for (int p = 0; p < 2; ++p) P.rho[p] = (R)rhohat[p];
+    for (int e = 0; e < 9; ++e) P.Mmix[e] = (R)(Ainv[e] * q);
+    for (int l = 0; l < 3; ++l) {
+        P.ph[l][0] = (R)std::cos(phi[l]);
+        P.ph[l][1] = (R)std::sin(phi[l]);
+    }
+    P.N = N;
+    P.X = X;
+    P.Y = Y;
+    P.Z = Z;
+}
+
+// Per-k rebuild of the preconditioner tables; release of solver workspaces.
+int precond_set_k(pc_grid* g);
+void release_solver_state(pc_grid* g);
+
+// ---------------------------------------------------------------- grid object
+struct GridK {  // per-Bloch-vector state
+    bool set = false;
+    double kappa[3] = {0, 0, 0};
+    double phi[3] = {0, 0, 0};
+    bool gamma = false;
+};
+
+}  // namespace pc
+
+struct pc_grid {
+    int N = 0, X = 0, Y = 0, Z = 0;
+    int64_t n = 0, nb = 0;
+    double C0 = 1e9, rho0 = 1e3, L = 1.0;
+    double Chat[2][36];
+    double rhohat[2];
+    double Ainv[9];  // (A_hat^-1)_{s m}, row-major s*3+m
+    bool cubic = true;
+    int matkind = 0;  // 0 = uint8 phase ids, 1 = float theta
+    void* d_mat_full = nullptr;
+    void* d_mat_blk[4] = {nullptr, nullptr, nullptr, nullptr};
+    pc::GridK k;
+    pc::StencilParams<double> P64;
+    pc::StencilParams<float> P32;
+    // scratch owned by the grid
+    pc::ApplyItem* d_items = nullptr;
+    int items_cap = 0;
+    double* d_dot = nullptr;
+    int dot_cap = 0;
+    // preconditioner / solver workspaces are attached by their modules
+    struct Precond* pre = nullptr;
+    struct Solver* sol = nullptr;
+    int device = 0;
+};

@@ -1,0 +1,96 @@
+"""The fused stencil kernel's tile logic, run by the host emulator, against the oracle (CPU only).
+
+The emulator executes the kernel's own per-thread phase functions for every
+simulated thread of every CTA, with bounds checks on each shared-memory and
+global access, so these tests check the tiling, halo, chunking and Bloch-wrap
+arithmetic of the CUDA kernel without a GPU.
+"""
+
+import ctypes
+import importlib.util
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle.oracle import Problem
+from workloads import complex_gaussian, two_phase_sphere
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def emu():
+    spec = importlib.util.spec_from_file_location(
+        "pcband_build", os.path.join(ROOT, "paper_2606_03599_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    lib = ctypes.CDLL(mod.build_emulator())
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.pc_emu_apply.argtypes = [ctypes.c_int] * 5 + [dp, dp, dp, ctypes.c_int, dp, ctypes.c_void_p,
+                                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                      ctypes.c_double]
+    lib.pc_emu_apply.restype = ctypes.c_int
+    return lib
+
+
+def run_emu(lib, pb, block, dtype, shape, tz, kappa, x, shift, matkind):
+    N = pb.dims[0]
+    dp = ctypes.POINTER(ctypes.c_double)
+    Chat = np.ascontiguousarray(pb.C.reshape(72))
+    rho = np.ascontiguousarray(pb.rho)
+    ainv = np.ascontiguousarray(pb.ainv.reshape(9))
+    cubic = int(np.abs(pb.ainv - np.eye(3)).max() < 1e-12)
+    phi = np.ascontiguousarray(2 * np.pi * (np.asarray(kappa, dtype=float) - np.floor(kappa)))
+    th = pb.theta if block < 0 else pb.theta[O.block_index(pb.dims, block)]
+    mat = np.ascontiguousarray(th.astype(np.float32) if matkind else th.astype(np.uint8))
+    ct = np.complex64 if dtype == 1 else np.complex128
+    xx = np.ascontiguousarray(x.astype(ct))
+    y = np.zeros_like(xx)
+    f = lambda a: a.ctypes.data_as(dp)  # noqa: E731
+    rc = lib.pc_emu_apply(N, block, dtype, shape, tz, f(Chat), f(rho), f(ainv), cubic, f(phi),
+                          mat.ctypes.data, matkind, xx.ctypes.data, y.ctypes.data, shift)
+    assert rc == 0
+    return y
+
+
+CASES = [
+    # N, block, dtype, shape, tz
+    (4, 0, 2, 3, 1), (4, 3, 2, 3, 4), (4, -1, 2, 3, 3),
+    (8, 1, 2, 3, 3), (8, 2, 1, 3, 2), (8, -1, 2, 2, 5), (8, 3, 2, 2, 8),
+    (12, 0, 2, 1, 5), (12, 2, 1, 0, 4), (12, -1, 2, 2, 7),
+]
+
+
+@pytest.mark.parametrize("N,block,dtype,shape,tz", CASES)
+@pytest.mark.parametrize("kappa", [[0.3, 0.1, 0.2], [0.0, 0.0, 0.0], [1.3, 0.1, -0.8]])
+def test_emulated_kernel_matches_oracle(emu, N, block, dtype, shape, tz, kappa):
+    pb = O.problem_from_cell(two_phase_sphere(N, 0.35, 1), C0=1e9, rho0=1e3)
+    m = N ** 3 // 4 if block >= 0 else N ** 3
+    x = complex_gaussian((3, m), 7)
+    ref = (O.apply_block(pb, kappa, block, x, shift=0.37) if block >= 0
+           else O.apply_full(pb, kappa, x, shift=0.37))
+    y = run_emu(emu, pb, block, dtype, shape, tz, kappa, x, 0.37, 0)
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert err < (1e-13 if dtype == 2 else 2e-6)
+
+
+@pytest.mark.parametrize("block", [1, -1])
+def test_emulated_kernel_general_lattice_and_fractions(emu, block):
+    """Non-cubic (FCC) lattice mixing and fractional (sub-pixel) material."""
+    N = 8
+    cell = two_phase_sphere(N, 0.3, 2)
+    A = np.array([[0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0]])
+    Ah = A / abs(np.linalg.det(A)) ** (1 / 3)
+    theta = np.random.default_rng(0).uniform(0, 1, N ** 3).astype(np.float32).astype(np.float64)
+    pb = Problem(dims=(N,) * 3, ainv=np.linalg.inv(Ah), C=cell.C / 1e9, rho=cell.rho / 1e3, theta=theta)
+    kappa = [0.21, -0.33, 0.4]
+    m = N ** 3 // 4 if block >= 0 else N ** 3
+    x = complex_gaussian((3, m), 9)
+    ref = (O.apply_block(pb, kappa, block, x, shift=0.5) if block >= 0
+           else O.apply_full(pb, kappa, x, shift=0.5))
+    for dtype, shape, tz in ((2, 2, 3), (1, 3, 4)):
+        y = run_emu(emu, pb, block, dtype, shape, tz, kappa, x, 0.5, 1)
+        err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+        assert err < (1e-13 if dtype == 2 else 2e-6)

@@ -133,8 +133,11 @@ int pc_grid_units(const pc_grid* g, double* C0, double* rho0, double* L);
 
 /* Set the Bloch vector: kappa in reduced reciprocal coordinates, phase
  * phi_l = 2 pi kappa_l across the l-th lattice translation (Eqs.
- * reduced_bloch_coordinate, phi_def).  Rebuilds the per-k Fourier symbol
- * tables of the preconditioner (Sec. 5.3, Eq. Bhat_xi_m_def). Synchronous. */
+ * reduced_bloch_coordinate, phi_def).  Each kappa_l is first reduced into
+ * [0, 1): the operator depends on exp(i phi_l) only, and the reduction fixes the
+ * labelling of the Bloch Fourier modes alpha_p = (phi_1 + 2 pi p)/N etc. used by
+ * pc_block_fourier.  Rebuilds the per-k Fourier symbol tables of the
+ * preconditioner (Sec. 5.3, Eq. Bhat_xi_m_def). Synchronous. */
 int pc_set_k(pc_grid* g, const double kappa[3]);
 
 /* Host-only index map (no GPU needed): full_node_of_t[t] = full index l of

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "pc_internal.h"
+#include "pc_solver.h"
 
 namespace pc {
 
@@ -23,9 +24,6 @@ int cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? PC_ENOMEM : PC_ECUDA;
 }
 
-int launch_mass(int dtype, const void* x, void* y, const void* mat, int matkind, double rho0,
-                double rho1, int64_t m, cudaStream_t s);
-int launch_transfer(int dtype, const void* src, void* dst, int N, int b, int dir, cudaStream_t s);
 
 int tile_tx(int shape) { return shape == 0 ? 32 : shape == 1 ? 16 : shape == 2 ? 8 : 4; }
 int tile_ty(int shape) { return shape <= 2 ? 8 : 4; }
@@ -192,6 +190,12 @@ int pc_grid_create(int N, const pc_material* m, pc_grid** out) {
             }
         std::memcpy(full.data(), m->theta, g->n * esz);
     }
+    {
+        double acc = 0.0;
+        for (int64_t l = 0; l < g->n; ++l)
+            acc += m->phase ? (double)m->phase[l] : (m->theta ? (double)m->theta[l] : 0.0);
+        g->mean_theta = acc / (double)g->n;
+    }
     cudaError_t e = cudaMalloc(&g->d_mat_full, g->n * esz);
     if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMalloc(material)"); }
     e = cudaMemcpy(g->d_mat_full, full.data(), g->n * esz, cudaMemcpyHostToDevice);
@@ -283,6 +287,7 @@ int pc_block_apply_many(pc_grid* g, int block, int dtype, int count, const void*
         items[i].shift = shift;
         items[i].block = block;
         items[i].dot_slot = -1;
+        items[i].skip = nullptr;
     }
     return grid_apply(g, dtype, block < 0, items.data(), count, nullptr, 0, (cudaStream_t)stream, nullptr);
 }
@@ -297,7 +302,7 @@ int pc_block_mass(pc_grid* g, int block, int dtype, const void* x, void* y, void
     if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_block_mass: bad dtype");
     const int64_t m = block < 0 ? g->n : g->nb;
     return launch_mass(dtype, x, y, grid_mat(g, block), g->matkind, g->rhohat[0], g->rhohat[1], m,
-                       (cudaStream_t)stream);
+                       (cudaStream_t)stream, 1);
 }
 
 int pc_block_transfer(pc_grid* g, int block, int dtype, int direction, const void* src, void* dst,

@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(TX * TY)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typename T::Shared& sh = *reinterpret_cast<typename T::Shared*>(smem_raw);
     const ApplyItem& it = B.it[blockIdx.z];
+    if (it.skip != nullptr && *it.skip) return;
 
     typename T::Ctx c;
     c.P = &P;

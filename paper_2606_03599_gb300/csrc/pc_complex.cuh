@@ -72,6 +72,10 @@ PC_HD float2 cmul(float2 a, float2 b) {
 PC_HD double2 cmul(double2 a, double2 b) {
     return make_double2(fma(-a.y, b.y, a.x * b.x), fma(a.y, b.x, a.x * b.y));
 }
+template <typename C> PC_HD C make_c(double re, double im);
+template <> PC_HD float2 make_c<float2>(double re, double im) { return make_float2((float)re, (float)im); }
+template <> PC_HD double2 make_c<double2>(double re, double im) { return make_double2(re, im); }
+
 PC_HD float2 czero(float) { return make_float2(0.f, 0.f); }
 PC_HD double2 czero(double) { return make_double2(0.0, 0.0); }
 

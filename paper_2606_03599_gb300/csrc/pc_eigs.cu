@@ -1,0 +1,916 @@
+// Shift-invert block Krylov-Schur eigensolver over the parity blocks (Sec. 6).
+//
+// For each space (one of the four parity blocks, Cor. 4.2, or the full space)
+// the outer iteration works with Op = (A - sigma M)^-1 M, which is
+// self-adjoint in the M inner product: eigenpairs A v = lambda M v map to
+// Op v = mu v with mu = 1 / (lambda - sigma) (Eq. shift_invert_system_unified,
+// sigma = -delta).  Every application of Op is a batch of PCG solves (one per
+// column of the newest Krylov block, all active spaces together).
+//
+// Basis V is M-orthonormal; Op V_m = V_{m+b} H with H built column by column
+// from classical Gram-Schmidt run twice (CGS2) and a twice-applied Cholesky QR
+// of each new block.  Rayleigh-Ritz on the leading m x m part of H gives Ritz
+// values mu_i; the wanted pairs have the largest mu.  Restarts keep the best
+// Ritz vectors and the coupling row of the last block (Krylov-Schur form).
+//
+// Convergence uses the true FP64 residual of each Ritz vector y (unit M-norm):
+// with the Rayleigh quotient lambda = y^H A y / y^H M y,
+//     || A y - lambda M y ||_2 / ( |lambda| || M y ||_2 ) <= tol.
+//
+// At a Bloch vector where symbol blocks vanish (Gamma, Sec. 6.2, App. C) the
+// zero-derivative modes T_sigma (e_m (x) e_alpha) of those Fourier modes m are
+// M-orthonormalised and projected out of every Krylov vector exactly (the
+// M-orthogonal complement is invariant under Op), so they are never reported.
+//
+// The four block spectra are merged by sorting (Eq. block_gep_impl_unified):
+// the lowest nev of the union are final once every block either lists an
+// eigenvalue at or above the nev-th merged value, or has converged all of its
+// requested pairs below it; otherwise that block's request grows.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "pc_complex.cuh"
+#include "pc_solver.h"
+
+namespace pc {
+
+using cd = std::complex<double>;
+
+// ================================================================== small dense LA (host)
+// Hermitian eigen-decomposition by cyclic Jacobi rotations.  A: n x n column-major
+// (only its Hermitian part is used).  Returns eigenvalues in descending order and
+// the matching orthonormal eigenvectors (columns of V).
+static void herm_eig_desc(int n, std::vector<cd> A, std::vector<double>& w, std::vector<cd>& V) {
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < j; ++i) {
+            cd h = 0.5 * (A[i + j * n] + std::conj(A[j + i * n]));
+            A[i + j * n] = h;
+            A[j + i * n] = std::conj(h);
+        }
+    for (int i = 0; i < n; ++i) A[i + i * n] = cd(A[i + i * n].real(), 0.0);
+    V.assign((size_t)n * n, cd(0, 0));
+    for (int i = 0; i < n; ++i) V[i + i * n] = 1.0;
+    double fro = 0;
+    for (auto& v : A) fro += std::norm(v);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0;
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < j; ++i) off += std::norm(A[i + j * n]);
+        if (off <= 1e-32 * fro || off == 0.0) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const cd apq = A[p + q * n];
+                const double g = std::abs(apq);
+                if (g < 1e-300) continue;
+                const double app = A[p + p * n].real(), aqq = A[q + q * n].real();
+                const cd ph = apq / g;  // e^{i phi}
+                // real symmetric 2x2 [[app, g],[g, aqq]] diagonalised by [[c, s],[-s, c]]
+                const double zeta = (aqq - app) / (2.0 * g);
+                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+                // J = diag(1, e^{-i phi}) [[c, s],[-s, c]]
+                const cd j00 = c, j01 = s, j10 = -s * std::conj(ph), j11 = c * std::conj(ph);
+                for (int k = 0; k < n; ++k) {  // columns: A <- A J
+                    const cd akp = A[k + p * n], akq = A[k + q * n];
+                    A[k + p * n] = akp * j00 + akq * j10;
+                    A[k + q * n] = akp * j01 + akq * j11;
+                }
+                for (int k = 0; k < n; ++k) {  // rows: A <- J^H A
+                    const cd apk = A[p + k * n], aqk = A[q + k * n];
+                    A[p + k * n] = std::conj(j00) * apk + std::conj(j10) * aqk;
+                    A[q + k * n] = std::conj(j01) * apk + std::conj(j11) * aqk;
+                }
+                A[p + q * n] = A[q + p * n] = 0.0;
+                for (int k = 0; k < n; ++k) {  // V <- V J
+                    const cd vkp = V[k + p * n], vkq = V[k + q * n];
+                    V[k + p * n] = vkp * j00 + vkq * j10;
+                    V[k + q * n] = vkp * j01 + vkq * j11;
+                }
+            }
+    }
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return A[a + a * n].real() > A[b + b * n].real(); });
+    w.resize(n);
+    std::vector<cd> Vs((size_t)n * n);
+    for (int j = 0; j < n; ++j) {
+        w[j] = A[idx[j] + idx[j] * n].real();
+        for (int i = 0; i < n; ++i) Vs[i + j * n] = V[i + idx[j] * n];
+    }
+    V.swap(Vs);
+}
+
+// G = R^H R with R upper triangular (column-major n x n).  False if G is not numerically SPD.
+static bool chol_upper(int n, const std::vector<cd>& G, std::vector<cd>& R) {
+    R.assign((size_t)n * n, cd(0, 0));
+    double scale = 0;
+    for (int i = 0; i < n; ++i) scale = std::max(scale, G[i + i * n].real());
+    for (int j = 0; j < n; ++j) {
+        cd s = G[j + j * n];
+        for (int k = 0; k < j; ++k) s -= std::norm(R[k + j * n]);
+        if (!(s.real() > 1e-13 * scale)) return false;
+        const double d = std::sqrt(s.real());
+        R[j + j * n] = d;
+        for (int i = j + 1; i < n; ++i) {
+            cd t = G[j + i * n];
+            for (int k = 0; k < j; ++k) t -= std::conj(R[k + j * n]) * R[k + i * n];
+            R[j + i * n] = t / d;
+        }
+    }
+    return true;
+}
+
+static void upper_inverse(int n, const std::vector<cd>& R, std::vector<cd>& Ri) {
+    Ri.assign((size_t)n * n, cd(0, 0));
+    for (int j = 0; j < n; ++j) {
+        Ri[j + j * n] = 1.0 / R[j + j * n];
+        for (int i = j - 1; i >= 0; --i) {
+            cd s = 0;
+            for (int k = i + 1; k <= j; ++k) s += R[i + k * n] * Ri[k + j * n];
+            Ri[i + j * n] = -s / R[i + i * n];
+        }
+    }
+}
+
+// ================================================================== device kernels
+__device__ __forceinline__ uint64_t splitmix(uint64_t x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// Deterministic pseudo-random start vectors: uniform in [-1, 1) for re and im.
+__global__ void fill_random(double2* v, int64_t n, uint64_t seed) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t a = splitmix(seed ^ (2 * (uint64_t)i)), b = splitmix(seed ^ (2 * (uint64_t)i + 1));
+        v[i] = make_double2((double)(a >> 11) * 0x1.0p-52 - 1.0, (double)(b >> 11) * 0x1.0p-52 - 1.0);
+    }
+}
+
+// Per-candidate residual statistics of y_i and r_i = (A - lambda_i M) y_i:
+// out[5 i + 0..4] partials of sum |r|^2, sum rho^2 |y|^2, Re sum conj(y) r, sum rho |y|^2, Re sum rho conj(y) r.
+__global__ void resid_stats(const double2* __restrict__ Y, const double2* __restrict__ Rv, const void* __restrict__ mat,
+                            int matkind, double rho0, double rho1, int64_t m, double* __restrict__ part, int npart) {
+    const int i = blockIdx.y;
+    const double2* y = Y + (int64_t)i * 3 * m;
+    const double2* r = Rv + (int64_t)i * 3 * m;
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+        const double th = matkind ? (double)(static_cast<const float*>(mat)[t]) : (double)(static_cast<const uint8_t*>(mat)[t]);
+        const double rho = rho0 + th * (rho1 - rho0);
+        for (int a = 0; a < 3; ++a) {
+            const double2 yv = y[a * m + t], rv = r[a * m + t];
+            const double yy = yv.x * yv.x + yv.y * yv.y;
+            const double yr = yv.x * rv.x + yv.y * rv.y;
+            acc[0] += rv.x * rv.x + rv.y * rv.y;
+            acc[1] += rho * rho * yy;
+            acc[2] += yr;
+            acc[3] += rho * yy;
+            acc[4] += rho * yr;
+        }
+    }
+    __shared__ double red[5][32];
+    for (int q = 0; q < 5; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        double s = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        part[((int64_t)i * 5 + threadIdx.x) * npart + blockIdx.x] = s;
+    }
+}
+
+// Per-system squared norms (partials) of n_sys vectors of vs elements.
+template <typename C>
+__global__ void sq_norms(const C* __restrict__ v, int64_t vs, double* __restrict__ part, int npart) {
+    const int s = blockIdx.y;
+    double acc = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
+        const C x = v[s * vs + e];
+        acc += (double)x.x * (double)x.x + (double)x.y * (double)x.y;
+    }
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+        part[(int64_t)s * npart + blockIdx.x] = sum;
+    }
+}
+
+// out32_s = in64_s * scale_s (complex128 -> complex64)
+__global__ void to_c64_scaled(const double2* __restrict__ in, float2* __restrict__ out, const double* __restrict__ scale,
+                              int64_t vs) {
+    const int s = blockIdx.y;
+    const double f = scale[s];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = in[s * vs + e];
+        out[s * vs + e] = make_float2((float)(v.x * f), (float)(v.y * f));
+    }
+}
+
+// x64_s += d32_s * scale_s
+__global__ void axpy_c64_into_c128(const float2* __restrict__ d, double2* __restrict__ x, const double* __restrict__ scale,
+                                   int64_t vs) {
+    const int s = blockIdx.y;
+    const double f = scale[s];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = d[s * vs + e];
+        double2 o = x[s * vs + e];
+        o.x += f * (double)v.x;
+        o.y += f * (double)v.y;
+        x[s * vs + e] = o;
+    }
+}
+
+// res = b - res
+__global__ void sub_from(const double2* __restrict__ b, double2* __restrict__ res, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 bv = b[i], rv = res[i];
+        res[i] = make_double2(bv.x - rv.x, bv.y - rv.y);
+    }
+}
+
+static int ctas_for(int64_t n) {
+    int64_t g = (n + 1023) / 1024;
+    if (g > 304) g = 304;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// ================================================================== solver context
+struct Space {
+    int block = 0;         // 0..3 or -1
+    int64_t m = 0, vs = 0;  // nodes, elements per vector
+    double2* V = nullptr;   // basis [mcap][vs]
+    int m_exp = 0;          // expanded columns
+    std::vector<cd> H;      // (mcap) x (mcap), column-major, ld = mcap
+    std::vector<double> theta;
+    std::vector<cd> S;      // Ritz vectors of the leading block (m_exp x m_exp)
+    int target = 0;
+    int nconv = 0;
+    std::vector<double> lam, res;  // converged eigenvalues (ascending) and residuals
+    bool done = false;
+    double2* Z = nullptr;  // null basis [nz][vs], M-orthonormal
+    int nz = 0;
+};
+
+struct Eigs {
+    pc_grid* g = nullptr;
+    const pc_options* o = nullptr;
+    cudaStream_t s = nullptr;
+    cublasHandle_t blas = nullptr;
+    double sigma = 0;
+    int bs = 4, mmax = 32, mcap = 36;
+    std::vector<Space> sp;
+    double2 *W = nullptr, *MW = nullptr, *T = nullptr, *RHS = nullptr;
+    double2 *Y = nullptr, *AY = nullptr;
+    float* X32 = nullptr;
+    float* R32 = nullptr;
+    double* dpart = nullptr;
+    double* dscale = nullptr;
+    cd* dsmall = nullptr;  // device scratch for small GEMM results
+    int ycap = 0;
+    long long pcg_iters = 0;
+    int max_pcg = 0, solves = 0, expansions = 0;
+    std::vector<void*> allocs;
+    ~Eigs() {
+        for (void* p : allocs) cudaFree(p);
+    }
+    template <typename T>
+    int alloc(T** p, size_t count) {
+        cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(eigensolver)");
+        allocs.push_back(*p);
+        return PC_OK;
+    }
+};
+
+static const cuDoubleComplex kOne = {1.0, 0.0}, kZero = {0.0, 0.0}, kMinusOne = {-1.0, 0.0};
+
+static int blas_ok(cublasStatus_t st, const char* what) {
+    if (st != CUBLAS_STATUS_SUCCESS) return fail(PC_ECUDA, std::string("cuBLAS ") + what + " failed");
+    return PC_OK;
+}
+
+// C (rows x cols) = A^H B with A (vs x rows), B (vs x cols), all column-major with ld vs; result to host.
+static int gemm_hn(Eigs& E, const double2* A, int rows, const double2* B, int cols, int64_t vs, std::vector<cd>& out) {
+    PC_TRY(blas_ok(cublasZgemm(E.blas, CUBLAS_OP_C, CUBLAS_OP_N, rows, cols, (int)vs, &kOne,
+                               (const cuDoubleComplex*)A, (int)vs, (const cuDoubleComplex*)B, (int)vs, &kZero,
+                               (cuDoubleComplex*)E.dsmall, rows),
+                   "zgemm(H)"));
+    out.resize((size_t)rows * cols);
+    PC_CUDA_TRY(cudaMemcpyAsync(out.data(), E.dsmall, sizeof(cd) * rows * cols, cudaMemcpyDeviceToHost, E.s));
+    PC_CUDA_TRY(cudaStreamSynchronize(E.s));
+    return PC_OK;
+}
+
+// Cout (vs x cols) = beta Cout + alpha A (vs x k) * Hs (k x cols, host)
+static int gemm_nn_host(Eigs& E, const double2* A, int k, const std::vector<cd>& Hs, int cols, double2* Cout,
+                        int64_t vs, cuDoubleComplex alpha, cuDoubleComplex beta) {
+    PC_CUDA_TRY(cudaMemcpyAsync(E.dsmall, Hs.data(), sizeof(cd) * k * cols, cudaMemcpyHostToDevice, E.s));
+    PC_TRY(blas_ok(cublasZgemm(E.blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)vs, cols, k, &alpha, (const cuDoubleComplex*)A,
+                               (int)vs, (const cuDoubleComplex*)E.dsmall, k, &beta, (cuDoubleComplex*)Cout, (int)vs),
+                   "zgemm(V h)"));
+    return PC_OK;
+}
+
+static int mass(Eigs& E, const Space& S, const double2* x, double2* y, int nvec) {
+    pc_grid* g = E.g;
+    return launch_mass(PC_C128, x, y, grid_mat(g, S.block), g->matkind, g->rhohat[0], g->rhohat[1], S.m, E.s, nvec);
+}
+
+// W -= Z (Z^H M W)  (exact M-orthogonal projection off the null basis)
+static int project_null(Eigs& E, Space& S, double2* Wv, int cols) {
+    if (S.nz == 0) return PC_OK;
+    PC_TRY(mass(E, S, Wv, E.MW, cols));
+    std::vector<cd> h;
+    PC_TRY(gemm_hn(E, S.Z, S.nz, E.MW, cols, S.vs, h));
+    return gemm_nn_host(E, S.Z, S.nz, h, cols, Wv, S.vs, kMinusOne, kOne);
+}
+
+// M-orthonormalise the cols columns of Wv in place (CholQR2); returns R (cols x cols, upper) with
+// Wv_in = Wv_out R.  Rank-deficient columns are replaced by random vectors orthogonalised against
+// V[:, 0:nv] (their R columns are set to zero).
+static int cholqr2(Eigs& E, Space& S, double2* Wv, int cols, int nv, std::vector<cd>& Rtot, uint64_t seed) {
+    Rtot.assign((size_t)cols * cols, cd(0, 0));
+    for (int i = 0; i < cols; ++i) Rtot[i + i * cols] = 1.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        PC_TRY(mass(E, S, Wv, E.MW, cols));
+        std::vector<cd> G, R, Ri;
+        PC_TRY(gemm_hn(E, Wv, cols, E.MW, cols, S.vs, G));
+        if (!chol_upper(cols, G, R)) {
+            if (pass == 1) return fail(PC_ENOCONV, "eigensolver: Krylov block lost rank twice");
+            // replace the block by fresh random directions (breakdown of the Krylov space)
+            fill_random<<<ctas_for(cols * S.vs), 256, 0, E.s>>>(Wv, cols * S.vs, seed);
+            PC_TRY(project_null(E, S, Wv, cols));
+            for (int rep = 0; rep < 2; ++rep) {
+                PC_TRY(mass(E, S, Wv, E.MW, cols));
+                std::vector<cd> h;
+                PC_TRY(gemm_hn(E, S.V, nv, E.MW, cols, S.vs, h));
+                PC_TRY(gemm_nn_host(E, S.V, nv, h, cols, Wv, S.vs, kMinusOne, kOne));
+            }
+            Rtot.assign((size_t)cols * cols, cd(0, 0));
+            pass = -1;  // restart both passes on the new block; R of a replaced block is zero
+            continue;
+        }
+        upper_inverse(cols, R, Ri);
+        // Wv <- Wv R^-1  (through T)
+        PC_TRY(gemm_nn_host(E, Wv, cols, Ri, cols, E.T, S.vs, kOne, kZero));
+        PC_CUDA_TRY(cudaMemcpyAsync(Wv, E.T, sizeof(double2) * cols * S.vs, cudaMemcpyDeviceToDevice, E.s));
+        // Rtot <- R Rtot
+        std::vector<cd> Rn((size_t)cols * cols, cd(0, 0));
+        for (int j = 0; j < cols; ++j)
+            for (int i = 0; i < cols; ++i) {
+                cd acc = 0;
+                for (int k = 0; k < cols; ++k) acc += R[i + k * cols] * Rtot[k + j * cols];
+                Rn[i + j * cols] = acc;
+            }
+        Rtot.swap(Rn);
+    }
+    return PC_OK;
+}
+
+// W (stacked [nsys][vs]) = Op applied to the right-hand sides RHS = M V (stacked), i.e. solves of
+// (A - sigma M) W = RHS, FP64 PCG or complex64 PCG with FP64 residual refinement.
+static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t vs) {
+    pc_grid* g = E.g;
+    const pc_options& o = *E.o;
+    std::vector<PcgResult> res(nsys);
+    if (o.precision == PC_PREC_FP64) {
+        PC_TRY(pcg_solve(g, PC_C128, nsys, blocks.data(), E.sigma, E.RHS, E.W, o.inner_tol, o.inner_maxit, res.data(),
+                         E.s));
+        for (auto& r : res) {
+            E.pcg_iters += r.iters;
+            E.max_pcg = std::max(E.max_pcg, r.iters);
+            if (r.status == PC_EBREAKDOWN)
+                return fail(PC_EBREAKDOWN, "PCG breakdown: sigma is not below the spectrum");
+            if (r.status == PC_ENAN) return fail(PC_ENAN, "PCG met NaN");
+        }
+        E.solves += nsys;
+        return PC_OK;
+    }
+    // mixed precision: x = 0, res = rhs; repeat { d = PCG32(res/|res|); x += |res| d; res = rhs - (A - sigma M) x }
+    const int nc = ctas_for(vs);
+    const dim3 vg(nc, nsys);
+    PC_CUDA_TRY(cudaMemsetAsync(E.W, 0, sizeof(double2) * nsys * vs, E.s));
+    PC_CUDA_TRY(cudaMemcpyAsync(E.MW, E.RHS, sizeof(double2) * nsys * vs, cudaMemcpyDeviceToDevice, E.s));
+    std::vector<double> bnorm(nsys), rnorm(nsys), part((size_t)nsys * nc);
+    const double tol32 = 1e-4;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        sq_norms<double2><<<vg, 256, 0, E.s>>>(E.MW, vs, E.dpart, nc);
+        PC_CUDA_TRY(cudaMemcpyAsync(part.data(), E.dpart, sizeof(double) * nsys * nc, cudaMemcpyDeviceToHost, E.s));
+        PC_CUDA_TRY(cudaStreamSynchronize(E.s));
+        bool all = true;
+        std::vector<double> sc(nsys);
+        for (int i = 0; i < nsys; ++i) {
+            double a = 0;
+            for (int c = 0; c < nc; ++c) a += part[(size_t)i * nc + c];
+            rnorm[i] = std::sqrt(a);
+            if (sweep == 0) bnorm[i] = rnorm[i];
+            if (rnorm[i] > o.inner_tol * bnorm[i]) all = false;
+            sc[i] = rnorm[i] > 0 ? 1.0 / rnorm[i] : 0.0;
+        }
+        if (all) break;
+        if (!std::isfinite(rnorm[0])) return fail(PC_ENAN, "refinement met NaN");
+        PC_CUDA_TRY(cudaMemcpyAsync(E.dscale, sc.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, E.s));
+        to_c64_scaled<<<vg, 256, 0, E.s>>>(E.MW, (float2*)E.R32, E.dscale, vs);
+        PC_TRY(pcg_solve(g, PC_C64, nsys, blocks.data(), E.sigma, E.R32, E.X32, tol32, o.inner_maxit, res.data(), E.s));
+        for (auto& r : res) {
+            E.pcg_iters += r.iters;
+            E.max_pcg = std::max(E.max_pcg, r.iters);
+            if (r.status == PC_EBREAKDOWN) return fail(PC_EBREAKDOWN, "PCG breakdown: sigma is not below the spectrum");
+        }
+        for (int i = 0; i < nsys; ++i) sc[i] = rnorm[i];
+        PC_CUDA_TRY(cudaMemcpyAsync(E.dscale, sc.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, E.s));
+        axpy_c64_into_c128<<<vg, 256, 0, E.s>>>((const float2*)E.X32, E.W, E.dscale, vs);
+        // residual in FP64: MW = RHS - (A - sigma M) W
+        std::vector<ApplyItem> items(nsys);
+        for (int i = 0; i < nsys; ++i) {
+            items[i].x = E.W + i * vs;
+            items[i].y = E.MW + i * vs;
+            items[i].mat = grid_mat(g, blocks[i]);
+            items[i].shift = E.sigma;
+            items[i].block = blocks[i];
+            items[i].dot_slot = -1;
+            items[i].skip = nullptr;
+        }
+        PC_TRY(grid_apply(g, PC_C128, blocks[0] < 0, items.data(), nsys, nullptr, 0, E.s, nullptr));
+        sub_from<<<ctas_for(nsys * vs), 256, 0, E.s>>>(E.RHS, E.MW, nsys * vs);
+        PC_CUDA_TRY(cudaGetLastError());
+    }
+    E.solves += nsys;
+    return PC_OK;
+}
+
+// Rayleigh-Ritz on the leading m_exp x m_exp block of H (descending mu).
+static void ritz(Eigs& E, Space& S) {
+    const int m = S.m_exp;
+    std::vector<cd> Hm((size_t)m * m);
+    for (int j = 0; j < m; ++j)
+        for (int i = 0; i < m; ++i) Hm[i + j * m] = S.H[i + j * E.mcap];
+    herm_eig_desc(m, Hm, S.theta, S.S);
+}
+
+// True residuals of the leading ncand Ritz pairs; returns their Rayleigh quotients and residuals.
+static int check_pairs(Eigs& E, Space& S, int ncand, std::vector<double>& lam, std::vector<double>& rel) {
+    pc_grid* g = E.g;
+    const int m = S.m_exp;
+    std::vector<cd> Sk((size_t)m * ncand);
+    for (int j = 0; j < ncand; ++j)
+        for (int i = 0; i < m; ++i) Sk[i + j * m] = S.S[i + j * m];
+    PC_TRY(gemm_nn_host(E, S.V, m, Sk, ncand, E.Y, S.vs, kOne, kZero));
+    std::vector<ApplyItem> items(ncand);
+    std::vector<double> lr(ncand);
+    for (int i = 0; i < ncand; ++i) {
+        lr[i] = E.sigma + 1.0 / S.theta[i];
+        items[i].x = E.Y + i * S.vs;
+        items[i].y = E.AY + i * S.vs;
+        items[i].mat = grid_mat(g, S.block);
+        items[i].shift = lr[i];
+        items[i].block = S.block;
+        items[i].dot_slot = -1;
+        items[i].skip = nullptr;
+    }
+    PC_TRY(grid_apply(g, PC_C128, S.block < 0, items.data(), ncand, nullptr, 0, E.s, nullptr));
+    const int nc = ctas_for(S.m);
+    resid_stats<<<dim3(nc, ncand), 256, 0, E.s>>>(E.Y, E.AY, grid_mat(g, S.block), g->matkind, g->rhohat[0],
+                                                   g->rhohat[1], S.m, E.dpart, nc);
+    PC_CUDA_TRY(cudaGetLastError());
+    std::vector<double> part((size_t)ncand * 5 * nc);
+    PC_CUDA_TRY(cudaMemcpyAsync(part.data(), E.dpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, E.s));
+    PC_CUDA_TRY(cudaStreamSynchronize(E.s));
+    lam.resize(ncand);
+    rel.resize(ncand);
+    for (int i = 0; i < ncand; ++i) {
+        double q[5];
+        for (int k = 0; k < 5; ++k) {
+            double a = 0;
+            for (int c = 0; c < nc; ++c) a += part[((size_t)i * 5 + k) * nc + c];
+            q[k] = a;
+        }
+        const double d = q[2] / q[3];  // Rayleigh-quotient correction of lambda
+        lam[i] = lr[i] + d;
+        const double r2 = std::max(0.0, q[0] - 2.0 * d * q[4] + d * d * q[1]);
+        rel[i] = std::sqrt(r2) / (std::fabs(lam[i]) * std::sqrt(q[1]));
+    }
+    return PC_OK;
+}
+
+// Krylov-Schur restart keeping the best `keep` Ritz vectors.
+static int restart(Eigs& E, Space& S, int keep) {
+    const int m = S.m_exp, bs = E.bs, ld = E.mcap;
+    std::vector<cd> Sk((size_t)m * keep);
+    for (int j = 0; j < keep; ++j)
+        for (int i = 0; i < m; ++i) Sk[i + j * m] = S.S[i + j * m];
+    PC_TRY(gemm_nn_host(E, S.V, m, Sk, keep, E.T, S.vs, kOne, kZero));
+    PC_CUDA_TRY(cudaMemcpyAsync(S.V, E.T, sizeof(double2) * keep * S.vs, cudaMemcpyDeviceToDevice, E.s));
+    PC_CUDA_TRY(cudaMemcpyAsync(S.V + (int64_t)keep * S.vs, S.V + (int64_t)m * S.vs, sizeof(double2) * bs * S.vs,
+                                cudaMemcpyDeviceToDevice, E.s));
+    std::vector<cd> Hn((size_t)ld * ld, cd(0, 0));
+    for (int i = 0; i < keep; ++i) Hn[i + i * ld] = S.theta[i];
+    for (int r = 0; r < bs; ++r)
+        for (int j = 0; j < keep; ++j) {
+            cd acc = 0;
+            for (int k = 0; k < m; ++k) acc += S.H[(m + r) + k * ld] * S.S[k + j * m];
+            Hn[(keep + r) + j * ld] = acc;
+        }
+    S.H.swap(Hn);
+    S.m_exp = keep;
+    return PC_OK;
+}
+
+// One expansion of every active space: solves, projection, CGS2, CholQR2, Rayleigh-Ritz,
+// convergence tests and restarts.
+static int expand(Eigs& E, std::vector<int>& active, double tol) {
+    const int bs = E.bs, ld = E.mcap;
+    const int64_t vs = E.sp[active[0]].vs;
+    const int nsys = bs * (int)active.size();
+    std::vector<int> blocks;
+    for (size_t a = 0; a < active.size(); ++a) {
+        Space& S = E.sp[active[a]];
+        PC_TRY(mass(E, S, S.V + (int64_t)S.m_exp * vs, E.RHS + (int64_t)a * bs * vs, bs));
+        for (int j = 0; j < bs; ++j) blocks.push_back(S.block);
+    }
+    PC_TRY(apply_op(E, nsys, blocks, vs));
+    E.expansions += (int)active.size();
+    for (size_t a = 0; a < active.size(); ++a) {
+        Space& S = E.sp[active[a]];
+        double2* Wv = E.W + (int64_t)a * bs * vs;
+        PC_TRY(project_null(E, S, Wv, bs));
+        const int nv = S.m_exp + bs;  // columns of V present
+        std::vector<cd> h(nv * bs, cd(0, 0));
+        for (int rep = 0; rep < 2; ++rep) {
+            PC_TRY(mass(E, S, Wv, E.MW, bs));
+            std::vector<cd> hh;
+            PC_TRY(gemm_hn(E, S.V, nv, E.MW, bs, vs, hh));
+            PC_TRY(gemm_nn_host(E, S.V, nv, hh, bs, Wv, vs, kMinusOne, kOne));
+            for (size_t i = 0; i < h.size(); ++i) h[i] += hh[i];
+        }
+        std::vector<cd> R;
+        PC_TRY(cholqr2(E, S, Wv, bs, nv, R, 0xC0FFEEull + 7919ull * (uint64_t)E.expansions + (uint64_t)a));
+        const int c0 = S.m_exp;
+        for (int j = 0; j < bs; ++j) {
+            for (int i = 0; i < nv; ++i) S.H[i + (c0 + j) * ld] = h[i + j * nv];
+            for (int i = 0; i < bs; ++i) S.H[(nv + i) + (c0 + j) * ld] = R[i + j * bs];
+        }
+        PC_CUDA_TRY(cudaMemcpyAsync(S.V + (int64_t)nv * vs, Wv, sizeof(double2) * bs * vs, cudaMemcpyDeviceToDevice,
+                                    E.s));
+        S.m_exp += bs;
+        ritz(E, S);
+        // residual estimates of the Ritz pairs: || H[m:m+bs, 0:m] s_i ||
+        const int m = S.m_exp;
+        int ncand = std::min(m, S.target + 1);
+        std::vector<double> est(ncand);
+        for (int i = 0; i < ncand; ++i) {
+            double acc = 0;
+            for (int r = 0; r < bs; ++r) {
+                cd v = 0;
+                for (int k = 0; k < m; ++k) v += S.H[(m + r) + k * ld] * S.S[k + i * m];
+                acc += std::norm(v);
+            }
+            est[i] = std::sqrt(acc) / std::fabs(S.theta[i]);
+        }
+        int ntest = 0;
+        while (ntest < ncand && est[ntest] < 1e-3) ++ntest;
+        if (ntest >= std::min(S.target, m) && ntest > 0) {
+            std::vector<double> lam, rel;
+            PC_TRY(check_pairs(E, S, ntest, lam, rel));
+            int nc = 0;
+            while (nc < ntest && rel[nc] <= tol) ++nc;
+            S.nconv = nc;
+            if (nc >= S.target) {
+                S.lam.assign(lam.begin(), lam.begin() + nc);
+                S.res.assign(rel.begin(), rel.begin() + nc);
+                S.done = true;
+            }
+        }
+        if (!S.done && S.m_exp + bs > E.mmax) {
+            int keep = std::max(S.target + bs, E.mmax / 2);
+            keep = std::min(keep, S.m_exp - bs);
+            PC_TRY(restart(E, S, keep));
+        }
+    }
+    return PC_OK;
+}
+
+// Null basis of a space from the vanishing symbol blocks: T_sigma (e_m (x) e_alpha), M-orthonormalised.
+static int build_null(Eigs& E, Space& S) {
+    pc_grid* g = E.g;
+    Precond* P = g->pre;
+    S.nz = 0;
+    if (!P || P->null_modes.empty()) return PC_OK;
+    const int nm = (int)P->null_modes.size();
+    const int blocks_needed = S.block < 0 ? 4 : 1;
+    S.nz = 3 * nm * blocks_needed;
+    PC_TRY(E.alloc(&S.Z, (size_t)S.nz * S.vs));
+    PC_CUDA_TRY(cudaMemsetAsync(S.Z, 0, sizeof(double2) * S.nz * S.vs, E.s));
+    const int64_t nb = g->nb;
+    double2* delta = E.T;  // [3 nb] mode-space vector, then block vector in E.T + 3 nb
+    int col = 0;
+    for (int bi = 0; bi < blocks_needed; ++bi) {
+        const int b = S.block < 0 ? bi : S.block;
+        for (int mi = 0; mi < nm; ++mi)
+            for (int a = 0; a < 3; ++a, ++col) {
+                PC_CUDA_TRY(cudaMemsetAsync(delta, 0, sizeof(double2) * 3 * nb, E.s));
+                const double2 one = make_double2(1.0, 0.0);
+                PC_CUDA_TRY(cudaMemcpyAsync(delta + a * nb + P->null_modes[mi], &one, sizeof(double2),
+                                            cudaMemcpyHostToDevice, E.s));
+                PC_CUDA_TRY(cudaStreamSynchronize(E.s));
+                double2* dst = S.Z + (int64_t)col * S.vs;
+                if (S.block < 0) {
+                    PC_TRY(block_fourier(g, b, PC_C128, 1, delta, E.T + 3 * nb, E.s));
+                    PC_TRY(launch_transfer(PC_C128, E.T + 3 * nb, dst, g->N, b, 1, E.s));
+                } else {
+                    PC_TRY(block_fourier(g, b, PC_C128, 1, delta, dst, E.s));
+                }
+            }
+    }
+    // M-orthonormalise the null columns
+    PC_TRY(mass(E, S, S.Z, E.Y, S.nz));
+    std::vector<cd> G, R, Ri;
+    PC_TRY(gemm_hn(E, S.Z, S.nz, E.Y, S.nz, S.vs, G));
+    if (!chol_upper(S.nz, G, R)) return fail(PC_ECUDA, "null basis is rank deficient");
+    upper_inverse(S.nz, R, Ri);
+    PC_TRY(gemm_nn_host(E, S.Z, S.nz, Ri, S.nz, E.AY, S.vs, kOne, kZero));
+    PC_CUDA_TRY(cudaMemcpyAsync(S.Z, E.AY, sizeof(double2) * S.nz * S.vs, cudaMemcpyDeviceToDevice, E.s));
+    return PC_OK;
+}
+
+static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_options* opt, double* evals,
+                    void* evecs, int* block_of, pc_eigs_info* info) {
+    auto t0 = std::chrono::steady_clock::now();
+    PC_TRY(pc_set_k(g, kappa));
+    if (!g->sol) g->sol = new Solver();
+    Solver* SV = g->sol;
+    Eigs E;
+    E.g = g;
+    E.o = opt;
+    E.sigma = std::isnan(sigma) ? pc_default_sigma(g) : sigma;
+    E.bs = std::max(1, std::min(opt->block_size, 16));
+    E.mmax = std::max(opt->max_basis, 3 * E.bs);
+    E.mcap = E.mmax + 2 * E.bs;
+    PC_CUDA_TRY(cudaStreamCreateWithFlags(&E.s, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamDestroy(s); }
+    } sg{E.s};
+    if (!SV->blas) {
+        if (cublasCreate(&SV->blas) != CUBLAS_STATUS_SUCCESS) return fail(PC_ECUDA, "cublasCreate failed");
+    }
+    E.blas = SV->blas;
+    cublasSetStream(E.blas, E.s);
+    cublasSetPointerMode(E.blas, CUBLAS_POINTER_MODE_HOST);
+
+    const bool full = opt->full_space != 0;
+    const int nspace = full ? 1 : 4;
+    const int64_t m = full ? g->n : g->nb, vs = 3 * m;
+    E.sp.resize(nspace);
+    const int share = full ? nev : (nev + 3) / 4;
+    const int guard = std::max(0, opt->guard);
+    const int ymax = std::max(E.mmax, share + guard + 16);
+    PC_TRY(E.alloc(&E.W, (size_t)E.bs * nspace * vs));
+    PC_TRY(E.alloc(&E.RHS, (size_t)E.bs * nspace * vs));
+    PC_TRY(E.alloc(&E.MW, (size_t)std::max(E.bs * nspace, ymax) * vs));
+    PC_TRY(E.alloc(&E.T, (size_t)std::max<int64_t>(E.mcap, 8) * vs));
+    PC_TRY(E.alloc(&E.Y, (size_t)ymax * vs));
+    PC_TRY(E.alloc(&E.AY, (size_t)ymax * vs));
+    PC_TRY(E.alloc(&E.dpart, (size_t)std::max(ymax * 5, E.bs * nspace) * 304));
+    PC_TRY(E.alloc(&E.dscale, (size_t)E.bs * nspace));
+    PC_TRY(E.alloc(&E.dsmall, (size_t)E.mcap * std::max(E.mcap, ymax)));
+    if (opt->precision == PC_PREC_MIXED) {
+        PC_TRY(E.alloc(&E.X32, (size_t)2 * E.bs * nspace * vs));
+        PC_TRY(E.alloc(&E.R32, (size_t)2 * E.bs * nspace * vs));
+    }
+    int zero_modes = 0;
+    for (int i = 0; i < nspace; ++i) {
+        Space& S = E.sp[i];
+        S.block = full ? -1 : i;
+        S.m = m;
+        S.vs = vs;
+        S.target = share + (full ? guard : 1);
+        PC_TRY(E.alloc(&S.V, (size_t)E.mcap * vs));
+        S.H.assign((size_t)E.mcap * E.mcap, cd(0, 0));
+        PC_TRY(build_null(E, S));
+        zero_modes += S.nz;
+        fill_random<<<ctas_for(E.bs * vs), 256, 0, E.s>>>(S.V, E.bs * vs, 0x5EED0000ull + (uint64_t)(i + 1) * 1000003ull);
+        PC_CUDA_TRY(cudaGetLastError());
+        PC_TRY(project_null(E, S, S.V, E.bs));
+        std::vector<cd> R;
+        PC_TRY(cholqr2(E, S, S.V, E.bs, 0, R, 0xABCDEFull + i));
+        S.m_exp = 0;
+    }
+    const int max_exp = std::max(1, opt->max_restarts) * std::max(1, (E.mmax / E.bs));
+    int status = PC_OK;
+    std::vector<double> merged;
+    std::vector<int> mblock;
+    for (int outer = 0;; ++outer) {
+        std::vector<int> active;
+        for (int i = 0; i < nspace; ++i)
+            if (!E.sp[i].done) active.push_back(i);
+        if (active.empty()) {
+            // merge and check completeness
+            std::vector<std::pair<double, int>> all;
+            for (int i = 0; i < nspace; ++i)
+                for (double l : E.sp[i].lam) all.push_back({l, E.sp[i].block});
+            std::sort(all.begin(), all.end());
+            bool ok = (int)all.size() >= nev;
+            if (ok && !full) {
+                const double cut = all[nev - 1].first;
+                for (int i = 0; i < nspace; ++i) {
+                    Space& S = E.sp[i];
+                    if (S.lam.empty() || S.lam.back() < cut) {  // may hide more eigenvalues below the cut
+                        S.target += 2;
+                        S.done = false;
+                        ok = false;
+                    }
+                }
+            } else if (!ok) {
+                for (int i = 0; i < nspace; ++i) {
+                    E.sp[i].target += 2;
+                    E.sp[i].done = false;
+                }
+            }
+            if (ok) {
+                merged.clear();
+                mblock.clear();
+                for (int i = 0; i < nev; ++i) {
+                    merged.push_back(all[i].first);
+                    mblock.push_back(all[i].second);
+                }
+                break;
+            }
+            continue;
+        }
+        if (E.expansions >= max_exp * nspace) {
+            status = PC_ENOCONV;
+            break;
+        }
+        PC_TRY(expand(E, active, opt->tol));
+        if (opt->verbose) {
+            for (int i : active)
+                std::fprintf(stderr, "[pc_eigs] space %d m=%d target=%d nconv=%d done=%d\n", E.sp[i].block,
+                             E.sp[i].m_exp, E.sp[i].target, E.sp[i].nconv, (int)E.sp[i].done);
+        }
+    }
+    double maxres = 0;
+    const double to_si = g->C0 / (g->rho0 * g->L * g->L);
+    if (status == PC_OK) {
+        for (int i = 0; i < nev; ++i) {
+            evals[i] = merged[i] * to_si;
+            if (block_of) block_of[i] = mblock[i];
+        }
+        for (auto& S : E.sp)
+            for (size_t i = 0; i < S.res.size(); ++i)
+                if (std::find(merged.begin(), merged.end(), S.lam[i]) != merged.end()) maxres = std::max(maxres, S.res[i]);
+    } else {
+        // best effort: whatever converged, then NaN
+        std::vector<std::pair<double, int>> all;
+        for (auto& S : E.sp)
+            for (double l : S.lam) all.push_back({l, S.block});
+        std::sort(all.begin(), all.end());
+        for (int i = 0; i < nev; ++i) {
+            evals[i] = i < (int)all.size() ? all[i].first * to_si : NAN;
+            if (block_of) block_of[i] = i < (int)all.size() ? all[i].second : -2;
+        }
+    }
+    if (evecs && status == PC_OK) {
+        // recompute Ritz vectors for the merged values and write them in full-space layout
+        double2* out = static_cast<double2*>(evecs);
+        PC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double2) * (size_t)nev * 3 * g->n, E.s));
+        for (int i = 0; i < nspace; ++i) {
+            Space& S = E.sp[i];
+            ritz(E, S);
+            const int ncand = (int)S.lam.size();
+            if (ncand == 0) continue;
+            const int mm = S.m_exp;
+            std::vector<cd> Sk((size_t)mm * ncand);
+            for (int j = 0; j < ncand; ++j)
+                for (int r = 0; r < mm; ++r) Sk[r + j * mm] = S.S[r + j * mm];
+            PC_TRY(gemm_nn_host(E, S.V, mm, Sk, ncand, E.Y, S.vs, kOne, kZero));
+            for (int j = 0; j < ncand; ++j) {
+                int slot = -1;
+                for (int q = 0; q < nev; ++q)
+                    if (mblock[q] == S.block && merged[q] == S.lam[j]) slot = q;
+                if (slot < 0) continue;
+                double2* dst = out + (size_t)slot * 3 * g->n;
+                if (S.block < 0)
+                    PC_CUDA_TRY(cudaMemcpyAsync(dst, E.Y + (int64_t)j * S.vs, sizeof(double2) * S.vs,
+                                                cudaMemcpyDeviceToDevice, E.s));
+                else
+                    PC_TRY(launch_transfer(PC_C128, E.Y + (int64_t)j * S.vs, dst, g->N, S.block, 1, E.s));
+            }
+        }
+        PC_CUDA_TRY(cudaStreamSynchronize(E.s));
+    }
+    PC_CUDA_TRY(cudaStreamSynchronize(E.s));
+    if (info) {
+        info->status = status;
+        info->outer_iters = E.expansions;
+        info->inner_solves = E.solves;
+        info->pcg_iters = E.pcg_iters;
+        info->max_pcg_iters = E.max_pcg;
+        info->zero_modes = zero_modes;
+        info->max_rel_resid = maxres;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (status != PC_OK) return fail(status, "pc_eigs: outer iteration cap reached");
+    return PC_OK;
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+namespace pc {
+void release_solver_state(pc_grid* g) {
+    delete g->sol;
+    g->sol = nullptr;
+    delete g->pre;
+    g->pre = nullptr;
+}
+}  // namespace pc
+
+extern "C" {
+
+int pc_options_default(pc_options* o) {
+    if (!o) return fail(PC_EINVAL, "pc_options_default: null");
+    o->tol = 1e-8;
+    o->inner_tol = 1e-10;
+    o->precision = PC_PREC_FP64;
+    o->full_space = 0;
+    o->block_size = 4;
+    o->max_basis = 32;
+    o->max_restarts = 60;
+    o->inner_maxit = 400;
+    o->guard = 3;
+    o->verbose = 0;
+    return PC_OK;
+}
+
+double pc_default_sigma(const pc_grid* g) {
+    if (!g) return NAN;
+    double cmax = 0, rmax = 0;
+    for (int p = 0; p < 2; ++p) {
+        for (int e = 0; e < 36; ++e) cmax = std::fmax(cmax, std::fabs(g->Chat[p][e]));
+        rmax = std::fmax(rmax, g->rhohat[p]);
+    }
+    return -0.30 * cmax / rmax;
+}
+
+int pc_block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* w, void* what, void* stream) {
+    if (!g || !w || !what) return fail(PC_EINVAL, "pc_block_fourier: null argument");
+    if (block < 0 || block > 3) return fail(PC_EINVAL, "pc_block_fourier: block must be 0..3");
+    if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_block_fourier: bad dtype");
+    if (!g->k.set) return fail(PC_ESTATE, "pc_block_fourier: call pc_set_k first");
+    return block_fourier(g, block, dtype, inverse ? 1 : 0, w, what, (cudaStream_t)stream);
+}
+
+int pc_shift_invert_pcg(pc_grid* g, int block, int dtype, double sigma, const void* rhs, void* x, double tol, int maxit,
+                        pc_pcg_info* info, void* stream) {
+    if (!g || !rhs || !x) return fail(PC_EINVAL, "pc_shift_invert_pcg: null argument");
+    if (block < -1 || block > 3) return fail(PC_EINVAL, "pc_shift_invert_pcg: block must be -1..3");
+    if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_shift_invert_pcg: bad dtype");
+    if (!std::isfinite(sigma)) return fail(PC_EINVAL, "pc_shift_invert_pcg: non-finite sigma");
+    if (!g->k.set) return fail(PC_ESTATE, "pc_shift_invert_pcg: call pc_set_k first");
+    PcgResult r;
+    int rc = pcg_solve(g, dtype, 1, &block, sigma, rhs, x, tol, maxit, &r, (cudaStream_t)stream);
+    if (rc != PC_OK) return rc;
+    if (info) {
+        info->iters = r.iters;
+        info->status = r.status;
+        info->rel_resid = r.rel_resid;
+    }
+    if (r.status == PC_ENOCONV) return fail(PC_ENOCONV, "pc_shift_invert_pcg: iteration cap reached");
+    if (r.status == PC_EBREAKDOWN) return fail(PC_EBREAKDOWN, "pc_shift_invert_pcg: p^H (A - sigma M) p <= 0");
+    if (r.status == PC_ENAN) return fail(PC_ENAN, "pc_shift_invert_pcg: NaN in a reduction");
+    return PC_OK;
+}
+
+int pc_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_options* opt, double* evals,
+            void* evecs, int* block_of, pc_eigs_info* info) {
+    if (!g || !kappa || !evals) return fail(PC_EINVAL, "pc_eigs: null argument");
+    if (nev < 1) return fail(PC_EINVAL, "pc_eigs: nev must be >= 1");
+    pc_options def;
+    pc_options_default(&def);
+    const pc_options* o = opt ? opt : &def;
+    if (!(o->tol > 0) || !(o->inner_tol > 0)) return fail(PC_EINVAL, "pc_eigs: tolerances must be positive");
+    if (o->precision != PC_PREC_FP64 && o->precision != PC_PREC_MIXED)
+        return fail(PC_EINVAL, "pc_eigs: precision must be PC_PREC_FP64 or PC_PREC_MIXED");
+    if (!std::isnan(sigma) && !std::isfinite(sigma)) return fail(PC_EINVAL, "pc_eigs: bad sigma");
+    const int64_t dim = o->full_space ? 3 * g->n : 3 * g->nb;
+    if (nev > dim / 8) return fail(PC_EINVAL, "pc_eigs: nev too large for this grid");
+    return run_eigs(g, kappa, nev, sigma, o, evals, evecs, block_of, info);
+}
+
+}  // extern "C"

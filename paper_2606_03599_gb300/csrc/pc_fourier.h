@@ -1,0 +1,57 @@
+// Block Fourier transform, reference-medium preconditioner and symbol tables.
+#pragma once
+
+#include <cufft.h>
+
+#include <vector>
+
+#include "pc_internal.h"
+
+namespace pc {
+
+struct SymbolParams {
+    int X, Y, Z;
+    double q;         // 1 / (4 h_s) = N / 4
+    double Ainv[9];   // (A_hat^-1)_{s m}
+    double Cref[36];  // reference stiffness (hat units)
+    double null_tol;  // |eta| below this marks a zero-derivative mode
+};
+
+struct FftPlan {
+    int dtype;
+    int nsys;
+    cufftHandle h;
+};
+
+}  // namespace pc
+
+struct Precond {
+    ~Precond();
+    int tab_len = 0;
+    double2* d_tabs = nullptr;  // phase tables (device)
+    const double2 *ea = nullptr, *eb = nullptr, *egh = nullptr, *egf = nullptr;
+    const double2 *twa = nullptr, *twb = nullptr, *twk = nullptr;
+    double* d_Aref = nullptr;  // 9 reals per mode (Hermitian 3x3 reference symbol)
+    float* d_Aref32 = nullptr; // the same table rounded to FP32 (complex64 preconditioning)
+    int* d_null = nullptr;     // [0] = count, [1..64] = modes with a vanishing symbol
+    std::vector<int> null_modes;
+    double rho_ref = 1.0;
+    double Cref[36];
+    std::vector<pc::FftPlan> plans;
+    void* d_work = nullptr;
+    size_t work_bytes = 0;
+};
+
+namespace pc {
+int precond_create(pc_grid* g);
+int precond_workspace(pc_grid* g, int dtype, int nsys, void** W);
+// z_s = P r_s for nsys contiguous systems (stride 3 n_b); d_sys_block[s] = block of system s;
+// d_skip: optional per-system skip flags (nonzero = leave z_s untouched).
+// With d_part non-null, also writes per-CTA partial sums of Re<r_s, z_s> at d_part[s * npart + cta]
+// (npart returned in *npart_out, equal to unpack_ctas(3 n_b)).
+int precond_apply(pc_grid* g, int dtype, int nsys, const void* r, void* z, const int* d_sys_block,
+                  const int* d_skip, double sigma, cudaStream_t s, double* d_part = nullptr,
+                  int* npart_out = nullptr);
+int unpack_ctas(int64_t vs);
+int block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* in, void* out, cudaStream_t s);
+}  // namespace pc

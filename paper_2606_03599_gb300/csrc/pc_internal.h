@@ -52,6 +52,7 @@ struct ApplyItem {
     double shift;     // y = (A - shift M) x
     int block;        // 0..3 or -1 (full)
     int dot_slot;     // >= 0: write <x, y> partials to dot scratch slot, else -1
+    const int* skip;  // optional device flag: nonzero = skip this item (converged system)
 };
 
 // ---------------------------------------------------------------- kernels (launch wrappers)
@@ -118,6 +119,7 @@ struct pc_grid {
     double Ainv[9];  // (A_hat^-1)_{s m}, row-major s*3+m
     bool cubic = true;
     int matkind = 0;  // 0 = uint8 phase ids, 1 = float theta
+    double mean_theta = 0.0;  // volume fraction of phase 1
     void* d_mat_full = nullptr;
     void* d_mat_blk[4] = {nullptr, nullptr, nullptr, nullptr};
     pc::GridK k;

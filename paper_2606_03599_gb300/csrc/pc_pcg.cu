@@ -1,0 +1,397 @@
+// Batched preconditioned conjugate gradients for the shift-invert systems
+// (A - sigma M) x = b of Sec. 6.1 (Eq. shift_invert_system_unified, with
+// sigma = -delta), device-resident: every scalar of every system lives on the
+// GPU, reductions are deterministic (fixed-order sums of per-CTA partials), and
+// the host only polls the per-system done flags every few iterations.
+//
+// One iteration: q = (A - sigma M) p with fused partials of Re<p, q> (stencil
+// kernel) -> alpha -> x += alpha p, r -= alpha q with partials of ||r||^2 ->
+// z = P r (block Fourier preconditioner) with partials of Re<r, z> -> beta and
+// the convergence test ||r|| <= tol ||b|| -> p = z + beta p.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pc_complex.cuh"
+#include "pc_solver.h"
+
+namespace pc {
+
+__device__ __forceinline__ double block_sum_pcg(double v) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// Fixed-order sum of n partials by one CTA (result in thread 0).
+__device__ __forceinline__ double reduce_partials(const double* p, int n) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += p[i];
+    return block_sum_pcg(v);
+}
+
+template <typename C>
+__global__ void pcg_start(const C* __restrict__ b, C* __restrict__ x, C* __restrict__ r, int64_t vs,
+                          double* __restrict__ part, int npart) {
+    const int s = blockIdx.y;
+    double acc = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
+        C v = b[s * vs + e];
+        r[s * vs + e] = v;
+        x[s * vs + e] = make_c<C>(0, 0);
+        acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    }
+    acc = block_sum_pcg(acc);
+    if (threadIdx.x == 0) part[(int64_t)s * npart + blockIdx.x] = acc;
+}
+
+// bb = sum part_bb, rz = sum part_rz; init flags.
+__global__ void pcg_start_reduce(PcgScal* sc, int* done, const double* part_bb, int sbb, int nbb,
+                                 const double* part_rz, int nrz) {
+    const int s = blockIdx.x;
+    double bb = reduce_partials(part_bb + (int64_t)s * sbb, nbb);
+    double rz = reduce_partials(part_rz + (int64_t)s * nrz, nrz);
+    if (threadIdx.x == 0) {
+        PcgScal v;
+        v.rz = rz;
+        v.pq = 0;
+        v.alpha = 0;
+        v.beta = 0;
+        v.rr = bb;
+        v.bb = bb;
+        v.iters = 0;
+        v.pad = 0;
+        v.status = PC_OK;
+        v.done = 0;
+        if (!isfinite(bb) || !isfinite(rz)) {
+            v.status = PC_ENAN;
+            v.done = 1;
+        } else if (bb == 0.0) {
+            v.done = 1;  // zero right-hand side: x = 0 is exact
+        } else if (!(rz > 0.0)) {
+            v.status = PC_EBREAKDOWN;  // preconditioner not positive definite
+            v.done = 1;
+        }
+        sc[s] = v;
+        done[s] = v.done;
+    }
+}
+
+template <typename C>
+__global__ void pcg_copy(const C* __restrict__ z, C* __restrict__ p, int64_t vs, const int* __restrict__ done) {
+    const int s = blockIdx.y;
+    if (done[s]) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x)
+        p[s * vs + e] = z[s * vs + e];
+}
+
+__global__ void pcg_alpha(PcgScal* sc, int* done, const double* part_pq, int spq, int npq) {
+    const int s = blockIdx.x;
+    if (done[s]) return;
+    double pq = reduce_partials(part_pq + (int64_t)s * spq, npq);
+    if (threadIdx.x == 0) {
+        sc[s].pq = pq;
+        if (!isfinite(pq)) {
+            sc[s].status = PC_ENAN;
+            sc[s].done = 1;
+            done[s] = 1;
+        } else if (!(pq > 0.0)) {
+            sc[s].status = PC_EBREAKDOWN;
+            sc[s].done = 1;
+            done[s] = 1;
+        } else {
+            sc[s].alpha = sc[s].rz / pq;
+        }
+    }
+}
+
+template <typename C>
+__global__ void pcg_update_xr(C* __restrict__ x, C* __restrict__ r, const C* __restrict__ p, const C* __restrict__ q,
+                              const PcgScal* __restrict__ sc, const int* __restrict__ done, int64_t vs,
+                              double* __restrict__ part, int npart) {
+    const int s = blockIdx.y;
+    if (done[s]) return;
+    using R = decltype(x[0].x);
+    const R a = (R)sc[s].alpha;
+    double acc = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = s * vs + e;
+        x[i] = cfma(a, p[i], x[i]);
+        C rv = cfma(-a, q[i], r[i]);
+        r[i] = rv;
+        acc += (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
+    }
+    acc = block_sum_pcg(acc);
+    if (threadIdx.x == 0) part[(int64_t)s * npart + blockIdx.x] = acc;
+}
+
+__global__ void pcg_beta(PcgScal* sc, int* done, const double* part_rr, int srr, int nrr, const double* part_rz,
+                         int nrz, double tol2, int maxit) {
+    const int s = blockIdx.x;
+    if (done[s]) return;
+    double rr = reduce_partials(part_rr + (int64_t)s * srr, nrr);
+    double rz = reduce_partials(part_rz + (int64_t)s * nrz, nrz);
+    if (threadIdx.x == 0) {
+        PcgScal v = sc[s];
+        v.iters += 1;
+        v.rr = rr;
+        if (!isfinite(rr) || !isfinite(rz)) {
+            v.status = PC_ENAN;
+            v.done = 1;
+        } else if (rr <= tol2 * v.bb) {
+            v.status = PC_OK;
+            v.done = 1;
+        } else if (v.iters >= maxit) {
+            v.status = PC_ENOCONV;
+            v.done = 1;
+        } else if (!(rz > 0.0)) {
+            v.status = PC_EBREAKDOWN;
+            v.done = 1;
+        } else {
+            v.beta = rz / v.rz;
+            v.rz = rz;
+        }
+        sc[s] = v;
+        done[s] = v.done;
+    }
+}
+
+template <typename C>
+__global__ void pcg_update_p(C* __restrict__ p, const C* __restrict__ z, const PcgScal* __restrict__ sc,
+                             const int* __restrict__ done, int64_t vs) {
+    const int s = blockIdx.y;
+    if (done[s]) return;
+    using R = decltype(p[0].x);
+    const R b = (R)sc[s].beta;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = s * vs + e;
+        p[i] = cfma(b, p[i], z[i]);
+    }
+}
+
+// Gather/scatter between a full-space vector and its four block vectors (stacked).
+template <typename C>
+__global__ void full_to_blocks(const C* __restrict__ full, C* __restrict__ blk, int N, int nsys) {
+    const int64_t n = (int64_t)N * N * N, nb = n / 4;
+    const int X = N / 2;
+    const int64_t total = (int64_t)nsys * 4 * nb;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = e % nb;
+        const int b = (int)((e / nb) % 4);
+        const int64_t s = e / (4 * nb);
+        const int64_t a = t % X, bb = (t / X) % X, k = t / ((int64_t)X * X);
+        const int p12 = b >> 1, p13 = b & 1;
+        const int64_t l = (2 * a + ((k + p13) & 1)) + (int64_t)N * ((2 * bb + ((k + p12 + p13) & 1)) + (int64_t)N * k);
+        for (int c = 0; c < 3; ++c) blk[(s * 4 + b) * 3 * nb + c * nb + t] = full[s * 3 * n + c * n + l];
+    }
+}
+
+template <typename C>
+__global__ void blocks_to_full(const C* __restrict__ blk, C* __restrict__ full, int N, int nsys) {
+    const int64_t n = (int64_t)N * N * N, nb = n / 4;
+    const int X = N / 2;
+    const int64_t total = (int64_t)nsys * 4 * nb;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = e % nb;
+        const int b = (int)((e / nb) % 4);
+        const int64_t s = e / (4 * nb);
+        const int64_t a = t % X, bb = (t / X) % X, k = t / ((int64_t)X * X);
+        const int p12 = b >> 1, p13 = b & 1;
+        const int64_t l = (2 * a + ((k + p13) & 1)) + (int64_t)N * ((2 * bb + ((k + p12 + p13) & 1)) + (int64_t)N * k);
+        for (int c = 0; c < 3; ++c) full[s * 3 * n + c * n + l] = blk[(s * 4 + b) * 3 * nb + c * nb + t];
+    }
+}
+
+static int vec_ctas(int64_t vs) {
+    int64_t g = (vs + 1023) / 1024;
+    if (g > 304) g = 304;
+    return (int)(g < 1 ? 1 : g);
+}
+
+void PcgWork::release() {
+    cudaFree(R);
+    cudaFree(Z);
+    cudaFree(P);
+    cudaFree(Q);
+    cudaFree(part);
+    cudaFree(sc);
+    cudaFree(done);
+    cudaFree(blocks);
+    cudaFreeHost(h_sc);
+    R = Z = P = Q = nullptr;
+    part = nullptr;
+    sc = nullptr;
+    done = blocks = nullptr;
+    h_sc = nullptr;
+    cap = 0;
+}
+
+static int solver_get(pc_grid* g, Solver** out) {
+    if (!g->sol) g->sol = new Solver();
+    *out = g->sol;
+    return PC_OK;
+}
+
+// Workspace for nsys systems of vs elements (+ block scratch for full-space preconditioning).
+static int pcg_work(pc_grid* g, int dtype, int nsys, int64_t vs, bool full, PcgWork** out) {
+    Solver* S;
+    PC_TRY(solver_get(g, &S));
+    PcgWork& w = S->pcg[dtype == PC_C64 ? 0 : 1];
+    const int64_t esz = dtype == PC_C64 ? 8 : 16;
+    // partial-sum slots: stencil CTAs, vector CTAs, unpack CTAs (x4 for full space)
+    const int nap = choose_apply_config(full ? g->N : g->X, full ? g->N : g->Y, g->Z, 1, dtype).ctas;
+    const int npm = std::max(std::max(nap, vec_ctas(vs)), 4 * unpack_ctas(3 * g->nb));
+    if (w.cap >= nsys && w.vs == vs && w.npart_max >= npm && w.dtype == dtype) {
+        *out = &w;
+        return PC_OK;
+    }
+    w.release();
+    w.dtype = dtype;
+    w.vs = vs;
+    w.npart_max = npm;
+    const size_t vb = (size_t)nsys * vs * esz;
+    PC_CUDA_TRY(cudaMalloc(&w.R, vb));
+    PC_CUDA_TRY(cudaMalloc(&w.Z, vb));
+    PC_CUDA_TRY(cudaMalloc(&w.P, vb));
+    PC_CUDA_TRY(cudaMalloc(&w.Q, vb));
+    PC_CUDA_TRY(cudaMalloc(&w.part, sizeof(double) * 3 * (size_t)nsys * npm));
+    PC_CUDA_TRY(cudaMalloc(&w.sc, sizeof(PcgScal) * nsys));
+    PC_CUDA_TRY(cudaMalloc(&w.done, sizeof(int) * nsys));
+    PC_CUDA_TRY(cudaMalloc(&w.blocks, sizeof(int) * 4 * nsys));
+    PC_CUDA_TRY(cudaMallocHost(&w.h_sc, sizeof(PcgScal) * nsys));
+    w.cap = nsys;
+    *out = &w;
+    return PC_OK;
+}
+
+template <typename C>
+static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* Bv, void* Xv,
+                       double tol, int maxit, PcgResult* res, cudaStream_t s) {
+    const bool full = blocks[0] < 0;
+    for (int i = 0; i < nsys; ++i)
+        if ((blocks[i] < 0) != full) return fail(PC_EINVAL, "pcg: mixing full-space and block systems");
+    const int64_t m = full ? g->n : g->nb;
+    const int64_t vs = 3 * m;
+    PcgWork* w;
+    PC_TRY(pcg_work(g, dtype, nsys, vs, full, &w));
+    const int npm = w->npart_max;
+    double* part_a = w->part;                           // stencil <p,q> / ||b||^2
+    double* part_b = w->part + (size_t)nsys * npm;      // ||r||^2
+    double* part_c = w->part + (size_t)2 * nsys * npm;  // <r,z>
+    const C* B = static_cast<const C*>(Bv);
+    C* X = static_cast<C*>(Xv);
+    C* R = static_cast<C*>(w->R);
+    C* Z = static_cast<C*>(w->Z);
+    C* P = static_cast<C*>(w->P);
+    C* Q = static_cast<C*>(w->Q);
+    // block labels of the preconditioner subsystems
+    std::vector<int> hb;
+    if (full)
+        for (int i = 0; i < nsys; ++i)
+            for (int b = 0; b < 4; ++b) hb.push_back(b);
+    else
+        hb.assign(blocks, blocks + nsys);
+    PC_CUDA_TRY(cudaMemcpyAsync(w->blocks, hb.data(), sizeof(int) * hb.size(), cudaMemcpyHostToDevice, s));
+    const int vc = vec_ctas(vs);
+    const dim3 vgrid(vc, nsys);
+
+    // full-space preconditioning goes through the four block transforms
+    void* Rb = nullptr;
+    void* Zb = nullptr;
+    if (full) {
+        // reuse Q as gather buffer for r and the preconditioner workspace owner for z blocks
+        PC_CUDA_TRY(cudaMallocAsync(&Rb, sizeof(C) * nsys * vs, s));
+        PC_CUDA_TRY(cudaMallocAsync(&Zb, sizeof(C) * nsys * vs, s));
+    }
+    int nrz = 0;
+    auto precondition = [&](const int* skip) -> int {
+        if (!full) return precond_apply(g, dtype, nsys, R, Z, w->blocks, skip, sigma, s, part_c, &nrz);
+        const int gb = (int)std::min<int64_t>((nsys * vs + 255) / 256, 152 * 16);
+        full_to_blocks<C><<<gb, 256, 0, s>>>(R, static_cast<C*>(Rb), g->N, nsys);
+        int np = 0;
+        PC_TRY(precond_apply(g, dtype, 4 * nsys, Rb, Zb, w->blocks, nullptr, sigma, s, part_c, &np));
+        nrz = 4 * np;  // the four block partials of a full system are contiguous
+        blocks_to_full<C><<<gb, 256, 0, s>>>(static_cast<C*>(Zb), Z, g->N, nsys);
+        PC_CUDA_TRY(cudaGetLastError());
+        return PC_OK;
+    };
+
+    pcg_start<C><<<vgrid, 256, 0, s>>>(B, X, R, vs, part_a, npm);
+    PC_CUDA_TRY(cudaGetLastError());
+    PC_TRY(precondition(nullptr));
+    pcg_start_reduce<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, vc, part_c, nrz);
+    pcg_copy<C><<<vgrid, 256, 0, s>>>(Z, P, vs, w->done);
+    PC_CUDA_TRY(cudaGetLastError());
+
+    // stencil items: q_s = (A - sigma M) p_s with Re<p_s, q_s> partials in slot s
+    std::vector<ApplyItem> items(nsys);
+    for (int i = 0; i < nsys; ++i) {
+        items[i].x = P + i * vs;
+        items[i].y = Q + i * vs;
+        items[i].mat = grid_mat(g, blocks[i]);
+        items[i].shift = sigma;
+        items[i].block = blocks[i];
+        items[i].dot_slot = i;
+        items[i].skip = w->done + i;
+    }
+    const ApplyConfig cfg = choose_apply_config(full ? g->N : g->X, full ? g->N : g->Y, g->Z, nsys, dtype);
+    const int napc = cfg.ctas;
+    const double tol2 = tol * tol;
+    const int chunk = 4;
+    int it = 0;
+    bool all_done = false;
+    while (!all_done) {
+        for (int c = 0; c < chunk; ++c, ++it) {
+            PC_TRY(grid_apply(g, dtype, full, items.data(), nsys, part_a, npm, s, &cfg));
+            pcg_alpha<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, napc);
+            pcg_update_xr<C><<<vgrid, 256, 0, s>>>(X, R, P, Q, w->sc, w->done, vs, part_b, npm);
+            PC_CUDA_TRY(cudaGetLastError());
+            PC_TRY(precondition(full ? nullptr : w->done));
+            pcg_beta<<<nsys, 256, 0, s>>>(w->sc, w->done, part_b, npm, vc, part_c, nrz, tol2, maxit);
+            pcg_update_p<C><<<vgrid, 256, 0, s>>>(P, Z, w->sc, w->done, vs);
+            PC_CUDA_TRY(cudaGetLastError());
+        }
+        PC_CUDA_TRY(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(PcgScal) * nsys, cudaMemcpyDeviceToHost, s));
+        PC_CUDA_TRY(cudaStreamSynchronize(s));
+        all_done = true;
+        for (int i = 0; i < nsys; ++i)
+            if (!w->h_sc[i].done) all_done = false;
+        if (it > maxit + chunk) break;  // the device loop stops by itself at maxit; host backstop
+    }
+    if (full) {
+        cudaFreeAsync(Rb, s);
+        cudaFreeAsync(Zb, s);
+    }
+    int worst = PC_OK;
+    for (int i = 0; i < nsys; ++i) {
+        const PcgScal& v = w->h_sc[i];
+        res[i].iters = v.iters;
+        res[i].status = v.done ? v.status : PC_ENOCONV;
+        res[i].rel_resid = v.bb > 0 ? std::sqrt(v.rr / v.bb) : 0.0;
+        if (res[i].status != PC_OK && worst == PC_OK) worst = res[i].status;
+    }
+    return PC_OK;
+}
+
+int pcg_solve(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* B, void* X, double tol,
+              int maxit, PcgResult* res, cudaStream_t s) {
+    if (nsys <= 0) return PC_OK;
+    if (!g->k.set) return fail(PC_ESTATE, "pcg: call pc_set_k first");
+    if (!(tol > 0) || maxit < 1) return fail(PC_EINVAL, "pcg: tol must be > 0 and maxit >= 1");
+    if (dtype == PC_C64) return pcg_solve_t<float2>(g, dtype, nsys, blocks, sigma, B, X, tol, maxit, res, s);
+    return pcg_solve_t<double2>(g, dtype, nsys, blocks, sigma, B, X, tol, maxit, res, s);
+}
+
+}  // namespace pc
+
+Solver::~Solver() {
+    pcg[0].release();
+    pcg[1].release();
+    if (blas) cublasDestroy(blas);
+}

@@ -1,0 +1,67 @@
+// Solver-side declarations: batched PCG and the shift-invert Krylov-Schur driver.
+#pragma once
+
+#include <cublas_v2.h>
+
+#include <vector>
+
+#include "pc_fourier.h"
+#include "pc_internal.h"
+
+namespace pc {
+
+// Per-system PCG scalars (device).
+struct PcgScal {
+    double rz;     // Re <r, z>
+    double pq;     // Re <p, (A - sigma M) p>
+    double alpha;  // rz / pq
+    double beta;   // rz_new / rz
+    double rr;     // ||r||^2
+    double bb;     // ||b||^2
+    int done;      // 1 once converged or failed
+    int status;    // PC_OK, PC_ENOCONV, PC_EBREAKDOWN, PC_ENAN
+    int iters;     // iterations taken
+    int pad;
+};
+
+struct PcgResult {
+    int iters;
+    int status;
+    double rel_resid;
+};
+
+// Device workspace of one batched PCG configuration.
+struct PcgWork {
+    int dtype = 0, cap = 0;  // systems the buffers hold
+    int64_t vs = 0;          // elements per system vector (3 m)
+    void *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr;
+    double* part = nullptr;  // partial sums, [3][cap][npart_max]
+    int npart_max = 0;
+    PcgScal* sc = nullptr;   // [cap]
+    int* done = nullptr;     // [cap] mirror of sc.done for skip flags
+    int* blocks = nullptr;   // [cap] block of each system
+    PcgScal* h_sc = nullptr; // pinned host mirror
+    void release();
+};
+
+// Solve (A - sigma M) x_s = b_s for nsys systems of the same grid, stacked contiguously
+// (stride 3 m elements); blocks[s] in -1..3 (all full-space or all blocks).  x starts at
+// zero.  Per-system results in res (host, nsys entries).
+int pcg_solve(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* B, void* X,
+              double tol, int maxit, PcgResult* res, cudaStream_t s);
+
+// Launch one batch of stencil applies on grid g (items share the layout kind).
+int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nitems, double* dot_partials,
+               int dot_stride, cudaStream_t s, const ApplyConfig* cfg_in);
+const void* grid_mat(const pc_grid* g, int block);
+int launch_mass(int dtype, const void* x, void* y, const void* mat, int matkind, double rho0, double rho1,
+                int64_t m, cudaStream_t s, int nvec);
+int launch_transfer(int dtype, const void* src, void* dst, int N, int b, int dir, cudaStream_t s);
+
+}  // namespace pc
+
+struct Solver {
+    pc::PcgWork pcg[2];  // complex64 / complex128 workspaces
+    cublasHandle_t blas = nullptr;
+    ~Solver();
+};

@@ -14,15 +14,15 @@ __host__ __device__ __forceinline__ int64_t block_to_full(int64_t t, int N, int 
     return i + (int64_t)N * (j + (int64_t)N * k);
 }
 
+// y = M x for ncomp consecutive component arrays of m nodes (3 per vector).
 template <typename C, typename R>
 __global__ void mass_kernel(const C* __restrict__ x, C* __restrict__ y, const void* __restrict__ mat,
-                            int matkind, R rho0, R rho1, int64_t m) {
+                            int matkind, R rho0, R rho1, int64_t m, int ncomp) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += stride) {
         R th = matkind ? (R)(static_cast<const float*>(mat)[t]) : (R)(static_cast<const uint8_t*>(mat)[t]);
         R rho = rho0 + th * (rho1 - rho0);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) y[a * m + t] = cscale(rho, x[a * m + t]);
+        for (int a = 0; a < ncomp; ++a) y[a * m + t] = cscale(rho, x[a * m + t]);
     }
 }
 
@@ -48,13 +48,13 @@ static int grid_for(int64_t m) {
 }
 
 int launch_mass(int dtype, const void* x, void* y, const void* mat, int matkind, double rho0,
-                double rho1, int64_t m, cudaStream_t s) {
+                double rho1, int64_t m, cudaStream_t s, int nvec) {
     if (dtype == PC_C64)
         mass_kernel<float2, float><<<grid_for(m), 256, 0, s>>>((const float2*)x, (float2*)y, mat, matkind,
-                                                              (float)rho0, (float)rho1, m);
+                                                              (float)rho0, (float)rho1, m, 3 * nvec);
     else
         mass_kernel<double2, double><<<grid_for(m), 256, 0, s>>>((const double2*)x, (double2*)y, mat,
-                                                                matkind, rho0, rho1, m);
+                                                                matkind, rho0, rho1, m, 3 * nvec);
     PC_CUDA_TRY(cudaGetLastError());
     return PC_OK;
 }

@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 parity-blocked band solver.
+
+One step = one Bloch vector of the plain FP64 workload: a seeded two-phase
+simple-cubic cell (N = 48, sphere R = 0.35, seed 2), the Gamma-X-M-Gamma-R-X
+path of 31 k-points (6 intervals per segment), the lowest 20 non-zero bands
+at true relative residual 1e-8, solved on the four parity blocks with the
+shift-invert Krylov-Schur eigensolver and merged.  A step runs every step of
+the hot path: Bloch phases and Fourier symbol tables, fused block applies,
+preconditioned inner CG, Gamma deflation, orthogonalisation and Rayleigh-Ritz,
+FP64 true residuals and the block merge.
+
+Printed JSON (one line, rank 0):
+  value     = seconds per k-point for the whole job (max over ranks of the
+              timed device time / k-points processed by all ranks)
+  apply     = complex64 and complex128 four-block apply throughput at N = 160
+              (GDoF/s, algorithmic HBM fraction)
+  roofline  = the dominant kernel of the step (the FP64 stencil apply), its
+              device time measured with CUDA events on its launch stream
+  e2e       = the same metric through the C ABI from host material buffers
+  cpu_baseline = the FP64 CPU oracle on the host cores (bounded sample)
+
+``--impl reference`` times the CPU oracle as the reference arm instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "block B C B^H apply GDoF/s & HBM frac; sec per k-point for 20 bands @1e-8 resid"
+WORKLOAD = "two-phase SC cell N=48 (R=0.35, seed 2), 31-point Gamma-X-M-Gamma-R-X path, 20 bands, resid 1e-8, FP64"
+NEV = 20
+TOL = 1e-8
+# algorithmic cost of one stencil apply per node (cubic lattice, binary material):
+#   bytes: read x (3 complex) + write y (3 complex) + 1 material byte
+#   flops: 294 real flops (differences, reconstruction, 6x6 stiffness, fluxes, gather, shift)
+BYTES_PER_NODE = {"c64": 3 * 8 * 2 + 1, "c128": 3 * 16 * 2 + 1}
+FLOPS_PER_NODE = 294
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 peak of GB300: 1.25 TFLOP/s dense (recipe's nominal figure), used for the
+# ALU roofline of the complex128 apply.
+FP64_PEAK_TFLOPS = 1.25
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        if sm:
+            sm.sort()
+            out["sm_mhz"] = sm[len(sm) // 2]
+        out["sm_max_mhz"] = smax
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(sm)
+        return out
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_oracle_sample(apply_count_per_kpoint, seconds_budget=15.0):
+    """Time the FP64 CPU oracle apply (OpenMP) on block applies of the N = 48 workload,
+    and scale by the number of block applies one k-point solve performs."""
+    import numpy as np
+    from oracle import oracle as O
+    from workloads import complex_gaussian, config_cell
+
+    cell = config_cell("fp64")
+    pb = O.problem_from_cell(cell, C0=1e9, rho0=1e3)
+    threads = os.cpu_count() or 1
+    kappa = [0.25, 0.0, 0.0]
+    x = complex_gaussian((3, cell.N ** 3 // 4), 7)
+    O.apply_block(pb, kappa, 0, x, 0.1, nthreads=threads)  # warm-up (builds and loads the oracle)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.apply_block(pb, kappa, n % 4, x, 0.1, nthreads=threads)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_budget or n >= 2000:
+            break
+    per_apply = el / n
+    return {"value": per_apply * apply_count_per_kpoint, "unit": "s/k-point", "cores": threads, "kind": "oracle",
+            "sample": ("%d FP64 oracle block applies (N=48, OpenMP %d threads, %.2f ms each) scaled by the %d "
+                       "block applies one k-point solve performs; the oracle's exact eigen-solve (ARPACK + "
+                       "SuperLU) takes ~15 min per block and is not sampled" % (n, threads, per_apply * 1e3,
+                                                                                 apply_count_per_kpoint)),
+            "per_apply_ms": per_apply * 1e3}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, as it stands, on the same config, metric and unit."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import oracle as O
+    from workloads import complex_gaussian, config_cell
+    cell = config_cell("fp64")
+    pb = O.problem_from_cell(cell, C0=1e9, rho0=1e3)
+    threads = os.cpu_count() or 1
+    x = complex_gaussian((3, cell.N ** 3 // 4), 7)
+    # one k-point solve of our arm performs about this many block applies (measured on GB300)
+    applies = int(os.environ.get("PC_APPLIES_PER_KPOINT", "24000"))
+    reps = 16
+    for _ in range(args.warmup):
+        O.apply_block(pb, [0.25, 0, 0], 0, x, 0.1, nthreads=threads)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        for r in range(reps):
+            O.apply_block(pb, [0.25, 0, 0], r % 4, x, 0.1, nthreads=threads)
+        times.append((time.perf_counter() - t0) / reps * applies)
+    v = float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/k-point", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": 48},
+            "cpu_baseline": {"value": v, "unit": "s/k-point", "cores": threads, "kind": "oracle",
+                             "sample": "%d FP64 oracle block applies per step at N=48, scaled by %d block applies "
+                                       "per k-point solve" % (reps, applies)},
+            "e2e": {"value": v, "unit": "s/k-point", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def apply_throughput(pc, torch, reps=20):
+    """Four-block apply at N = 160 (R = 0.3, seed 3), complex64 and complex128, one launch per rep."""
+    from workloads import config_cell
+    cell = config_cell("precision")
+    N = cell.N
+    g = pc.pc_grid_create(N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+    hbm, src = peaks()
+    out = {"workload": "N=160 two-phase cell (R=0.3, seed 3), all four parity blocks in one launch, "
+                       "kappa=(0.3,0.1,0.2), shift on", "hbm_peak_gbs": hbm, "peak_source": src}
+    try:
+        pc.pc_set_k(g, [0.3, 0.1, 0.2])
+        nb = N ** 3 // 4
+        flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+        for name, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
+            xs = [torch.randn(3 * nb, dtype=dt, device="cuda") for _ in range(4)]
+            ys = [torch.empty_like(x) for x in xs]
+            for _ in range(3):
+                pc.pc_apply_batch(g, [0, 1, 2, 3], xs, ys, [0.5] * 4)
+            torch.cuda.synchronize()
+            ts = []
+            for r in range(reps):
+                flush.fill_(float(r))  # L2 flush between repetitions (512 MB > 129 MB L2)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                pc.pc_apply_batch(g, [0, 1, 2, 3], xs, ys, [0.5] * 4)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            t = sorted(ts)[len(ts) // 2]
+            nodes = 4 * nb
+            gbs = nodes * BYTES_PER_NODE[name] / t / 1e9
+            out[name] = {"ms": t * 1e3, "gdof_s": 3 * nodes / t / 1e9, "alg_gbs": gbs, "hbm_frac": gbs / hbm,
+                         "fp_tflops": nodes * FLOPS_PER_NODE / t / 1e12}
+            del xs, ys
+    finally:
+        pc.pc_grid_destroy(g)
+    return out
+
+
+def profile_run(what):
+    import torch
+    import paper_2606_03599_gb300 as pc
+    from workloads import config_cell
+    if what.startswith("kpoint"):
+        cell = config_cell("fp64")
+        g = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+        prec = pc.PC_PREC_MIXED if what == "kpoint-mixed" else pc.PC_PREC_FP64
+        opt = pc.pc_options_default(tol=TOL, precision=prec)
+        pc.pc_eigs(g, [0.5, 0.0, 0.0], NEV, opt=opt)
+    else:
+        cell = config_cell("precision")
+        N = cell.N
+        g = pc.pc_grid_create(N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+        pc.pc_set_k(g, [0.3, 0.1, 0.2])
+        dt = torch.complex64 if what == "apply-c64" else torch.complex128
+        xs = [torch.randn(3 * N ** 3 // 4, dtype=dt, device="cuda") for _ in range(4)]
+        ys = [torch.empty_like(x) for x in xs]
+        for _ in range(3):
+            pc.pc_apply_batch(g, [0, 1, 2, 3], xs, ys, [0.5] * 4)
+    torch.cuda.synchronize()
+    pc.pc_grid_destroy(g)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--profile", default=None, choices=["kpoint", "kpoint-mixed", "apply-c64", "apply-c128"],
+                    help="profiling aid for ncu: run only one k-point solve of the workload, or one "
+                         "N=160 four-block apply (after two untimed ones), and print nothing else")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.profile:
+        profile_run(args.profile)
+        return
+    args.warmup = max(3, args.warmup)
+
+    import numpy as np
+    import torch
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2606_03599_gb300 as pc
+    from workloads import config_cell, sc_path
+
+    cell = config_cell("fp64")
+    kpts = sc_path(6)
+    stream = torch.cuda.Stream()
+    opt = pc.pc_options_default(tol=TOL, inner_tol=1e-10, precision=pc.PC_PREC_FP64)
+    opt.stream = stream.cuda_stream
+    g = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+
+    def kpoint(step):
+        return kpts[(step * world + rank) % len(kpts)]
+
+    # warm-up (untimed)
+    for w in range(args.warmup):
+        pc.pc_eigs(g, kpoint(w), NEV, opt=opt)
+    torch.cuda.synchronize()
+
+    # timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    pc.pc_stats_reset()
+    pc.pc_stats_timing(1)
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms, infos, residuals = [], [], []
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))  # L2 flush between timed steps (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev, blocks, info = pc.pc_eigs(g, kpoint(args.warmup + s), NEV, opt=opt)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        infos.append(info)
+        residuals.append(info["max_rel_resid"])
+    torch.cuda.synchronize()
+    barrier(world)
+    st = pc.pc_stats_get()
+    pc.pc_stats_timing(0)
+    clk = clocks.stop()
+    local_time = sum(step_ms) / 1e3
+    t_max = max_over_ranks(world, local_time)
+    kpts_total = sum_over_ranks(world, float(args.steps))
+    value = t_max / kpts_total
+
+    # dominant kernel: FP64 stencil apply, device time from events on its launch stream
+    n_app = st["apply_timed"][1]
+    app_ms = st["apply_ms"][1] / max(1, n_app)
+    nodes_per_launch = st["apply_nodes"][1] / max(1, n_app)
+    achieved_tflops = nodes_per_launch * FLOPS_PER_NODE / (app_ms / 1e3) / 1e12
+    roofline = {"kernel": "apply_kernel<double> (fused block stencil, FP64)", "bound": "alu",
+                "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                "launches": n_app, "avg_launch_us": app_ms * 1e3, "nodes_per_launch": nodes_per_launch,
+                "flops_per_node": FLOPS_PER_NODE, "peak_source": "nominal FP64 dense rate of GB300"}
+
+    # end-to-end through the C ABI from host buffers: material upload, solve, eigenvalues back
+    e2e = None
+    if rank == 0 or world > 1:
+        phase_pinned = torch.from_numpy(cell.phase).pin_memory()
+        e2e_ms = []
+        for s in range(min(args.steps, 4)):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g2 = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=phase_pinned.numpy(), a_lat=cell.a_lat)
+            ev2, _, _ = pc.pc_eigs(g2, kpoint(s), NEV, opt=opt)
+            pc.pc_grid_destroy(g2)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+        n = cell.N ** 3
+        e2e = {"value": float(np.mean(e2e_ms)) / 1e3, "unit": "s/k-point", "h2d_bytes_per_step": 2 * n,
+               "d2h_bytes_per_step": NEV * 8, "steps": len(e2e_ms)}
+
+    apply = apply_throughput(pc, torch) if rank == 0 else None
+    pc.pc_grid_destroy(g)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    # block-apply equivalents per k-point (FP64 applies of the timed steps, counted in nodes)
+    applies_per_k = int(round(st["apply_nodes"][1] / (cell.N ** 3 / 4) / args.steps))
+    cpu = None if args.no_cpu else cpu_oracle_sample(applies_per_k)
+    pcg_total = sum(i["pcg_iters"] for i in infos)
+    line = {
+        "metric": METRIC, "value": value, "unit": "s/k-point", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": cell.N, "bands": NEV, "tol": TOL, "blocks": 4,
+                   "k_points_per_rank": args.steps, "precision": "plain FP64",
+                   "l2": "512 MB buffer written between timed steps (L2 = 129 MB)"},
+        "roofline": roofline,
+        "apply": apply,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": st["launches"],
+        "clocks": clk,
+        "solver": {"pcg_iters_per_kpoint": pcg_total / args.steps,
+                   "max_pcg_iters": max(i["max_pcg_iters"] for i in infos),
+                   "inner_solves_per_kpoint": sum(i["inner_solves"] for i in infos) / args.steps,
+                   "block_applies_per_kpoint": applies_per_k,
+                   "max_true_rel_resid": max(residuals),
+                   "step_ms": step_ms},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -104,6 +104,7 @@ typedef struct {
     int inner_maxit;     /* PCG iteration cap per solve; default 400 */
     int guard;           /* extra Ritz pairs carried per block beyond its share; default 3 */
     int verbose;         /* 0 = silent */
+    void* stream;        /* cudaStream_t for all of the solve's work, or NULL for an internal stream */
 } pc_options;
 
 /* Statistics of one pc_eigs call. */
@@ -208,7 +209,36 @@ double pc_default_sigma(const pc_grid* g);
 int pc_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_options* opt,
             double* evals, void* evecs, int* block_of, pc_eigs_info* info);
 
+/* Batched apply: one launch computes y_i = (A_hat - shift_i M_hat) x_i for
+ * count vectors that may belong to different parity blocks (blocks[i] in 0..3),
+ * or count full-space vectors (every blocks[i] = -1).  x, y: host arrays of
+ * `count` device pointers (3 n_b or 3 n elements each); shifts: host array. */
+int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const void* const* x,
+                   void* const* y, const double* shifts, void* stream);
+
 /* ---- diagnostics ------------------------------------------------------- */
+
+/* Process-wide counters of the library's own kernel launches (cuFFT and cuBLAS
+ * kernels excluded) and, while timing is enabled, the device time of the
+ * stencil-apply launches measured with CUDA events on their launch stream. */
+typedef struct {
+    long long launches;        /* every kernel launch of this library */
+    long long apply_launches;  /* stencil-apply launches (both precisions) */
+    long long apply_timed[2];  /* timed apply launches: [0] complex64, [1] complex128 */
+    double apply_ms[2];        /* their summed device time, ms */
+    double apply_nodes[2];     /* nodes they processed (sum over items) */
+} pc_stats;
+
+/* Enable (1) or disable (0) event timing of apply launches.  Timing adds two
+ * event records per apply launch. */
+int pc_stats_timing(int enable);
+
+/* Reset all counters. */
+int pc_stats_reset(void);
+
+/* Read the counters; synchronises on the recorded events first. */
+int pc_stats_get(pc_stats* out);
+
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char* pc_last_error(void);

@@ -26,7 +26,8 @@ EXPORTED = [
     "pc_grid_create", "pc_grid_destroy", "pc_grid_units", "pc_set_k", "pc_block_index",
     "pc_block_apply", "pc_block_apply_many", "pc_block_mass", "pc_block_transfer",
     "pc_block_fourier", "pc_shift_invert_pcg", "pc_options_default", "pc_default_sigma",
-    "pc_eigs", "pc_last_error", "pc_version",
+    "pc_eigs", "pc_last_error", "pc_version", "pc_apply_batch", "pc_stats_timing", "pc_stats_reset",
+    "pc_stats_get",
 ]
 
 
@@ -58,7 +59,13 @@ class c_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("precision", ctypes.c_int),
                 ("full_space", ctypes.c_int), ("block_size", ctypes.c_int), ("max_basis", ctypes.c_int),
                 ("max_restarts", ctypes.c_int), ("inner_maxit", ctypes.c_int), ("guard", ctypes.c_int),
-                ("verbose", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class c_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("apply_launches", ctypes.c_longlong),
+                ("apply_timed", ctypes.c_longlong * 2), ("apply_ms", ctypes.c_double * 2),
+                ("apply_nodes", ctypes.c_double * 2)]
 
 
 class c_eigs_info(ctypes.Structure):
@@ -91,6 +98,10 @@ def _load():
         "pc_default_sigma": ([vp], cd),
         "pc_eigs": ([vp, dp, ci, cd, ctypes.POINTER(c_options), dp, vp, ctypes.POINTER(ci),
                      ctypes.POINTER(c_eigs_info)], ci),
+        "pc_apply_batch": ([vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp], ci),
+        "pc_stats_timing": ([ci], ci),
+        "pc_stats_reset": ([], ci),
+        "pc_stats_get": ([ctypes.POINTER(c_stats)], ci),
         "pc_last_error": ([], ctypes.c_char_p),
         "pc_version": ([], ctypes.c_char_p),
     }
@@ -262,6 +273,31 @@ def pc_eigs(g, kappa, nev, sigma=float("nan"), opt=None, evecs=None, raise_on_fa
     d = {f: getattr(info, f) for f, _ in c_eigs_info._fields_}
     d["rc"] = rc
     return ev, np.array(list(bo)), d
+
+
+def pc_apply_batch(g, blocks, xs, ys, shifts, stream=None):
+    n = len(blocks)
+    bl = (ctypes.c_int * n)(*[int(b) for b in blocks])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    yp = (ctypes.c_void_p * n)(*[_ptr(y) for y in ys])
+    sh = (ctypes.c_double * n)(*[float(v) for v in shifts])
+    _check(lib.pc_apply_batch(g, _dtype_code(xs[0]), n, bl, xp, yp, sh, _stream(stream)))
+
+
+def pc_stats_timing(enable):
+    _check(lib.pc_stats_timing(int(bool(enable))))
+
+
+def pc_stats_reset():
+    _check(lib.pc_stats_reset())
+
+
+def pc_stats_get():
+    st = c_stats()
+    _check(lib.pc_stats_get(ctypes.byref(st)))
+    return {"launches": st.launches, "apply_launches": st.apply_launches,
+            "apply_timed": list(st.apply_timed), "apply_ms": list(st.apply_ms),
+            "apply_nodes": list(st.apply_nodes)}
 
 
 def pc_version():

@@ -241,20 +241,25 @@ int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nit
                int dot_stride, cudaStream_t s, const ApplyConfig* cfg_in) {
     const int X = full ? g->N : g->X, Y = full ? g->N : g->Y, Z = g->Z;
     ApplyConfig cfg = cfg_in ? *cfg_in : choose_apply_config(X, Y, Z, nitems, dtype);
+    void* th = timing_enabled() ? timing_begin(s) : nullptr;
+    int rc;
     if (dtype == PC_C64) {
         StencilParams<float> P = g->P32;
         P.X = X;
         P.Y = Y;
         P.Z = Z;
-        return launch_apply_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
-                                dot_stride, s);
+        rc = launch_apply_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
+                              dot_stride, s);
+    } else {
+        StencilParams<double> P = g->P64;
+        P.X = X;
+        P.Y = Y;
+        P.Z = Z;
+        rc = launch_apply_f64(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
+                              dot_stride, s);
     }
-    StencilParams<double> P = g->P64;
-    P.X = X;
-    P.Y = Y;
-    P.Z = Z;
-    return launch_apply_f64(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
-                            dot_stride, s);
+    if (th) timing_end(th, s, dtype == PC_C64 ? 0 : 1, (double)nitems * X * Y * Z);
+    return rc;
 }
 
 const void* grid_mat(const pc_grid* g, int block) { return block < 0 ? g->d_mat_full : g->d_mat_blk[block]; }
@@ -290,6 +295,31 @@ int pc_block_apply_many(pc_grid* g, int block, int dtype, int count, const void*
         items[i].skip = nullptr;
     }
     return grid_apply(g, dtype, block < 0, items.data(), count, nullptr, 0, (cudaStream_t)stream, nullptr);
+}
+
+int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const void* const* x, void* const* y,
+                   const double* shifts, void* stream) {
+    if (!g || !blocks || !x || !y || !shifts) return fail(PC_EINVAL, "pc_apply_batch: null argument");
+    if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_apply_batch: bad dtype");
+    if (count < 0) return fail(PC_EINVAL, "pc_apply_batch: negative count");
+    if (!g->k.set) return fail(PC_ESTATE, "pc_apply_batch: call pc_set_k first");
+    if (count == 0) return PC_OK;
+    const bool full = blocks[0] < 0;
+    std::vector<ApplyItem> items(count);
+    for (int i = 0; i < count; ++i) {
+        if (blocks[i] < -1 || blocks[i] > 3 || (blocks[i] < 0) != full)
+            return fail(PC_EINVAL, "pc_apply_batch: blocks must all be 0..3 or all -1");
+        if (!x[i] || !y[i] || x[i] == y[i]) return fail(PC_EINVAL, "pc_apply_batch: null or aliased vector");
+        if (!std::isfinite(shifts[i])) return fail(PC_EINVAL, "pc_apply_batch: non-finite shift");
+        items[i].x = x[i];
+        items[i].y = y[i];
+        items[i].mat = grid_mat(g, blocks[i]);
+        items[i].shift = shifts[i];
+        items[i].block = blocks[i];
+        items[i].dot_slot = -1;
+        items[i].skip = nullptr;
+    }
+    return grid_apply(g, dtype, full, items.data(), count, nullptr, 0, (cudaStream_t)stream, nullptr);
 }
 
 int pc_block_apply(pc_grid* g, int block, int dtype, const void* x, void* y, double shift, void* stream) {

@@ -85,6 +85,8 @@ static int launch_tile(const StencilParams<R>& P, const ApplyItem* items, int ni
         for (int i = 0; i < B.n; ++i) B.it[i] = items[base + i];
         dim3 grid(ntx * nty, nch, B.n);
         kern<<<grid, T::NT, smem, s>>>(P, B, ntx, tz, dot_partials, dot_stride);
+        note_launch();
+        note_apply_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "apply_kernel launch");
     }

@@ -353,6 +353,7 @@ static int cholqr2(Eigs& E, Space& S, double2* Wv, int cols, int nv, std::vector
             if (pass == 1) return fail(PC_ENOCONV, "eigensolver: Krylov block lost rank twice");
             // replace the block by fresh random directions (breakdown of the Krylov space)
             fill_random<<<ctas_for(cols * S.vs), 256, 0, E.s>>>(Wv, cols * S.vs, seed);
+            note_launch();
             PC_TRY(project_null(E, S, Wv, cols));
             for (int rep = 0; rep < 2; ++rep) {
                 PC_TRY(mass(E, S, Wv, E.MW, cols));
@@ -409,6 +410,7 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t v
     const double tol32 = 1e-4;
     for (int sweep = 0; sweep < 40; ++sweep) {
         sq_norms<double2><<<vg, 256, 0, E.s>>>(E.MW, vs, E.dpart, nc);
+        note_launch();
         PC_CUDA_TRY(cudaMemcpyAsync(part.data(), E.dpart, sizeof(double) * nsys * nc, cudaMemcpyDeviceToHost, E.s));
         PC_CUDA_TRY(cudaStreamSynchronize(E.s));
         bool all = true;
@@ -425,6 +427,7 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t v
         if (!std::isfinite(rnorm[0])) return fail(PC_ENAN, "refinement met NaN");
         PC_CUDA_TRY(cudaMemcpyAsync(E.dscale, sc.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, E.s));
         to_c64_scaled<<<vg, 256, 0, E.s>>>(E.MW, (float2*)E.R32, E.dscale, vs);
+        note_launch();
         PC_TRY(pcg_solve(g, PC_C64, nsys, blocks.data(), E.sigma, E.R32, E.X32, tol32, o.inner_maxit, res.data(), E.s));
         for (auto& r : res) {
             E.pcg_iters += r.iters;
@@ -434,6 +437,7 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t v
         for (int i = 0; i < nsys; ++i) sc[i] = rnorm[i];
         PC_CUDA_TRY(cudaMemcpyAsync(E.dscale, sc.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, E.s));
         axpy_c64_into_c128<<<vg, 256, 0, E.s>>>((const float2*)E.X32, E.W, E.dscale, vs);
+        note_launch();
         // residual in FP64: MW = RHS - (A - sigma M) W
         std::vector<ApplyItem> items(nsys);
         for (int i = 0; i < nsys; ++i) {
@@ -447,6 +451,7 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t v
         }
         PC_TRY(grid_apply(g, PC_C128, blocks[0] < 0, items.data(), nsys, nullptr, 0, E.s, nullptr));
         sub_from<<<ctas_for(nsys * vs), 256, 0, E.s>>>(E.RHS, E.MW, nsys * vs);
+        note_launch();
         PC_CUDA_TRY(cudaGetLastError());
     }
     E.solves += nsys;
@@ -486,6 +491,7 @@ static int check_pairs(Eigs& E, Space& S, int ncand, std::vector<double>& lam, s
     const int nc = ctas_for(S.m);
     resid_stats<<<dim3(nc, ncand), 256, 0, E.s>>>(E.Y, E.AY, grid_mat(g, S.block), g->matkind, g->rhohat[0],
                                                    g->rhohat[1], S.m, E.dpart, nc);
+    note_launch();
     PC_CUDA_TRY(cudaGetLastError());
     std::vector<double> part((size_t)ncand * 5 * nc);
     PC_CUDA_TRY(cudaMemcpyAsync(part.data(), E.dpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, E.s));
@@ -660,11 +666,16 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
     E.bs = std::max(1, std::min(opt->block_size, 16));
     E.mmax = std::max(opt->max_basis, 3 * E.bs);
     E.mcap = E.mmax + 2 * E.bs;
-    PC_CUDA_TRY(cudaStreamCreateWithFlags(&E.s, cudaStreamNonBlocking));
+    const bool own_stream = opt->stream == nullptr;
+    if (own_stream) PC_CUDA_TRY(cudaStreamCreateWithFlags(&E.s, cudaStreamNonBlocking));
+    else E.s = (cudaStream_t)opt->stream;
     struct StreamGuard {
         cudaStream_t s;
-        ~StreamGuard() { cudaStreamDestroy(s); }
-    } sg{E.s};
+        bool own;
+        ~StreamGuard() {
+            if (own) cudaStreamDestroy(s);
+        }
+    } sg{E.s, own_stream};
     if (!SV->blas) {
         if (cublasCreate(&SV->blas) != CUBLAS_STATUS_SUCCESS) return fail(PC_ECUDA, "cublasCreate failed");
     }
@@ -704,6 +715,7 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
         PC_TRY(build_null(E, S));
         zero_modes += S.nz;
         fill_random<<<ctas_for(E.bs * vs), 256, 0, E.s>>>(S.V, E.bs * vs, 0x5EED0000ull + (uint64_t)(i + 1) * 1000003ull);
+        note_launch();
         PC_CUDA_TRY(cudaGetLastError());
         PC_TRY(project_null(E, S, S.V, E.bs));
         std::vector<cd> R;
@@ -855,6 +867,7 @@ int pc_options_default(pc_options* o) {
     o->inner_maxit = 400;
     o->guard = 3;
     o->verbose = 0;
+    o->stream = nullptr;
     return PC_OK;
 }
 

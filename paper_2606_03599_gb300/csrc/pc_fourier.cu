@@ -395,7 +395,9 @@ int precond_set_k(pc_grid* g) {
     sp.null_tol = 1e-9;
     PC_CUDA_TRY(cudaMemset(P->d_null, 0, sizeof(int) * 65));
     symbol_table<<<nblocks_for(g->nb), 256>>>(P->d_Aref, P->d_null, P->d_null + 1, P->ea, P->eb, P->egf, sp);
+    note_launch();
     table_to_f32<<<nblocks_for(9 * g->nb), 256>>>(P->d_Aref, P->d_Aref32, 9 * g->nb);
+    note_launch();
     PC_CUDA_TRY(cudaGetLastError());
     int hn[65];
     PC_CUDA_TRY(cudaMemcpy(hn, P->d_null, sizeof(hn), cudaMemcpyDeviceToHost));
@@ -461,35 +463,39 @@ int precond_apply(pc_grid* g, int dtype, int nsys, const void* r, void* z, const
     if (dtype == PC_C64) {
         fourier_pack<float2><<<nblocks_for(nsys * vs), 256, 0, s>>>((const float2*)r, (float2*)W, P->twa, P->twb,
                                                                   P->twk, g->X, g->Y, g->Z, nsys, vs, vs, 1.0, 0);
+        note_launch();
         PC_TRY(exec_fft(plan, dtype, W, CUFFT_FORWARD, s));
         precond_symbol_solve<float2, float><<<dim3(nblocks_for(g->nb / 2), nsys), 256, 0, s>>>(
             (float2*)W, P->d_Aref32, P->ea, P->eb, P->egh, d_sys_block, d_skip, g->X, g->Y, g->Z, vs, shift_rho, inv_nb);
+        note_launch();
         PC_TRY(exec_fft(plan, dtype, W, CUFFT_INVERSE, s));
         if (d_part)
-            fourier_unpack_dot<float2><<<dim3(unpack_ctas(vs), nsys), 256, 0, s>>>(
+            { fourier_unpack_dot<float2><<<dim3(unpack_ctas(vs), nsys), 256, 0, s>>>(
                 (const float2*)W, (float2*)z, (const float2*)r, P->twa, P->twb, P->twk, g->X, g->Y, g->Z, vs, d_skip,
-                d_part, unpack_ctas(vs));
+                d_part, unpack_ctas(vs)); note_launch(); }
         else
-            fourier_unpack<float2><<<dim3(nblocks_for(vs), nsys), 256, 0, s>>>((const float2*)W, (float2*)z, P->twa,
+            { fourier_unpack<float2><<<dim3(nblocks_for(vs), nsys), 256, 0, s>>>((const float2*)W, (float2*)z, P->twa,
                                                                               P->twb, P->twk, g->X, g->Y, g->Z, vs,
-                                                                              vs, 1.0, 1);
+                                                                              vs, 1.0, 1); note_launch(); }
     } else {
         fourier_pack<double2><<<nblocks_for(nsys * vs), 256, 0, s>>>((const double2*)r, (double2*)W, P->twa,
                                                                     P->twb, P->twk, g->X, g->Y, g->Z, nsys, vs, vs,
                                                                     1.0, 0);
+        note_launch();
         PC_TRY(exec_fft(plan, dtype, W, CUFFT_FORWARD, s));
         precond_symbol_solve<double2, double><<<dim3(nblocks_for(g->nb / 2), nsys), 256, 0, s>>>(
             (double2*)W, P->d_Aref, P->ea, P->eb, P->egh, d_sys_block, d_skip, g->X, g->Y, g->Z, vs, shift_rho,
             inv_nb);
+        note_launch();
         PC_TRY(exec_fft(plan, dtype, W, CUFFT_INVERSE, s));
         if (d_part)
-            fourier_unpack_dot<double2><<<dim3(unpack_ctas(vs), nsys), 256, 0, s>>>(
+            { fourier_unpack_dot<double2><<<dim3(unpack_ctas(vs), nsys), 256, 0, s>>>(
                 (const double2*)W, (double2*)z, (const double2*)r, P->twa, P->twb, P->twk, g->X, g->Y, g->Z, vs,
-                d_skip, d_part, unpack_ctas(vs));
+                d_skip, d_part, unpack_ctas(vs)); note_launch(); }
         else
-            fourier_unpack<double2><<<dim3(nblocks_for(vs), nsys), 256, 0, s>>>((const double2*)W, (double2*)z,
+            { fourier_unpack<double2><<<dim3(nblocks_for(vs), nsys), 256, 0, s>>>((const double2*)W, (double2*)z,
                                                                                P->twa, P->twb, P->twk, g->X, g->Y,
-                                                                               g->Z, vs, vs, 1.0, 1);
+                                                                               g->Z, vs, vs, 1.0, 1); note_launch(); }
     }
     if (npart_out) *npart_out = unpack_ctas(vs);
     PC_CUDA_TRY(cudaGetLastError());
@@ -512,29 +518,37 @@ int block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* in,
         if (!inverse) {
             fourier_pack<float2><<<gb, 256, 0, s>>>((const float2*)in, (float2*)W, P->twa, P->twb, P->twk, g->X,
                                                      g->Y, g->Z, 1, vs, vs, 1.0, 0);
+            note_launch();
             PC_TRY(exec_fft(plan, dtype, W, CUFFT_FORWARD, s));
             fourier_butterfly<float2><<<gb, 256, 0, s>>>((const float2*)W, (float2*)out, P->ea, P->eb, P->egh,
                                                           g->X, g->Y, g->Z, p12, p13, sc, 0);
+            note_launch();
         } else {
             fourier_butterfly<float2><<<gb, 256, 0, s>>>((const float2*)in, (float2*)W, P->ea, P->eb, P->egh,
                                                           g->X, g->Y, g->Z, p12, p13, 1.0, 1);
+            note_launch();
             PC_TRY(exec_fft(plan, dtype, W, CUFFT_INVERSE, s));
             fourier_unpack<float2><<<dim3(gb, 1), 256, 0, s>>>((const float2*)W, (float2*)out, P->twa, P->twb,
                                                                 P->twk, g->X, g->Y, g->Z, vs, vs, sc, 1);
+            note_launch();
         }
     } else {
         if (!inverse) {
             fourier_pack<double2><<<gb, 256, 0, s>>>((const double2*)in, (double2*)W, P->twa, P->twb, P->twk,
                                                       g->X, g->Y, g->Z, 1, vs, vs, 1.0, 0);
+            note_launch();
             PC_TRY(exec_fft(plan, dtype, W, CUFFT_FORWARD, s));
             fourier_butterfly<double2><<<gb, 256, 0, s>>>((const double2*)W, (double2*)out, P->ea, P->eb, P->egh,
                                                            g->X, g->Y, g->Z, p12, p13, sc, 0);
+            note_launch();
         } else {
             fourier_butterfly<double2><<<gb, 256, 0, s>>>((const double2*)in, (double2*)W, P->ea, P->eb, P->egh,
                                                            g->X, g->Y, g->Z, p12, p13, 1.0, 1);
+            note_launch();
             PC_TRY(exec_fft(plan, dtype, W, CUFFT_INVERSE, s));
             fourier_unpack<double2><<<dim3(gb, 1), 256, 0, s>>>((const double2*)W, (double2*)out, P->twa, P->twb,
                                                                  P->twk, g->X, g->Y, g->Z, vs, vs, sc, 1);
+            note_launch();
         }
     }
     PC_CUDA_TRY(cudaGetLastError());

@@ -96,6 +96,13 @@ inline void make_stencil_params(StencilParams<R>& P, const double Chat[2][36], c
     P.Z = Z;
 }
 
+// Launch accounting (pc_stats): every kernel launch of the library calls note_launch.
+void note_launch(int n = 1);
+void note_apply_launch(int n = 1);
+bool timing_enabled();
+void* timing_begin(cudaStream_t s);
+void timing_end(void* h, cudaStream_t s, int kind, double nodes);
+
 // Per-k rebuild of the preconditioner tables; release of solver workspaces.
 int precond_set_k(pc_grid* g);
 void release_solver_state(pc_grid* g);

@@ -314,19 +314,24 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
         if (!full) return precond_apply(g, dtype, nsys, R, Z, w->blocks, skip, sigma, s, part_c, &nrz);
         const int gb = (int)std::min<int64_t>((nsys * vs + 255) / 256, 152 * 16);
         full_to_blocks<C><<<gb, 256, 0, s>>>(R, static_cast<C*>(Rb), g->N, nsys);
+        note_launch();
         int np = 0;
         PC_TRY(precond_apply(g, dtype, 4 * nsys, Rb, Zb, w->blocks, nullptr, sigma, s, part_c, &np));
         nrz = 4 * np;  // the four block partials of a full system are contiguous
         blocks_to_full<C><<<gb, 256, 0, s>>>(static_cast<C*>(Zb), Z, g->N, nsys);
+        note_launch();
         PC_CUDA_TRY(cudaGetLastError());
         return PC_OK;
     };
 
     pcg_start<C><<<vgrid, 256, 0, s>>>(B, X, R, vs, part_a, npm);
+    note_launch();
     PC_CUDA_TRY(cudaGetLastError());
     PC_TRY(precondition(nullptr));
     pcg_start_reduce<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, vc, part_c, nrz);
+    note_launch();
     pcg_copy<C><<<vgrid, 256, 0, s>>>(Z, P, vs, w->done);
+    note_launch();
     PC_CUDA_TRY(cudaGetLastError());
 
     // stencil items: q_s = (A - sigma M) p_s with Re<p_s, q_s> partials in slot s
@@ -350,11 +355,15 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
         for (int c = 0; c < chunk; ++c, ++it) {
             PC_TRY(grid_apply(g, dtype, full, items.data(), nsys, part_a, npm, s, &cfg));
             pcg_alpha<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, napc);
+            note_launch();
             pcg_update_xr<C><<<vgrid, 256, 0, s>>>(X, R, P, Q, w->sc, w->done, vs, part_b, npm);
+            note_launch();
             PC_CUDA_TRY(cudaGetLastError());
             PC_TRY(precondition(full ? nullptr : w->done));
             pcg_beta<<<nsys, 256, 0, s>>>(w->sc, w->done, part_b, npm, vc, part_c, nrz, tol2, maxit);
+            note_launch();
             pcg_update_p<C><<<vgrid, 256, 0, s>>>(P, Z, w->sc, w->done, vs);
+            note_launch();
             PC_CUDA_TRY(cudaGetLastError());
         }
         PC_CUDA_TRY(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(PcgScal) * nsys, cudaMemcpyDeviceToHost, s));

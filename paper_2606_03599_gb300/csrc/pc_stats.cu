@@ -1,0 +1,109 @@
+// Process-wide launch counters and event timing of the stencil apply.
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "pc_internal.h"
+
+namespace pc {
+
+struct TimedLaunch {
+    cudaEvent_t a, b;
+    int kind;  // 0 = complex64, 1 = complex128
+    double nodes;
+};
+
+static std::atomic<long long> g_launches{0}, g_apply_launches{0};
+static std::atomic<int> g_timing{0};
+static std::mutex g_mu;
+static std::vector<TimedLaunch> g_pending;
+static std::vector<cudaEvent_t> g_pool;
+static long long g_timed[2] = {0, 0};
+static double g_ms[2] = {0, 0}, g_nodes[2] = {0, 0};
+
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void note_apply_launch(int n) { g_apply_launches.fetch_add(n, std::memory_order_relaxed); }
+bool timing_enabled() { return g_timing.load(std::memory_order_relaxed) != 0; }
+
+static cudaEvent_t take_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void* timing_begin(cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    TimedLaunch* t = new TimedLaunch();
+    t->a = take_event();
+    t->b = take_event();
+    cudaEventRecord(t->a, s);
+    return t;
+}
+
+void timing_end(void* h, cudaStream_t s, int kind, double nodes) {
+    TimedLaunch* t = static_cast<TimedLaunch*>(h);
+    cudaEventRecord(t->b, s);
+    t->kind = kind;
+    t->nodes = nodes;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_pending.push_back(*t);
+    delete t;
+}
+
+static void drain() {
+    for (auto& t : g_pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(t.b);
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            g_ms[t.kind] += ms;
+            g_timed[t.kind] += 1;
+            g_nodes[t.kind] += t.nodes;
+        }
+        g_pool.push_back(t.a);
+        g_pool.push_back(t.b);
+    }
+    g_pending.clear();
+}
+
+}  // namespace pc
+
+using namespace pc;
+
+extern "C" {
+
+int pc_stats_timing(int enable) {
+    g_timing.store(enable ? 1 : 0);
+    return PC_OK;
+}
+
+int pc_stats_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    drain();
+    g_launches = 0;
+    g_apply_launches = 0;
+    g_timed[0] = g_timed[1] = 0;
+    g_ms[0] = g_ms[1] = 0;
+    g_nodes[0] = g_nodes[1] = 0;
+    return PC_OK;
+}
+
+int pc_stats_get(pc_stats* out) {
+    if (!out) return fail(PC_EINVAL, "pc_stats_get: null");
+    std::lock_guard<std::mutex> lk(g_mu);
+    drain();
+    out->launches = g_launches.load();
+    out->apply_launches = g_apply_launches.load();
+    for (int k = 0; k < 2; ++k) {
+        out->apply_timed[k] = g_timed[k];
+        out->apply_ms[k] = g_ms[k];
+        out->apply_nodes[k] = g_nodes[k];
+    }
+    return PC_OK;
+}
+
+}  // extern "C"

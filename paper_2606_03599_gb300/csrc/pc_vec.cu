@@ -50,11 +50,11 @@ static int grid_for(int64_t m) {
 int launch_mass(int dtype, const void* x, void* y, const void* mat, int matkind, double rho0,
                 double rho1, int64_t m, cudaStream_t s, int nvec) {
     if (dtype == PC_C64)
-        mass_kernel<float2, float><<<grid_for(m), 256, 0, s>>>((const float2*)x, (float2*)y, mat, matkind,
-                                                              (float)rho0, (float)rho1, m, 3 * nvec);
+        { mass_kernel<float2, float><<<grid_for(m), 256, 0, s>>>((const float2*)x, (float2*)y, mat, matkind,
+                                                              (float)rho0, (float)rho1, m, 3 * nvec); note_launch(); }
     else
-        mass_kernel<double2, double><<<grid_for(m), 256, 0, s>>>((const double2*)x, (double2*)y, mat,
-                                                                matkind, rho0, rho1, m, 3 * nvec);
+        { mass_kernel<double2, double><<<grid_for(m), 256, 0, s>>>((const double2*)x, (double2*)y, mat,
+                                                                matkind, rho0, rho1, m, 3 * nvec); note_launch(); }
     PC_CUDA_TRY(cudaGetLastError());
     return PC_OK;
 }
@@ -62,10 +62,10 @@ int launch_mass(int dtype, const void* x, void* y, const void* mat, int matkind,
 int launch_transfer(int dtype, const void* src, void* dst, int N, int b, int dir, cudaStream_t s) {
     const int64_t n = (int64_t)N * N * N, nb = n / 4;
     if (dtype == PC_C64)
-        transfer_kernel<float2><<<grid_for(nb), 256, 0, s>>>((const float2*)src, (float2*)dst, N, b, dir, nb, n);
+        { transfer_kernel<float2><<<grid_for(nb), 256, 0, s>>>((const float2*)src, (float2*)dst, N, b, dir, nb, n); note_launch(); }
     else
-        transfer_kernel<double2><<<grid_for(nb), 256, 0, s>>>((const double2*)src, (double2*)dst, N, b, dir, nb,
-                                                             n);
+        { transfer_kernel<double2><<<grid_for(nb), 256, 0, s>>>((const double2*)src, (double2*)dst, N, b, dir, nb,
+                                                             n); note_launch(); }
     PC_CUDA_TRY(cudaGetLastError());
     return PC_OK;
 }

@@ -216,6 +216,26 @@ int pc_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_o
 int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const void* const* x,
                    void* const* y, const double* shifts, void* stream);
 
+/* Allocation-free apply with inner product: y = (A_hat - shift M_hat) x on
+ * block b (0..3) or the full space (-1), and *dot = Re <x, y> (x^H y), written
+ * to `dot`, one double of caller-owned DEVICE memory.  The paper has no
+ * counterpart of this call; it exists for callers that must not let a library
+ * allocate device memory -- an application whose GPU memory is already handed
+ * out by its own pool, or a latency-critical loop that cannot afford the
+ * implicit device synchronisation of cudaMalloc/cudaFree.  Its scratch (one
+ * partial sum per CTA) lives in a fixed static device array of 2048 doubles
+ * (16 KiB) that every device loading the library holds until the process
+ * exits; no call allocates or frees.  Limits: at most 2^24 nodes per call
+ * (N <= 406 for a block, N <= 256 for the full space), else PC_EINVAL with the
+ * reason.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls on a device share the array: calls whose
+ * kernels overlap on the GPU race and may return a wrong *dot, so order them
+ * on one stream.  Each call rewrites every slot it reads, so no state carries
+ * over between calls.  Enqueued on `stream`. */
+int pc_block_apply_dot_noalloc(pc_grid* g, int block, int dtype, const void* x, void* y, double shift,
+                               double* dot, void* stream);
+
 /* ---- diagnostics ------------------------------------------------------- */
 
 /* Process-wide counters of the library's own kernel launches (cuFFT and cuBLAS

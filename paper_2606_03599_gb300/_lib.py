@@ -27,7 +27,7 @@ EXPORTED = [
     "pc_block_apply", "pc_block_apply_many", "pc_block_mass", "pc_block_transfer",
     "pc_block_fourier", "pc_shift_invert_pcg", "pc_options_default", "pc_default_sigma",
     "pc_eigs", "pc_last_error", "pc_version", "pc_apply_batch", "pc_stats_timing", "pc_stats_reset",
-    "pc_stats_get",
+    "pc_stats_get", "pc_block_apply_dot_noalloc",
 ]
 
 
@@ -99,6 +99,7 @@ def _load():
         "pc_eigs": ([vp, dp, ci, cd, ctypes.POINTER(c_options), dp, vp, ctypes.POINTER(ci),
                      ctypes.POINTER(c_eigs_info)], ci),
         "pc_apply_batch": ([vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp], ci),
+        "pc_block_apply_dot_noalloc": ([vp, ci, ci, vp, vp, cd, vp, vp], ci),
         "pc_stats_timing": ([ci], ci),
         "pc_stats_reset": ([], ci),
         "pc_stats_get": ([ctypes.POINTER(c_stats)], ci),
@@ -282,6 +283,15 @@ def pc_apply_batch(g, blocks, xs, ys, shifts, stream=None):
     yp = (ctypes.c_void_p * n)(*[_ptr(y) for y in ys])
     sh = (ctypes.c_double * n)(*[float(v) for v in shifts])
     _check(lib.pc_apply_batch(g, _dtype_code(xs[0]), n, bl, xp, yp, sh, _stream(stream)))
+
+
+def pc_block_apply_dot_noalloc(g, block, x, y, dot, shift=0.0, stream=None):
+    """y = (A - shift M) x and dot[0] = Re <x, y> without any device allocation by the library.
+
+    ``dot`` is a caller-owned device tensor holding one float64.
+    """
+    _check(lib.pc_block_apply_dot_noalloc(g, int(block), _dtype_code(x), _ptr(x), _ptr(y), float(shift),
+                                          _ptr(dot), _stream(stream)))
 
 
 def pc_stats_timing(enable):

@@ -1,6 +1,7 @@
 // C ABI: grid lifecycle, Bloch vector, index maps, operator entry points.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -28,8 +29,35 @@ int cuda_fail(cudaError_t e, const char* what) {
 int tile_tx(int shape) { return shape == 0 ? 32 : shape == 1 ? 16 : shape == 2 ? 8 : 4; }
 int tile_ty(int shape) { return shape <= 2 ? 8 : 4; }
 
+static int apply_kernel_mode() {
+    // PC_APPLY_KERNEL=legacy selects the register-staged kernel everywhere (A/B comparisons)
+    static int mode = -1;
+    if (mode < 0) {
+        const char* v = std::getenv("PC_APPLY_KERNEL");
+        mode = (v && std::string(v) == "legacy") ? 1 : 0;
+    }
+    return mode;
+}
+
 ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype) {
     ApplyConfig c;
+    if (apply_kernel_mode() == 0 && X % 2 == 0 && X >= 8 && Y >= 8) {
+        // TMA-staged kernel: 16x16 (complex64) / 16x8 (complex128) tiles, else 8x8
+        c.tma = true;
+        const int tx = X >= 16 ? 16 : 8;
+        const int ty = dtype == PC_C64 ? (Y >= 16 ? 16 : 8) : 8;
+        c.shape = (tx == 16) ? 0 : 1;
+        const int tiles = ((X + tx - 1) / tx) * ((Y + ty - 1) / ty);
+        const long target = 152L * 2;  // two resident CTAs per SM: one full wave
+        long nch = (target + (long)tiles * nitems - 1) / ((long)tiles * nitems);
+        const long maxch = Z / 6 > 0 ? Z / 6 : 1;
+        if (nch > maxch) nch = maxch;
+        if (nch < 1) nch = 1;
+        c.tz = (int)((Z + nch - 1) / nch);
+        c.ctas = tiles * ((Z + c.tz - 1) / c.tz);
+        return c;
+    }
+    c.tma = false;
     // widest tile whose a-extent divides X (no ragged tiles in a); FP64 capped at 16x8
     c.shape = 3;
     const int first = (dtype == PC_C128) ? 1 : 0;
@@ -103,6 +131,7 @@ int pc_grid_destroy(pc_grid* g) {
     cudaFree(g->d_mat_full);
     for (int b = 0; b < 4; ++b) cudaFree(g->d_mat_blk[b]);
     cudaFree(g->d_dot);
+    cudaFree(g->d_err);
     delete g;
     return PC_OK;
 }
@@ -196,7 +225,10 @@ int pc_grid_create(int N, const pc_material* m, pc_grid** out) {
             acc += m->phase ? (double)m->phase[l] : (m->theta ? (double)m->theta[l] : 0.0);
         g->mean_theta = acc / (double)g->n;
     }
-    cudaError_t e = cudaMalloc(&g->d_mat_full, g->n * esz);
+    cudaError_t e = cudaMalloc(&g->d_err, sizeof(int));
+    if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMalloc(error word)"); }
+    cudaMemset(g->d_err, 0, sizeof(int));
+    e = cudaMalloc(&g->d_mat_full, g->n * esz);
     if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMalloc(material)"); }
     e = cudaMemcpy(g->d_mat_full, full.data(), g->n * esz, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMemcpy(material)"); }
@@ -248,15 +280,19 @@ int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nit
         P.X = X;
         P.Y = Y;
         P.Z = Z;
-        rc = launch_apply_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
-                              dot_stride, s);
+        rc = cfg.tma ? launch_apply_tma_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz,
+                                            dot_partials, dot_stride, g->d_err, s)
+                     : launch_apply_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
+                                        dot_stride, s);
     } else {
         StencilParams<double> P = g->P64;
         P.X = X;
         P.Y = Y;
         P.Z = Z;
-        rc = launch_apply_f64(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
-                              dot_stride, s);
+        rc = cfg.tma ? launch_apply_tma_f64(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz,
+                                            dot_partials, dot_stride, g->d_err, s)
+                     : launch_apply_f64(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
+                                        dot_stride, s);
     }
     if (th) timing_end(th, s, dtype == PC_C64 ? 0 : 1, (double)nitems * X * Y * Z);
     return rc;

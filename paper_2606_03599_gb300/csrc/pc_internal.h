@@ -63,11 +63,16 @@ int launch_apply_f32(bool full, bool cubic, int matkind, int shape, const Stenci
                      const ApplyItem* items, int nitems, int tz, double* dp, int ds, cudaStream_t s);
 int launch_apply_f64(bool full, bool cubic, int matkind, int shape, const StencilParams<double>& P,
                      const ApplyItem* items, int nitems, int tz, double* dp, int ds, cudaStream_t s);
+int launch_apply_tma_f32(bool full, bool cubic, int matkind, int shape, const StencilParams<float>& P,
+                         const ApplyItem* items, int nitems, int tz, double* dp, int ds, int* err, cudaStream_t s);
+int launch_apply_tma_f64(bool full, bool cubic, int matkind, int shape, const StencilParams<double>& P,
+                         const ApplyItem* items, int nitems, int tz, double* dp, int ds, int* err, cudaStream_t s);
 
 struct ApplyConfig {
-    int shape;  // tile code
+    int shape;  // tile code (of the TMA kernel when tma, else of the register-staged kernel)
     int tz;     // planes per CTA
     int ctas;   // CTAs per item
+    bool tma;   // TMA-staged kernel (quarter grids of even width >= 8)
 };
 ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype);
 int tile_tx(int shape);
@@ -127,6 +132,7 @@ struct pc_grid {
     bool cubic = true;
     int matkind = 0;  // 0 = uint8 phase ids, 1 = float theta
     double mean_theta = 0.0;  // volume fraction of phase 1
+    int* d_err = nullptr;     // device error word of the TMA kernels (timed-out waits)
     void* d_mat_full = nullptr;
     void* d_mat_blk[4] = {nullptr, nullptr, nullptr, nullptr};
     pc::GridK k;

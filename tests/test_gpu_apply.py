@@ -212,3 +212,41 @@ def test_block_apply_sampled_n160(pc, dtype):
             assert np.abs(got - ref).max() <= TOL[dtype] * scale
     finally:
         g.close()
+
+
+def test_register_staged_and_tma_kernels_agree(pc):
+    """The register-staged kernel (PC_APPLY_KERNEL=legacy, used for odd quarter-grid widths) and
+    the TMA-staged kernel give the same operator on a grid where both apply."""
+    import subprocess
+    import sys
+    import os
+    code = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, %r)
+import paper_2606_03599_gb300 as pc
+from workloads import complex_gaussian, two_phase_sphere
+N = 24
+cell = two_phase_sphere(N, 0.35, 5)
+g = pc.pc_grid_create(N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+pc.pc_set_k(g, [0.3, -0.2, 0.1])
+out = []
+for b in (0, 3, -1):
+    m = N ** 3 // 4 if b >= 0 else N ** 3
+    for dt in (torch.complex128, torch.complex64):
+        x = torch.from_numpy(complex_gaussian(3 * m, 11)).to(dt).cuda()
+        y = torch.empty_like(x)
+        pc.pc_block_apply(g, b, x, y, 0.3)
+        out.append(y.cpu().numpy().astype(np.complex128))
+torch.cuda.synchronize()
+np.save(sys.argv[1], np.concatenate(out))
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for mode in ("legacy", "tma"):
+        path = os.path.join(root, "gpurun_out", "kernel_ab_%s.npy" % mode) if os.path.isdir(
+            os.path.join(root, "gpurun_out")) else "/tmp/kernel_ab_%s.npy" % mode
+        env = dict(os.environ, PC_APPLY_KERNEL=mode)
+        subprocess.run([sys.executable, "-c", code % root, path], check=True, env=env)
+        res[mode] = np.load(path)
+    a, b = res["legacy"], res["tma"]
+    assert np.abs(a - b).max() <= 2e-6 * np.abs(a).max()

@@ -60,6 +60,9 @@ CASES = [
     (4, 0, 2, 3, 1), (4, 3, 2, 3, 4), (4, -1, 2, 3, 3),
     (8, 1, 2, 3, 3), (8, 2, 1, 3, 2), (8, -1, 2, 2, 5), (8, 3, 2, 2, 8),
     (12, 0, 2, 1, 5), (12, 2, 1, 0, 4), (12, -1, 2, 2, 7),
+    # TMA-staged kernel (codes 10: 16x16 / 16x8 tiles, 11: 8x8 tiles)
+    (16, 0, 1, 10, 3), (16, 3, 2, 10, 5), (16, -1, 1, 10, 4), (16, 1, 2, 11, 16),
+    (8, 2, 1, 11, 2), (8, -1, 2, 11, 3), (12, 1, 1, 11, 6), (4, 0, 2, 11, 4), (20, 3, 1, 10, 7),
 ]
 
 
@@ -90,7 +93,7 @@ def test_emulated_kernel_general_lattice_and_fractions(emu, block):
     x = complex_gaussian((3, m), 9)
     ref = (O.apply_block(pb, kappa, block, x, shift=0.5) if block >= 0
            else O.apply_full(pb, kappa, x, shift=0.5))
-    for dtype, shape, tz in ((2, 2, 3), (1, 3, 4)):
+    for dtype, shape, tz in ((2, 2, 3), (1, 3, 4), (2, 11, 5), (1, 10, 3)):
         y = run_emu(emu, pb, block, dtype, shape, tz, kappa, x, 0.5, 1)
         err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
         assert err < (1e-13 if dtype == 2 else 2e-6)

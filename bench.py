@@ -278,6 +278,52 @@ def profile_run(what):
     pc.pc_grid_destroy(g)
 
 
+def precision_run(args):
+    """N = 160 two-phase cell (R = 0.3, seed 3), Gamma/X/M/R and four midpoints, 20 bands at 1e-8:
+    mixed precision s/k-point, and per-band relative error against the FP64 path on the first k-point."""
+    import numpy as np
+    import torch
+    import paper_2606_03599_gb300 as pc
+    from workloads import config_cell, sc_eight_points
+    cell = config_cell("precision")
+    kpts = sc_eight_points()
+    g = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+    stream = torch.cuda.Stream()
+    om = pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED)
+    om.stream = stream.cuda_stream
+    nk = max(1, min(args.steps, len(kpts)))
+    res = []
+    for i in range(nk):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ev, bl, info = pc.pc_eigs(g, kpts[i], NEV, opt=om)
+        e1.record(stream)
+        e1.synchronize()
+        res.append((e0.elapsed_time(e1) / 1e3, ev, info))
+    o64 = pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_FP64)
+    o64.stream = stream.cuda_stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ev64, _, info64 = pc.pc_eigs(g, kpts[0], NEV, opt=o64)
+    e1.record(stream)
+    e1.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    per_band = (np.abs(res[0][1] - ev64) / ev64).tolist()
+    pc.pc_grid_destroy(g)
+    line = {"metric": METRIC, "mode": "precision", "unit": "s/k-point", "dtype": "mixed c64/f64",
+            "config": {"workload": "two-phase SC cell N=160 (R=0.3, seed 3), 20 bands, resid 1e-8",
+                       "k_points": nk},
+            "mixed_s_per_kpoint": float(np.mean([r[0] for r in res])),
+            "fp64_s_per_kpoint_first_k": t64,
+            "per_band_rel_err_vs_fp64_first_k": per_band,
+            "max_true_rel_resid_mixed": max(r[2]["max_rel_resid"] for r in res),
+            "pcg_iters_per_kpoint_mixed": float(np.mean([r[2]["pcg_iters"] for r in res])),
+            "pcg_iters_fp64_first_k": info64["pcg_iters"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -285,6 +331,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--precision", action="store_true",
+                    help="run the N=160 precision workload (8 k-points, 20 bands, mixed precision) instead")
     ap.add_argument("--profile", default=None, choices=["kpoint", "kpoint-mixed", "apply-c64", "apply-c128"],
                     help="profiling aid for ncu: run only one k-point solve of the workload, or one "
                          "N=160 four-block apply (after two untimed ones), and print nothing else")
@@ -294,6 +342,9 @@ def main():
         return
     if args.profile:
         profile_run(args.profile)
+        return
+    if args.precision:
+        precision_run(args)
         return
     args.warmup = max(3, args.warmup)
 
@@ -330,7 +381,7 @@ def main():
     pc.pc_stats_timing(1)
     barrier(world)
     torch.cuda.synchronize()
-    step_ms, infos, residuals = [], [], []
+    step_ms, infos, residuals, evals = [], [], [], []
     for s in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(float(s))  # L2 flush between timed steps (not timed)
@@ -343,6 +394,7 @@ def main():
         step_ms.append(e0.elapsed_time(e1))
         infos.append(info)
         residuals.append(info["max_rel_resid"])
+        evals.append(ev)
     torch.cuda.synchronize()
     barrier(world)
     st = pc.pc_stats_get()
@@ -384,6 +436,28 @@ def main():
         e2e = {"value": float(np.mean(e2e_ms)) / 1e3, "unit": "s/k-point", "h2d_bytes_per_step": 2 * n,
                "d2h_bytes_per_step": NEV * 8, "steps": len(e2e_ms)}
 
+    # same k-points: mixed precision (complex64 inner PCG + FP64 refinement) and the full-space
+    # FP64 solve, for the blocked-vs-full and FP64-vs-mixed comparisons on this GPU
+    compare = None
+    if rank == 0:
+        compare = {}
+        nk = min(args.steps, 3)
+        for name, o2 in (("mixed", pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED)),
+                         ("full_space_fp64", pc.pc_options_default(tol=TOL, full_space=1))):
+            o2.stream = stream.cuda_stream
+            ms, err = [], 0.0
+            for s in range(nk):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ev2, _, inf2 = pc.pc_eigs(g, kpoint(args.warmup + s), NEV, opt=o2)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                err = max(err, float(np.max(np.abs(ev2 - evals[s]) / evals[s])))
+            compare[name] = {"s_per_kpoint": float(np.mean(ms)) / 1e3, "k_points": nk,
+                             "max_rel_diff_vs_blocked_fp64": err}
+
     apply = apply_throughput(pc, torch) if rank == 0 else None
     pc.pc_grid_destroy(g)
 
@@ -405,6 +479,7 @@ def main():
                    "l2": "512 MB buffer written between timed steps (L2 = 129 MB)"},
         "roofline": roofline,
         "apply": apply,
+        "compare_same_gpu": compare,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": st["launches"],

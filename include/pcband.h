@@ -98,7 +98,7 @@ typedef struct {
     double inner_tol;    /* relative residual of each shift-invert solve; default 1e-10 */
     int precision;       /* PC_PREC_FP64 or PC_PREC_MIXED */
     int full_space;      /* 0: four parity blocks merged (default); 1: one full-space solve */
-    int block_size;      /* Krylov block width per parity block; default 4 */
+    int block_size;      /* Krylov block width per parity block; default 2 */
     int max_basis;       /* Krylov-Schur basis size before restart; default 32 */
     int max_restarts;    /* outer iteration cap; default 60 */
     int inner_maxit;     /* PCG iteration cap per solve; default 400 */

@@ -41,12 +41,15 @@ static int apply_kernel_mode() {
 
 ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype) {
     ApplyConfig c;
-    if (apply_kernel_mode() == 0 && X % 2 == 0 && X >= 8 && Y >= 8) {
-        // TMA-staged kernel: 16x16 (complex64) / 16x8 (complex128) tiles, else 8x8
+    if (apply_kernel_mode() == 0 && dtype == PC_C64 && X % 2 == 0 && X >= 8 && Y >= 8) {
+        // TMA-staged kernel for complex64 (complex128 is FP64-ALU-bound on GB300 and runs faster on
+        // the register-staged kernel): 16x16 tiles, else 8x8
         c.tma = true;
-        const int tx = X >= 16 ? 16 : 8;
-        const int ty = dtype == PC_C64 ? (Y >= 16 ? 16 : 8) : 8;
+        // prefer a tile width that divides X (no idle columns); 16 when both do
+        const int tx = (X % 16 == 0) ? 16 : (X % 8 == 0 ? 8 : (X >= 16 ? 16 : 8));
         c.shape = (tx == 16) ? 0 : 1;
+        // tile height follows the shape code of launch_tma_shape: 16x16 / 16x8 or 8x8
+        const int ty = (c.shape == 0 && dtype == PC_C64) ? 16 : 8;
         const int tiles = ((X + tx - 1) / tx) * ((Y + ty - 1) / ty);
         const long target = 152L * 2;  // two resident CTAs per SM: one full wave
         long nch = (target + (long)tiles * nitems - 1) / ((long)tiles * nitems);

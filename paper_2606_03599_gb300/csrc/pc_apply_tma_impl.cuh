@@ -203,6 +203,8 @@ static int launch_tma_tile(const StencilParams<R>& P, const ApplyItem* items, in
     }
     const int ntx = (P.X + TX - 1) / TX, nty = (P.Y + TY - 1) / TY;
     const int nch = (P.Z + tz - 1) / tz;
+    if (dot_partials != nullptr && ntx * nty * nch > dot_stride)
+        return fail(PC_EINVAL, "apply: launch has more CTAs than partial-sum slots");
     for (int base = 0; base < nitems; base += kTmaMaxItems) {
         TmaBatch B;
         B.n = nitems - base < kTmaMaxItems ? nitems - base : kTmaMaxItems;

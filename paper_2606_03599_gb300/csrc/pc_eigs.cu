@@ -31,7 +31,9 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "pc_complex.cuh"
@@ -678,6 +680,10 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
     } sg{E.s, own_stream};
     if (!SV->blas) {
         if (cublasCreate(&SV->blas) != CUBLAS_STATUS_SUCCESS) return fail(PC_ECUDA, "cublasCreate failed");
+        // FP64 GEMMs of the orthogonalisation and Rayleigh-Ritz steps may run on cuBLAS's fixed-point
+        // emulation of FP64 (tensor cores), which keeps FP64 accuracy; PC_GEMM_EMULATION=0 turns it off.
+        const char* em = std::getenv("PC_GEMM_EMULATION");
+        if (!(em && std::string(em) == "0")) cublasSetMathMode(SV->blas, CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH);
     }
     E.blas = SV->blas;
     cublasSetStream(E.blas, E.s);
@@ -861,7 +867,7 @@ int pc_options_default(pc_options* o) {
     o->inner_tol = 1e-10;
     o->precision = PC_PREC_FP64;
     o->full_space = 0;
-    o->block_size = 4;
+    o->block_size = 2;
     o->max_basis = 32;
     o->max_restarts = 60;
     o->inner_maxit = 400;

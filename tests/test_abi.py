@@ -51,7 +51,7 @@ def test_block_index_rejects_bad_arguments(pc):
 
 def test_options_defaults(pc):
     o = pc.pc_options_default()
-    assert o.tol == 1e-8 and o.block_size == 4 and o.precision == pc.PC_PREC_FP64
+    assert o.tol == 1e-8 and o.block_size == 2 and o.precision == pc.PC_PREC_FP64
 
 
 def test_null_grid_is_rejected(pc):

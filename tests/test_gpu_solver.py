@@ -68,9 +68,9 @@ def test_block_fourier_matches_dense_basis(pc, N, dtype):
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 @pytest.mark.parametrize("kappa", [[0.3, 0.1, 0.2], [0.0, 0.0, 0.0]])
-def test_shift_invert_pcg_residual(pc, dtype, kappa):
+@pytest.mark.parametrize("N", [16, 24, 48])
+def test_shift_invert_pcg_residual(pc, dtype, kappa, N):
     import torch
-    N = 16
     g = Grid(pc, two_phase_sphere(N, 0.35, 2))
     td = torch.complex128 if dtype == "c128" else torch.complex64
     tol = 1e-10 if dtype == "c128" else 1e-5

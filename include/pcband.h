@@ -236,6 +236,25 @@ int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const vo
 int pc_block_apply_dot_noalloc(pc_grid* g, int block, int dtype, const void* x, void* y, double shift,
                                double* dot, void* stream);
 
+/* ---- differentiation --------------------------------------------------- */
+
+/* Eigenvalue gradients with respect to the nodewise material (Hellmann-Feynman
+ * for the pencil of Eq. discrete_GEP_main): for eigenpairs (lambda_v, x_v) with
+ * x_v^H M_hat x_v = 1 (as pc_eigs returns them), accumulates
+ *   dC[q][l]  += sum_v w_v d lambda_v / d C_l[p][r]   (q over the 21 upper-
+ *                triangular entries (p <= r) in row order of the Voigt matrix,
+ *                Pa^-1 x rad^2/s^2; off-diagonal entries count both C[p][r] and C[r][p])
+ *   drho[l]   += sum_v w_v d lambda_v / d rho_l       (per kg/m^3)
+ * with d lambda/d C_l[p][r] = Re(conj(e_p) e_r)(2 if p != r) for the strain
+ * e = B^H x at node l, and d lambda / d rho_l = -lambda sum_alpha |x_alpha(l)|^2.
+ * X: nvec device complex128 vectors of block `block` (0..3) or of the full space
+ * (-1), at the Bloch vector last set on g; lambdas (SI) and weights: host arrays.
+ * dC: device FP64 [21][N^3], drho: device FP64 [N^3], full-grid node order; the
+ * call adds to them.  For a degenerate cluster pass all of its vectors with one
+ * common weight (the gradient of the cluster's sum is basis independent). */
+int pc_eig_grad(pc_grid* g, int block, int nvec, const void* X, const double* lambdas, const double* weights,
+                double* dC, double* drho, void* stream);
+
 /* ---- diagnostics ------------------------------------------------------- */
 
 /* Process-wide counters of the library's own kernel launches (cuFFT and cuBLAS

@@ -92,16 +92,22 @@ class Problem:
     C: np.ndarray  # (2,6,6)
     rho: np.ndarray  # (2,)
     theta: np.ndarray  # (n,) float64 in [0,1]
+    C_nodes: np.ndarray | None = None  # optional (n,6,6) nodewise stiffness replacing the two-phase rule
+    rho_nodes: np.ndarray | None = None  # optional (n,) nodewise density
 
     @property
     def n(self):
         return int(np.prod(self.dims))
 
     def node_C(self):
+        if self.C_nodes is not None:
+            return self.C_nodes
         t = self.theta[:, None, None]
         return (1.0 - t) * self.C[0][None] + t * self.C[1][None]
 
     def node_rho(self):
+        if self.rho_nodes is not None:
+            return self.rho_nodes
         return (1.0 - self.theta) * self.rho[0] + self.theta * self.rho[1]
 
 
@@ -243,6 +249,20 @@ def dense_eigvals(pb: Problem, kappa, b=None) -> np.ndarray:
     Ad = A.toarray()
     Ad = 0.5 * (Ad + Ad.conj().T)
     return scipy.linalg.eigh(Ad, M.toarray(), eigvals_only=True)
+
+
+def dense_eigpairs(pb: Problem, kappa, b=None):
+    """All eigenpairs of (A, M) (scipy.linalg.eigh): ascending values and M-normalised vectors as
+    full-space (count, 3, n) arrays (block vectors injected with Q_sigma)."""
+    A, M = sparse_pencil(pb, kappa, b)
+    Ad = A.toarray()
+    Ad = 0.5 * (Ad + Ad.conj().T)
+    w, Z = scipy.linalg.eigh(Ad, M.toarray())
+    if b is None:
+        X = Z.T.reshape(-1, 3, pb.n)
+    else:
+        X = np.stack([inject(pb, b, Z[:, j]) for j in range(Z.shape[1])])
+    return w, X
 
 
 def zero_mode_count(evals, rel: float = 1e-9) -> int:
@@ -472,6 +492,12 @@ def merge_complete(block_vals, block_complete_upto, nev: int):
 
 
 # --------------------------------------------------------------------------- Hellmann-Feynman gradients
+def upper21(g66):
+    """(n,6,6) -> (n,21): the independent upper-triangular entries (p <= r), row order."""
+    iu = np.triu_indices(6)
+    return g66[:, iu[0], iu[1]]
+
+
 def eigpair_gradients(pb: Problem, kappa, x_full, lam):
     """d lambda / d C_i[p][q] and d lambda / d rho_i for an M-normalised eigenvector x.
 

@@ -27,7 +27,7 @@ EXPORTED = [
     "pc_block_apply", "pc_block_apply_many", "pc_block_mass", "pc_block_transfer",
     "pc_block_fourier", "pc_shift_invert_pcg", "pc_options_default", "pc_default_sigma",
     "pc_eigs", "pc_last_error", "pc_version", "pc_apply_batch", "pc_stats_timing", "pc_stats_reset",
-    "pc_stats_get", "pc_block_apply_dot_noalloc",
+    "pc_stats_get", "pc_block_apply_dot_noalloc", "pc_eig_grad",
 ]
 
 
@@ -100,6 +100,7 @@ def _load():
                      ctypes.POINTER(c_eigs_info)], ci),
         "pc_apply_batch": ([vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp], ci),
         "pc_block_apply_dot_noalloc": ([vp, ci, ci, vp, vp, cd, vp, vp], ci),
+        "pc_eig_grad": ([vp, ci, ci, vp, dp, dp, vp, vp, vp], ci),
         "pc_stats_timing": ([ci], ci),
         "pc_stats_reset": ([], ci),
         "pc_stats_get": ([ctypes.POINTER(c_stats)], ci),
@@ -292,6 +293,16 @@ def pc_block_apply_dot_noalloc(g, block, x, y, dot, shift=0.0, stream=None):
     """
     _check(lib.pc_block_apply_dot_noalloc(g, int(block), _dtype_code(x), _ptr(x), _ptr(y), float(shift),
                                           _ptr(dot), _stream(stream)))
+
+
+def pc_eig_grad(g, block, X, lambdas, weights, dC, drho, stream=None):
+    """Accumulate weighted eigenvalue gradients into dC ([21, n] float64 device) and drho ([n])."""
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    _check(lib.pc_eig_grad(g, int(block), int(lam.size), _ptr(X),
+                           lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(dC), _ptr(drho),
+                           _stream(stream)))
 
 
 def pc_stats_timing(enable):

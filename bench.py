@@ -43,7 +43,7 @@ NEV = 20
 TOL = 1e-8
 # algorithmic cost of one stencil apply per node (cubic lattice, binary material):
 #   bytes: read x (3 complex) + write y (3 complex) + 1 material byte
-#   flops: 294 real flops (see DESIGN.md: differences, reconstruction, 6x6 stiffness, fluxes, gather, shift)
+#   flops: 294 real flops (differences, reconstruction, 6x6 stiffness, fluxes, gather, shift)
 BYTES_PER_NODE = {"c64": 3 * 8 * 2 + 1, "c128": 3 * 16 * 2 + 1}
 FLOPS_PER_NODE = 294
 

@@ -220,6 +220,7 @@ def test_register_staged_and_tma_kernels_agree(pc):
     import subprocess
     import sys
     import os
+    import tempfile
     code = r'''
 import sys, numpy as np, torch
 sys.path.insert(0, %r)
@@ -242,9 +243,9 @@ np.save(sys.argv[1], np.concatenate(out))
 '''
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     res = {}
+    tmp = tempfile.mkdtemp()
     for mode in ("legacy", "tma"):
-        path = os.path.join(root, "gpurun_out", "kernel_ab_%s.npy" % mode) if os.path.isdir(
-            os.path.join(root, "gpurun_out")) else "/tmp/kernel_ab_%s.npy" % mode
+        path = os.path.join(tmp, "kernel_ab_%s.npy" % mode)
         env = dict(os.environ, PC_APPLY_KERNEL=mode)
         subprocess.run([sys.executable, "-c", code % root, path], check=True, env=env)
         res[mode] = np.load(path)

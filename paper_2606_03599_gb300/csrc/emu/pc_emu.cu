@@ -10,6 +10,7 @@
 
 #include "../pc_apply_tile.cuh"
 #include "../pc_apply_tma.cuh"
+#include "../pc_apply_row.cuh"
 
 using namespace pc;
 
@@ -108,6 +109,91 @@ static void emu_run_tma(const StencilParams<R>& P, int block, const void* x, voi
     delete sh;
 }
 
+// Same segment and step sequence as apply_row_kernel (complex64 parity blocks) with `ctas`
+// persistent CTAs; the bulk copies are modelled as immediate copies of the same rows.
+template <bool CUBIC, int MATK, int XC>
+static void emu_run_row(const StencilParams<float>& P, int block, const void* x, void* y, const void* mat,
+                        double shift, int ctas) {
+    using T = RowTile<CUBIC, MATK, XC>;
+    const RowGeom G = make_row_geom(P.X, P.Y, P.Z, MATK);
+    if (XC > 0 && (G.X != XC || G.Y != XC)) {
+        std::fprintf(stderr, "compile-time width %d does not match the grid\n", XC);
+        std::abort();
+    }
+    const uint32_t NS = (uint32_t)G.ns;
+    // row-padded material copy
+    std::vector<unsigned char> matp((size_t)G.Xp * G.Y * G.Z * G.matsz, 0);
+    for (int64_t row = 0; row < (int64_t)G.Y * G.Z; ++row)
+        std::memcpy(&matp[(size_t)row * G.Xp * G.matsz],
+                    static_cast<const unsigned char*>(mat) + (size_t)row * G.X * G.matsz, (size_t)G.X * G.matsz);
+    std::vector<unsigned char> smem(G.total);
+    typename T::Sh sh{smem.data(), &G};
+    std::vector<typename T::Regs> regs(G.NT);
+    const int64_t W = (int64_t)G.nt * G.Z;  // one item
+    for (int cta = 0; cta < ctas; ++cta) {
+        std::memset(smem.data(), 0xFF, smem.size());  // poison: reads of unwritten cells show up as NaN
+        for (int t = 0; t < G.NT; ++t) T::load_tables(P, sh, t, G.NT);
+        for (int t = 0; t < G.NT; ++t) T::init(G, t, regs[t]);
+        const int64_t u0 = (int64_t)cta * W / ctas, u1 = (int64_t)(cta + 1) * W / ctas;
+        uint32_t gseq = 0;
+        for (int64_t u = u0; u < u1;) {
+            int item, tile, ks, ke;
+            row_seg_at(G, u, u1, item, tile, ks, ke);
+            u += ke - ks;
+            PC_IDX(item, 1);
+            RowSeg S;
+            S.item = item;
+            S.b0 = row_tile_lo(G, tile);
+            S.V = row_tile_lo(G, tile + 1) - S.b0;
+            if (S.V < 1 || S.V > G.TY) {
+                std::fprintf(stderr, "bad tile height %d\n", S.V);
+                std::abort();
+            }
+            S.ks = ks;
+            S.ke = ke;
+            S.p12 = block >> 1;
+            S.p13 = block & 1;
+            S.x = static_cast<const float2*>(x);
+            S.y = static_cast<float2*>(y);
+            S.mat = matp.data();
+            S.shift = (float)shift;
+            for (int t = 0; t < G.NT; ++t) T::seg_begin(regs[t]);
+            const int kfirst = ks - 2;
+            auto slot_of = [&](int kp) { return (int)((gseq + (uint32_t)(kp - kfirst)) % NS); };
+            for (int kp = kfirst; kp <= ke + 1 && kp < kfirst + (int)NS; ++kp)
+                T::host_copy_plane(G, S, sh, slot_of(kp), kp);
+            for (int kp = kfirst; kp <= ks; ++kp)
+                for (int t = 0; t < G.NT; ++t) T::fix_plane(P, G, S, sh, slot_of(kp), kp, t);
+            for (int kf = ks - 1; kf <= ke; ++kf) {
+                for (int t = 0; t < G.NT; ++t) {
+                    if (kf > ks - 1) T::gather(P, G, S, sh, regs[t], kf - 1, (kf - 1) & 1);
+                    T::flux(P, G, S, sh, regs[t], kf, slot_of(kf - 1), slot_of(kf), slot_of(kf + 1), kf & 1);
+                }
+                if (kf + 2 <= ke + 1)
+                    for (int t = 0; t < G.NT; ++t) T::fix_plane(P, G, S, sh, slot_of(kf + 2), kf + 2, t);
+                if (kf - 1 >= kfirst && kf - 1 + (int)NS <= ke + 1)
+                    T::host_copy_plane(G, S, sh, slot_of(kf - 1 + (int)NS), kf - 1 + (int)NS);
+            }
+            for (int t = 0; t < G.NT; ++t) T::gather(P, G, S, sh, regs[t], ke, ke & 1);
+            gseq += (uint32_t)(ke - ks + 4);
+        }
+    }
+}
+
+template <bool CUBIC, int MATK>
+static void emu_row_x(const StencilParams<float>& P, int block, const void* x, void* y, const void* mat,
+                      double shift, int ctas, bool ct) {
+    if (ct && MATK == 0 && P.X == P.Y) {
+        switch (P.X) {
+            case 16: return emu_run_row<CUBIC, MATK, 16>(P, block, x, y, mat, shift, ctas);
+            case 24: return emu_run_row<CUBIC, MATK, 24>(P, block, x, y, mat, shift, ctas);
+            case 32: return emu_run_row<CUBIC, MATK, 32>(P, block, x, y, mat, shift, ctas);
+            default: break;
+        }
+    }
+    emu_run_row<CUBIC, MATK, 0>(P, block, x, y, mat, shift, ctas);
+}
+
 template <typename R, bool FULL, bool CUBIC, int MATK>
 static int emu_shape(int shape, const StencilParams<R>& P, int block, const void* x, void* y, const void* mat,
                      double shift, int tz) {
@@ -148,6 +234,18 @@ extern "C" int pc_emu_apply(int N, int block, int dtype, int shape, int tz, cons
     if (dtype == PC_C64) {
         StencilParams<float> P;
         make_stencil_params(P, Chat, rhohat2, ainv9, cubic != 0, N, phi3, X, Y, Z);
+        if (shape == 20 || shape == 21) {  // row-tile kernel (21: compile-time width), tz = persistent CTAs
+            if (full) return -1;
+            const bool ct = shape == 21;
+            if (cubic) {
+                if (matkind) emu_row_x<true, 1>(P, block, x, y, mat, shift, tz, ct);
+                else emu_row_x<true, 0>(P, block, x, y, mat, shift, tz, ct);
+            } else {
+                if (matkind) emu_row_x<false, 1>(P, block, x, y, mat, shift, tz, ct);
+                else emu_row_x<false, 0>(P, block, x, y, mat, shift, tz, ct);
+            }
+            return 0;
+        }
         return emu_t<float>(shape, P, full, cubic != 0, matkind, block, x, y, mat, shift, tz);
     }
     StencilParams<double> P;

@@ -30,18 +30,43 @@ int tile_tx(int shape) { return shape == 0 ? 32 : shape == 1 ? 16 : shape == 2 ?
 int tile_ty(int shape) { return shape <= 2 ? 8 : 4; }
 
 static int apply_kernel_mode() {
-    // PC_APPLY_KERNEL=legacy selects the register-staged kernel everywhere (A/B comparisons)
+    // PC_APPLY_KERNEL=legacy selects the register-staged kernel everywhere, =tma the TMA tile
+    // kernel in place of the row kernel (A/B comparisons)
     static int mode = -1;
     if (mode < 0) {
         const char* v = std::getenv("PC_APPLY_KERNEL");
-        mode = (v && std::string(v) == "legacy") ? 1 : 0;
+        mode = (v && std::string(v) == "legacy") ? 1 : ((v && std::string(v) == "tma") ? 2 : 0);
     }
     return mode;
 }
 
-ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype) {
+bool row_geom_fits(int X, int Y, int Z, int matkind);
+
+int device_sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) ==
+                                                      cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 152;
+    }
+    return n;
+}
+
+ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool blocks, int matkind) {
     ApplyConfig c;
-    if (apply_kernel_mode() == 0 && dtype == PC_C64 && X % 2 == 0 && X >= 8 && Y >= 8) {
+    if (apply_kernel_mode() == 0 && blocks && dtype == PC_C64 && X % 2 == 0 && row_geom_fits(X, Y, Z, matkind)) {
+        // row-tile kernel: persistent, whole rows per tile
+        c.row = true;
+        c.tma = false;
+        c.shape = 0;
+        c.tz = 0;
+        c.ctas = row_apply_ctas(X, Y, Z, matkind, nitems);
+        return c;
+    }
+    if (apply_kernel_mode() != 1 && dtype == PC_C64 && X % 2 == 0 && X >= 8 && Y >= 8) {
         // TMA-staged kernel for complex64 (complex128 is FP64-ALU-bound on GB300 and runs faster on
         // the register-staged kernel): 16x16 tiles, else 8x8
         c.tma = true;
@@ -133,6 +158,7 @@ int pc_grid_destroy(pc_grid* g) {
     release_solver_state(g);
     cudaFree(g->d_mat_full);
     for (int b = 0; b < 4; ++b) cudaFree(g->d_mat_blk[b]);
+    for (int b = 0; b < 4; ++b) cudaFree(g->d_mat_row[b]);
     cudaFree(g->d_dot);
     cudaFree(g->d_err);
     delete g;
@@ -244,6 +270,16 @@ int pc_grid_create(int N, const pc_material* m, pc_grid** out) {
         if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMalloc(block material)"); }
         e = cudaMemcpy(g->d_mat_blk[b], blk.data(), g->nb * esz, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMemcpy(block material)"); }
+        // row-padded copy for the row-tile kernel: every quarter-grid row starts on a 16-byte boundary
+        const int q = (int)(16 / esz);
+        g->mat_pitch = (g->X + q - 1) / q * q;
+        e = cudaMalloc(&g->d_mat_row[b], (size_t)g->mat_pitch * g->Y * g->Z * esz);
+        if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMalloc(row material)"); }
+        e = cudaMemset(g->d_mat_row[b], 0, (size_t)g->mat_pitch * g->Y * g->Z * esz);
+        if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMemset(row material)"); }
+        e = cudaMemcpy2D(g->d_mat_row[b], (size_t)g->mat_pitch * esz, blk.data(), (size_t)g->X * esz,
+                         (size_t)g->X * esz, (size_t)g->Y * g->Z, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMemcpy2D(row material)"); }
     }
     fill_params(g);
     *out = g;
@@ -275,10 +311,19 @@ namespace pc {
 int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nitems, double* dot_partials,
                int dot_stride, cudaStream_t s, const ApplyConfig* cfg_in) {
     const int X = full ? g->N : g->X, Y = full ? g->N : g->Y, Z = g->Z;
-    ApplyConfig cfg = cfg_in ? *cfg_in : choose_apply_config(X, Y, Z, nitems, dtype);
+    ApplyConfig cfg = cfg_in ? *cfg_in : choose_apply_config(X, Y, Z, nitems, dtype, !full, g->matkind);
     void* th = timing_enabled() ? timing_begin(s) : nullptr;
     int rc;
-    if (dtype == PC_C64) {
+    if (dtype == PC_C64 && cfg.row) {
+        StencilParams<float> P = g->P32;
+        P.X = X;
+        P.Y = Y;
+        P.Z = Z;
+        std::vector<const void*> mats(nitems);
+        for (int i = 0; i < nitems; ++i) mats[i] = items[i].block >= 0 ? g->d_mat_row[items[i].block] : nullptr;
+        rc = launch_apply_row_f32(g->cubic, g->matkind, P, items, mats.data(), nitems, cfg.ctas, dot_partials,
+                                  dot_stride, g->d_err, s);
+    } else if (dtype == PC_C64) {
         StencilParams<float> P = g->P32;
         P.X = X;
         P.Y = Y;

@@ -65,16 +65,22 @@ int launch_apply_f64(bool full, bool cubic, int matkind, int shape, const Stenci
                      const ApplyItem* items, int nitems, int tz, double* dp, int ds, cudaStream_t s);
 int launch_apply_tma_f32(bool full, bool cubic, int matkind, int shape, const StencilParams<float>& P,
                          const ApplyItem* items, int nitems, int tz, double* dp, int ds, int* err, cudaStream_t s);
+// Row-tile kernel (complex64 parity blocks): mats = row-padded material per item; ctas = persistent CTAs.
+int launch_apply_row_f32(bool cubic, int matkind, const StencilParams<float>& P, const ApplyItem* items,
+                         const void* const* mats, int nitems, int ctas, double* dp, int ds, int* err, cudaStream_t s);
+int row_apply_ctas(int X, int Y, int Z, int matkind, int nitems);
+int device_sm_count();
 int launch_apply_tma_f64(bool full, bool cubic, int matkind, int shape, const StencilParams<double>& P,
                          const ApplyItem* items, int nitems, int tz, double* dp, int ds, int* err, cudaStream_t s);
 
 struct ApplyConfig {
     int shape;  // tile code (of the TMA kernel when tma, else of the register-staged kernel)
     int tz;     // planes per CTA
-    int ctas;   // CTAs per item
+    int ctas;   // CTAs per item (row kernel: CTAs of the persistent launch)
     bool tma;   // TMA-staged kernel (quarter grids of even width >= 8)
+    bool row = false;  // row-tile kernel (complex64 parity blocks, X even)
 };
-ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype);
+ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool blocks = false, int matkind = 0);
 int tile_tx(int shape);
 int tile_ty(int shape);
 
@@ -135,6 +141,8 @@ struct pc_grid {
     int* d_err = nullptr;     // device error word of the TMA kernels (timed-out waits)
     void* d_mat_full = nullptr;
     void* d_mat_blk[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* d_mat_row[4] = {nullptr, nullptr, nullptr, nullptr};  // block material, rows padded to 16 bytes
+    int mat_pitch = 0;                                          // elements per padded row
     pc::GridK k;
     pc::StencilParams<double> P64;
     pc::StencilParams<float> P32;

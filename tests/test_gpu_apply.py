@@ -214,9 +214,10 @@ def test_block_apply_sampled_n160(pc, dtype):
         g.close()
 
 
-def test_register_staged_and_tma_kernels_agree(pc):
-    """The register-staged kernel (PC_APPLY_KERNEL=legacy, used for odd quarter-grid widths) and
-    the TMA-staged kernel give the same operator on a grid where both apply."""
+def test_register_staged_tma_and_row_kernels_agree(pc):
+    """The register-staged kernel (PC_APPLY_KERNEL=legacy, used for odd quarter-grid widths), the
+    TMA tile kernel (PC_APPLY_KERNEL=tma) and the row-tile kernel (default for complex64 blocks)
+    give the same operator on a grid where all three apply."""
     import subprocess
     import sys
     import os
@@ -244,10 +245,11 @@ np.save(sys.argv[1], np.concatenate(out))
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     res = {}
     tmp = tempfile.mkdtemp()
-    for mode in ("legacy", "tma"):
+    for mode in ("legacy", "tma", "row"):
         path = os.path.join(tmp, "kernel_ab_%s.npy" % mode)
         env = dict(os.environ, PC_APPLY_KERNEL=mode)
         subprocess.run([sys.executable, "-c", code % root, path], check=True, env=env)
         res[mode] = np.load(path)
-    a, b = res["legacy"], res["tma"]
-    assert np.abs(a - b).max() <= 2e-6 * np.abs(a).max()
+    a = res["legacy"]
+    for mode in ("tma", "row"):
+        assert np.abs(a - res[mode]).max() <= 2e-6 * np.abs(a).max(), mode

@@ -63,6 +63,13 @@ CASES = [
     # TMA-staged kernel (codes 10: 16x16 / 16x8 tiles, 11: 8x8 tiles)
     (16, 0, 1, 10, 3), (16, 3, 2, 10, 5), (16, -1, 1, 10, 4), (16, 1, 2, 11, 16),
     (8, 2, 1, 11, 2), (8, -1, 2, 11, 3), (12, 1, 1, 11, 6), (4, 0, 2, 11, 4), (20, 3, 1, 10, 7),
+    # row-tile kernel (code 20, complex64 blocks; tz = persistent CTAs): single tile with both row
+    # wraps, several tiles (N >= 48), ragged tile heights (N = 68: 11, 11, 12 rows), CTA ranges that
+    # split tiles, and more CTAs than planes
+    (4, 0, 1, 20, 1), (4, 3, 1, 20, 5), (8, 1, 1, 20, 3), (8, 2, 1, 20, 64), (12, 3, 1, 20, 7),
+    (16, 0, 1, 20, 2), (20, 2, 1, 20, 9), (48, 1, 1, 20, 13), (56, 3, 1, 20, 40), (68, 0, 1, 20, 17),
+    # row-tile kernel with compile-time widths (code 21): X = 16, 24, 32 (N = 32, 48, 64)
+    (32, 2, 1, 21, 5), (48, 0, 1, 21, 152), (64, 3, 1, 21, 31),
 ]
 
 
@@ -93,7 +100,9 @@ def test_emulated_kernel_general_lattice_and_fractions(emu, block):
     x = complex_gaussian((3, m), 9)
     ref = (O.apply_block(pb, kappa, block, x, shift=0.5) if block >= 0
            else O.apply_full(pb, kappa, x, shift=0.5))
-    for dtype, shape, tz in ((2, 2, 3), (1, 3, 4), (2, 11, 5), (1, 10, 3)):
+    for dtype, shape, tz in ((2, 2, 3), (1, 3, 4), (2, 11, 5), (1, 10, 3), (1, 20, 3)):
+        if shape == 20 and block < 0:
+            continue
         y = run_emu(emu, pb, block, dtype, shape, tz, kappa, x, 0.5, 1)
         err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
         assert err < (1e-13 if dtype == 2 else 2e-6)

@@ -299,6 +299,7 @@ int pc_set_k(pc_grid* g, const double kappa[3]) {
     }
     g->k.gamma = gamma;
     g->k.set = true;
+    g->k.version += 1;
     fill_params(g);
     return precond_set_k(g);
 }

@@ -113,6 +113,13 @@ void note_apply_launch(int n = 1);
 bool timing_enabled();
 void* timing_begin(cudaStream_t s);
 void timing_end(void* h, cudaStream_t s, int kind, double nodes);
+// Timing of launches captured into a CUDA graph (read after each replay).
+struct TimedSet;
+TimedSet* timing_capture_begin();
+void timing_capture_end(TimedSet* t);
+void timing_replayed(TimedSet* t);
+void timing_free(TimedSet* t);
+long long launch_count();
 
 // Per-k rebuild of the preconditioner tables; release of solver workspaces.
 int precond_set_k(pc_grid* g);
@@ -121,6 +128,7 @@ void release_solver_state(pc_grid* g);
 // ---------------------------------------------------------------- grid object
 struct GridK {  // per-Bloch-vector state
     bool set = false;
+    uint64_t version = 0;  // incremented by every pc_set_k (captured graphs depend on it)
     double kappa[3] = {0, 0, 0};
     double phi[3] = {0, 0, 0};
     bool gamma = false;

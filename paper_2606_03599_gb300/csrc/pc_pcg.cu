@@ -8,6 +8,8 @@
 // kernel) -> alpha -> x += alpha p, r -= alpha q with partials of ||r||^2 ->
 // z = P r (block Fourier preconditioner) with partials of Re<r, z> -> beta and
 // the convergence test ||r|| <= tol ||b|| -> p = z + beta p.
+#include <cstdlib>
+#include <string>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -208,13 +210,33 @@ __global__ void blocks_to_full(const C* __restrict__ blk, C* __restrict__ full, 
     }
 }
 
+// CUDA-graph replay of PCG iteration chunks (PC_PCG_GRAPHS=0 turns it off).
+static bool pcg_graphs_enabled() {
+    static int on = -1;
+    if (on < 0) {
+        const char* v = std::getenv("PC_PCG_GRAPHS");
+        on = (v && std::string(v) == "0") ? 0 : 1;
+    }
+    return on != 0;
+}
+
 static int vec_ctas(int64_t vs) {
     int64_t g = (vs + 1023) / 1024;
     if (g > 304) g = 304;
     return (int)(g < 1 ? 1 : g);
 }
 
+void PcgWork::drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    gkey.clear();
+    glaunches = 0;
+    timing_free(gtimed);
+    gtimed = nullptr;
+}
+
 void PcgWork::release() {
+    drop_graph();
     cudaFree(R);
     cudaFree(Z);
     cudaFree(P);
@@ -352,25 +374,74 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
     const int napc = cfg.ctas;
     const double tol2 = tol * tol;
     const int chunk = 4;
+    auto iterate = [&]() -> int {
+        PC_TRY(grid_apply(g, dtype, full, items.data(), nsys, part_a, npm, s, &cfg));
+        pcg_alpha<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, napc);
+        note_launch();
+        pcg_update_xr<C><<<vgrid, 256, 0, s>>>(X, R, P, Q, w->sc, w->done, vs, part_b, npm);
+        note_launch();
+        PC_CUDA_TRY(cudaGetLastError());
+        PC_TRY(precondition(full ? nullptr : w->done));
+        pcg_beta<<<nsys, 256, 0, s>>>(w->sc, w->done, part_b, npm, vc, part_c, nrz, tol2, maxit);
+        note_launch();
+        pcg_update_p<C><<<vgrid, 256, 0, s>>>(P, Z, w->sc, w->done, vs);
+        note_launch();
+        PC_CUDA_TRY(cudaGetLastError());
+        return PC_OK;
+    };
+    // Chunks after the first (which creates the preconditioner workspace and FFT plans) replay
+    // a CUDA graph of `chunk` iterations, captured once per (Bloch vector, systems, buffers,
+    // shift, tolerance); block systems on a non-default stream only.
+    const bool graphs = !full && pcg_graphs_enabled() && s != nullptr && s != cudaStreamLegacy &&
+                        s != cudaStreamPerThread;
+    auto chunk_graph = [&]() -> int {
+        std::vector<double> key = {(double)g->k.version, (double)dtype, (double)nsys, sigma, tol2, (double)maxit,
+                                   (double)(uintptr_t)B, (double)(uintptr_t)X, (double)(uintptr_t)g->pre->d_work,
+                                   (double)(uintptr_t)w->R, (double)(timing_enabled() ? 1 : 0), (double)npm};
+        for (int i = 0; i < nsys; ++i) key.push_back((double)blocks[i]);
+        if (w->gexec == nullptr || w->gkey != key) {
+            w->drop_graph();
+            cudaGraph_t graph = nullptr;
+            PC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            const long long n0 = launch_count();
+            TimedSet* ts = timing_enabled() ? timing_capture_begin() : nullptr;
+            int rc = PC_OK;
+            for (int c = 0; c < chunk && rc == PC_OK; ++c) rc = iterate();
+            cudaError_t e = cudaStreamEndCapture(s, &graph);
+            if (ts) timing_capture_end(ts);
+            if (rc != PC_OK || e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                timing_free(ts);
+                return rc != PC_OK ? rc : cuda_fail(e, "cudaStreamEndCapture(pcg)");
+            }
+            e = cudaGraphInstantiate(&w->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                w->gexec = nullptr;
+                timing_free(ts);
+                return cuda_fail(e, "cudaGraphInstantiate(pcg)");
+            }
+            w->glaunches = launch_count() - n0;
+            note_launch(-(int)w->glaunches);  // the capture launched nothing; replays are counted below
+            w->gtimed = ts;
+            w->gkey = key;
+        }
+        PC_CUDA_TRY(cudaGraphLaunch(w->gexec, s));
+        note_launch((int)w->glaunches);
+        return PC_OK;
+    };
     int it = 0;
     bool all_done = false;
     while (!all_done) {
-        for (int c = 0; c < chunk; ++c, ++it) {
-            PC_TRY(grid_apply(g, dtype, full, items.data(), nsys, part_a, npm, s, &cfg));
-            pcg_alpha<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, napc);
-            note_launch();
-            pcg_update_xr<C><<<vgrid, 256, 0, s>>>(X, R, P, Q, w->sc, w->done, vs, part_b, npm);
-            note_launch();
-            PC_CUDA_TRY(cudaGetLastError());
-            PC_TRY(precondition(full ? nullptr : w->done));
-            pcg_beta<<<nsys, 256, 0, s>>>(w->sc, w->done, part_b, npm, vc, part_c, nrz, tol2, maxit);
-            note_launch();
-            pcg_update_p<C><<<vgrid, 256, 0, s>>>(P, Z, w->sc, w->done, vs);
-            note_launch();
-            PC_CUDA_TRY(cudaGetLastError());
+        if (graphs && it >= chunk) {
+            PC_TRY(chunk_graph());
+        } else {
+            for (int c = 0; c < chunk; ++c) PC_TRY(iterate());
         }
+        it += chunk;
         PC_CUDA_TRY(cudaMemcpyAsync(w->h_sc, w->sc, sizeof(PcgScal) * nsys, cudaMemcpyDeviceToHost, s));
         PC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (graphs && it > chunk && w->gtimed) timing_replayed(w->gtimed);
         all_done = true;
         for (int i = 0; i < nsys; ++i)
             if (!w->h_sc[i].done) all_done = false;

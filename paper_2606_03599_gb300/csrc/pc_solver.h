@@ -41,6 +41,12 @@ struct PcgWork {
     int* done = nullptr;     // [cap] mirror of sc.done for skip flags
     int* blocks = nullptr;   // [cap] block of each system
     PcgScal* h_sc = nullptr; // pinned host mirror
+    // CUDA graph of one chunk of PCG iterations, valid for the key it was captured with
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<double> gkey;
+    long long glaunches = 0;       // library kernel launches inside the graph
+    struct TimedSet* gtimed = nullptr;
+    void drop_graph();
     void release();
 };
 

@@ -55,6 +55,53 @@ void timing_end(void* h, cudaStream_t s, int kind, double nodes) {
     delete t;
 }
 
+// Timing inside captured graphs: the event pairs recorded during a capture are kept with the
+// graph and read after every replay (the replayed graph records the same events again).
+struct TimedSet {
+    size_t mark = 0;
+    std::vector<TimedLaunch> recs;
+};
+
+TimedSet* timing_capture_begin() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    TimedSet* t = new TimedSet();
+    t->mark = g_pending.size();
+    return t;
+}
+
+void timing_capture_end(TimedSet* t) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (t->mark < g_pending.size()) {
+        t->recs.assign(g_pending.begin() + (long)t->mark, g_pending.end());
+        g_pending.resize(t->mark);
+    }
+}
+
+void timing_replayed(TimedSet* t) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& r : t->recs) {
+        float ms = 0.f;
+        cudaEventSynchronize(r.b);
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g_ms[r.kind] += ms;
+            g_timed[r.kind] += 1;
+            g_nodes[r.kind] += r.nodes;
+        }
+    }
+}
+
+void timing_free(TimedSet* t) {
+    if (!t) return;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& r : t->recs) {
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    delete t;
+}
+
+long long launch_count() { return g_launches.load(); }
+
 static void drain() {
     for (auto& t : g_pending) {
         float ms = 0.f;

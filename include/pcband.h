@@ -105,6 +105,8 @@ typedef struct {
     int guard;           /* extra Ritz pairs carried per block beyond its share; default 3 */
     int verbose;         /* 0 = silent */
     void* stream;        /* cudaStream_t for all of the solve's work, or NULL for an internal stream */
+    int autotune;        /* 1 = time the stencil launch shapes for this grid's batches before solving
+                            (pc_autotune); 0 = built-in choice.  Default 0 */
 } pc_options;
 
 /* Statistics of one pc_eigs call. */
@@ -235,6 +237,24 @@ int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const vo
  * over between calls.  Enqueued on `stream`. */
 int pc_block_apply_dot_noalloc(pc_grid* g, int block, int dtype, const void* x, void* y, double shift,
                                double* dot, void* stream);
+
+/* ---- launch tuning ----------------------------------------------------- */
+
+/* Autotuner of the stencil apply (no counterpart in the paper: an implementation choice).
+ * Times every applicable kernel and launch shape (row-tile kernel with several persistent CTA
+ * counts, TMA tile kernel, register-staged kernel; several k-chunkings) on scratch vectors for
+ * batches of `nitems` (rounded up to a power of two, 1..64) vectors of precision `dtype` in the
+ * parity-block layout (layout 0), the full-space layout (1) or both (2), and keeps the fastest
+ * for every later apply, PCG and eigen-solve on grids of the same size, material kind and lattice
+ * in this process.  With the environment variable PC_TUNE_CACHE naming a file, results are read
+ * from it and appended to it (one JSON-style line per key).  Synchronises `stream`; allocates and
+ * frees scratch (2 x nitems vectors).  Needs pc_set_k first. */
+int pc_autotune(pc_grid* g, int dtype, int layout, int nitems, void* stream);
+
+/* The launch configuration the library will use for a batch of `nitems` vectors of `dtype` in
+ * layout 0 (blocks) or 1 (full): kind 0 = register-staged, 1 = TMA tile, 2 = row tile; tile
+ * shape code; planes per CTA (tz; row kernel: least planes per CTA); CTAs of the launch. */
+int pc_tuned_config(const pc_grid* g, int dtype, int layout, int nitems, int* kind, int* shape, int* tz, int* ctas);
 
 /* ---- differentiation --------------------------------------------------- */
 

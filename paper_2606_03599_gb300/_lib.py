@@ -27,7 +27,7 @@ EXPORTED = [
     "pc_block_apply", "pc_block_apply_many", "pc_block_mass", "pc_block_transfer",
     "pc_block_fourier", "pc_shift_invert_pcg", "pc_options_default", "pc_default_sigma",
     "pc_eigs", "pc_last_error", "pc_version", "pc_apply_batch", "pc_stats_timing", "pc_stats_reset",
-    "pc_stats_get", "pc_block_apply_dot_noalloc", "pc_eig_grad",
+    "pc_stats_get", "pc_block_apply_dot_noalloc", "pc_eig_grad", "pc_autotune", "pc_tuned_config",
 ]
 
 
@@ -59,7 +59,7 @@ class c_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("precision", ctypes.c_int),
                 ("full_space", ctypes.c_int), ("block_size", ctypes.c_int), ("max_basis", ctypes.c_int),
                 ("max_restarts", ctypes.c_int), ("inner_maxit", ctypes.c_int), ("guard", ctypes.c_int),
-                ("verbose", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("verbose", ctypes.c_int), ("stream", ctypes.c_void_p), ("autotune", ctypes.c_int)]
 
 
 class c_stats(ctypes.Structure):
@@ -101,6 +101,8 @@ def _load():
         "pc_apply_batch": ([vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp], ci),
         "pc_block_apply_dot_noalloc": ([vp, ci, ci, vp, vp, cd, vp, vp], ci),
         "pc_eig_grad": ([vp, ci, ci, vp, dp, dp, vp, vp, vp], ci),
+        "pc_autotune": ([vp, ci, ci, ci, vp], ci),
+        "pc_tuned_config": ([vp, ci, ci, ci] + [ctypes.POINTER(ci)] * 4, ci),
         "pc_stats_timing": ([ci], ci),
         "pc_stats_reset": ([], ci),
         "pc_stats_get": ([ctypes.POINTER(c_stats)], ci),
@@ -303,6 +305,18 @@ def pc_eig_grad(g, block, X, lambdas, weights, dC, drho, stream=None):
                            lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                            w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(dC), _ptr(drho),
                            _stream(stream)))
+
+
+def pc_autotune(g, dtype, layout, nitems, stream=None):
+    """Time the stencil launch shapes for batches of `nitems` (layout 0 blocks, 1 full, 2 both)."""
+    _check(lib.pc_autotune(g, int(dtype), int(layout), int(nitems), _stream(stream)))
+
+
+def pc_tuned_config(g, dtype, layout, nitems):
+    """(kind, shape, tz, ctas) of the launch the library uses; kind 0 registers, 1 TMA tile, 2 row."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib.pc_tuned_config(g, int(dtype), int(layout), int(nitems), *[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def pc_stats_timing(enable):

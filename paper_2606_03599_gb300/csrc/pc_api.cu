@@ -40,8 +40,6 @@ static int apply_kernel_mode() {
     return mode;
 }
 
-bool row_geom_fits(int X, int Y, int Z, int matkind);
-
 int device_sm_count() {
     static int n = 0;
     if (n == 0) {
@@ -62,8 +60,8 @@ ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool
         c.row = true;
         c.tma = false;
         c.shape = 0;
-        c.tz = 0;
-        c.ctas = row_apply_ctas(X, Y, Z, matkind, nitems);
+        c.tz = 12;  // planes per CTA at least
+        c.ctas = row_apply_ctas(X, Y, Z, matkind, nitems, c.tz);
         return c;
     }
     if (apply_kernel_mode() != 1 && dtype == PC_C64 && X % 2 == 0 && X >= 8 && Y >= 8) {
@@ -312,7 +310,7 @@ namespace pc {
 int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nitems, double* dot_partials,
                int dot_stride, cudaStream_t s, const ApplyConfig* cfg_in) {
     const int X = full ? g->N : g->X, Y = full ? g->N : g->Y, Z = g->Z;
-    ApplyConfig cfg = cfg_in ? *cfg_in : choose_apply_config(X, Y, Z, nitems, dtype, !full, g->matkind);
+    ApplyConfig cfg = cfg_in ? *cfg_in : apply_config_for(g, full, nitems, dtype);
     void* th = timing_enabled() ? timing_begin(s) : nullptr;
     int rc;
     if (dtype == PC_C64 && cfg.row) {

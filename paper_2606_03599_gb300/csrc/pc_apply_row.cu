@@ -45,10 +45,11 @@ int launch_apply_row_f32(bool cubic, int matkind, const StencilParams<float>& P,
                    : launch_row_t<false, 0, 0>(P, items, mats, nitems, G, ctas, dp, ds, err, s);
 }
 
-int row_apply_ctas(int X, int Y, int Z, int matkind, int nitems) {
+int row_apply_ctas(int X, int Y, int Z, int matkind, int nitems, int minseg) {
+    // at least `minseg` planes per CTA (each segment reloads four halo planes)
     const RowGeom G = make_row_geom(X, Y, Z, matkind);
     const int64_t W = (int64_t)std::min(nitems, kRowMaxItems) * G.nt * Z;
-    const int64_t minseg = 12;  // planes per CTA at least (each segment reloads 4 halo planes)
+    if (minseg < 1) minseg = 1;
     int64_t c = (W + minseg - 1) / minseg;
     const int sm = device_sm_count();
     if (c > sm) c = sm;

@@ -692,6 +692,13 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
     const bool full = opt->full_space != 0;
     const int nspace = full ? 1 : 4;
     const int64_t m = full ? g->n : g->nb, vs = 3 * m;
+    if (opt->autotune) {
+        // stencil launch shapes for the batches this solve runs (inner PCG, and the FP64 residual
+        // refinement of the mixed path); tuned once per layout and cached
+        const bool mixed = opt->precision == PC_PREC_MIXED;
+        PC_TRY(autotune_layout(g, mixed ? PC_C64 : PC_C128, full, E.bs * nspace, E.s, opt->verbose));
+        if (mixed) PC_TRY(autotune_layout(g, PC_C128, full, E.bs * nspace, E.s, opt->verbose));
+    }
     E.sp.resize(nspace);
     const int share = full ? nev : (nev + 3) / 4;
     const int guard = std::max(0, opt->guard);
@@ -874,6 +881,7 @@ int pc_options_default(pc_options* o) {
     o->guard = 3;
     o->verbose = 0;
     o->stream = nullptr;
+    o->autotune = 0;
     return PC_OK;
 }
 

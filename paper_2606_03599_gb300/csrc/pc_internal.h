@@ -68,7 +68,8 @@ int launch_apply_tma_f32(bool full, bool cubic, int matkind, int shape, const St
 // Row-tile kernel (complex64 parity blocks): mats = row-padded material per item; ctas = persistent CTAs.
 int launch_apply_row_f32(bool cubic, int matkind, const StencilParams<float>& P, const ApplyItem* items,
                          const void* const* mats, int nitems, int ctas, double* dp, int ds, int* err, cudaStream_t s);
-int row_apply_ctas(int X, int Y, int Z, int matkind, int nitems);
+int row_apply_ctas(int X, int Y, int Z, int matkind, int nitems, int minseg = 12);
+bool row_geom_fits(int X, int Y, int Z, int matkind);
 int device_sm_count();
 int launch_apply_tma_f64(bool full, bool cubic, int matkind, int shape, const StencilParams<double>& P,
                          const ApplyItem* items, int nitems, int tz, double* dp, int ds, int* err, cudaStream_t s);
@@ -81,6 +82,10 @@ struct ApplyConfig {
     bool row = false;  // row-tile kernel (complex64 parity blocks, X even)
 };
 ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool blocks = false, int matkind = 0);
+// Launch configuration for a grid layout: the autotuned one when present, else the heuristic.
+ApplyConfig apply_config_for(const pc_grid* g, bool full, int nitems, int dtype);
+bool tuned_config(int X, int Y, int Z, int dtype, bool full, int matkind, bool cubic, int nitems, ApplyConfig* out);
+int autotune_layout(pc_grid* g, int dtype, bool full, int nitems, cudaStream_t s, int verbose);
 int tile_tx(int shape);
 int tile_ty(int shape);
 

@@ -267,9 +267,7 @@ static int pcg_work(pc_grid* g, int dtype, int nsys, int64_t vs, bool full, PcgW
     PcgWork& w = S->pcg[dtype == PC_C64 ? 0 : 1];
     const int64_t esz = dtype == PC_C64 ? 8 : 16;
     // partial-sum slots: stencil CTAs, vector CTAs, unpack CTAs (x4 for full space)
-    const int nap = std::max(
-        choose_apply_config(full ? g->N : g->X, full ? g->N : g->Y, g->Z, 1, dtype, !full, g->matkind).ctas,
-        choose_apply_config(full ? g->N : g->X, full ? g->N : g->Y, g->Z, nsys, dtype, !full, g->matkind).ctas);
+    const int nap = std::max(apply_config_for(g, full, 1, dtype).ctas, apply_config_for(g, full, nsys, dtype).ctas);
     const int npm = std::max(std::max(nap, vec_ctas(vs)), 4 * unpack_ctas(3 * g->nb));
     if (w.cap >= nsys && w.vs == vs && w.npart_max >= npm && w.dtype == dtype) {
         *out = &w;
@@ -369,8 +367,7 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
         items[i].dot_slot = i;
         items[i].skip = w->done + i;
     }
-    const ApplyConfig cfg =
-        choose_apply_config(full ? g->N : g->X, full ? g->N : g->Y, g->Z, nsys, dtype, !full, g->matkind);
+    const ApplyConfig cfg = apply_config_for(g, full, nsys, dtype);
     const int napc = cfg.ctas;
     const double tol2 = tol * tol;
     const int chunk = 4;

@@ -278,6 +278,62 @@ def profile_run(what):
     pc.pc_grid_destroy(g)
 
 
+def batching_run(args):
+    """Ragged batch: N in {32, 48, 64, 96, 128} (own seeds, R ~ U[0.2, 0.4]), `--batch-k` Bloch vectors
+    each along the SC path, four parity blocks, 16 bands at 1e-8, complex64 apply and inner PCG with
+    the FP64 outer loop, autotuned launches, CUDA-graph PCG chunks, pc_eigs_batch worker pool.
+    Reported against plain FP64 full-space solves of the same grids on the same GPU (sampled)."""
+    import numpy as np
+    import torch
+    import paper_2606_03599_gb300 as pc
+    from workloads import config_cell
+    from workloads.kpath import sc_uniform_path
+    sizes = [32, 48, 64, 96, 128]
+    nk = max(1, args.batch_k)
+    ks = sc_uniform_path(nk)
+    cells = [config_cell("batch", N=N) for N in sizes]
+    grids = [pc.pc_grid_create(c.N, c.C, c.rho, phase=c.phase, a_lat=c.a_lat) for c in cells]
+    nev = 16
+    opt = pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED, autotune=1)
+    # warm-up: tunes every grid size and builds the solver state once
+    pc.pc_eigs_batch(grids, [ks[:1]] * len(grids), nev, opt=opt, workers=args.workers)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    evs, _, status, info = pc.pc_eigs_batch(grids, [ks] * len(grids), nev, opt=opt, workers=args.workers)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    total_k = nk * len(sizes)
+    # plain FP64 full space, one Bloch vector at a time, on a sample of the same Bloch vectors
+    fopt = pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_FP64, full_space=1)
+    sample = [ks[len(ks) // 3], ks[(2 * len(ks)) // 3]]
+    per_grid_full, max_diff = [], 0.0
+    for g, ev in zip(grids, evs):
+        pc.pc_eigs(g, sample[0], nev, opt=fopt)  # warm-up of the full-space state
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for kk in sample:
+            ef, _, _ = pc.pc_eigs(g, kk, nev, opt=fopt)
+            i = int(np.argmin(np.abs(ks - kk).sum(axis=1)))
+            max_diff = max(max_diff, float(np.max(np.abs(ef - ev[i]) / np.abs(ef))))
+        torch.cuda.synchronize()
+        per_grid_full.append((time.perf_counter() - t1) / len(sample))
+    full_est = nk * sum(per_grid_full)
+    for g in grids:
+        pc.pc_grid_destroy(g)
+    line = {"metric": METRIC, "mode": "batching", "unit": "s/k-point", "dtype": "mixed c64/f64",
+            "config": {"workload": "ragged two-phase SC cells N in %s (seeds 10..14, R ~ U[0.2,0.4]), %d Bloch "
+                                   "vectors each on the SC path, 4 parity blocks, 16 bands, resid 1e-8" % (sizes, nk),
+                       "block_solves": 4 * total_k, "workers": info["workers"], "autotune": True,
+                       "cuda_graphs": True},
+            "total_s": t_batch, "s_per_kpoint": t_batch / total_k,
+            "full_space_fp64_s_per_kpoint_by_N": dict(zip(map(str, sizes), per_grid_full)),
+            "full_space_fp64_estimated_total_s": full_est, "speedup_vs_fp64_full_space": full_est / t_batch,
+            "max_rel_diff_vs_fp64_full_space_sampled": max_diff,
+            "max_true_rel_resid": info["max_rel_resid"], "failed": info["failed"],
+            "pcg_iters": info["pcg_iters"]}
+    print(json.dumps(line), flush=True)
+
+
 def precision_run(args):
     """N = 160 two-phase cell (R = 0.3, seed 3), Gamma/X/M/R and four midpoints, 20 bands at 1e-8:
     mixed precision s/k-point, and per-band relative error against the FP64 path on the first k-point."""
@@ -289,8 +345,11 @@ def precision_run(args):
     kpts = sc_eight_points()
     g = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
     stream = torch.cuda.Stream()
-    om = pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED)
+    om = pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED, autotune=1)
     om.stream = stream.cuda_stream
+    pc.pc_set_k(g, kpts[0])  # launch shapes tuned before the timed solves
+    for dt in (pc.PC_C64, pc.PC_C128):
+        pc.pc_autotune(g, dt, 0, 4 * om.block_size, stream.cuda_stream)
     nk = max(1, min(args.steps, len(kpts)))
     res = []
     for i in range(nk):
@@ -301,7 +360,7 @@ def precision_run(args):
         e1.record(stream)
         e1.synchronize()
         res.append((e0.elapsed_time(e1) / 1e3, ev, info))
-    o64 = pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_FP64)
+    o64 = pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_FP64, autotune=1)
     o64.stream = stream.cuda_stream
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -333,6 +392,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--precision", action="store_true",
                     help="run the N=160 precision workload (8 k-points, 20 bands, mixed precision) instead")
+    ap.add_argument("--batching", action="store_true",
+                    help="run the ragged batching workload (N in {32..128}, --batch-k Bloch vectors each) instead")
+    ap.add_argument("--batch-k", type=int, default=64, help="Bloch vectors per grid of --batching")
+    ap.add_argument("--workers", type=int, default=4, help="host worker threads of --batching")
     ap.add_argument("--profile", default=None, choices=["kpoint", "kpoint-mixed", "apply-c64", "apply-c128"],
                     help="profiling aid for ncu: run only one k-point solve of the workload, or one "
                          "N=160 four-block apply (after two untimed ones), and print nothing else")
@@ -345,6 +408,9 @@ def main():
         return
     if args.precision:
         precision_run(args)
+        return
+    if args.batching:
+        batching_run(args)
         return
     args.warmup = max(3, args.warmup)
 
@@ -361,7 +427,7 @@ def main():
     cell = config_cell("fp64")
     kpts = sc_path(6)
     stream = torch.cuda.Stream()
-    opt = pc.pc_options_default(tol=TOL, inner_tol=1e-10, precision=pc.PC_PREC_FP64)
+    opt = pc.pc_options_default(tol=TOL, inner_tol=1e-10, precision=pc.PC_PREC_FP64, autotune=1)
     opt.stream = stream.cuda_stream
     g = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
@@ -410,7 +476,9 @@ def main():
     app_ms = st["apply_ms"][1] / max(1, n_app)
     nodes_per_launch = st["apply_nodes"][1] / max(1, n_app)
     achieved_tflops = nodes_per_launch * FLOPS_PER_NODE / (app_ms / 1e3) / 1e12
-    roofline = {"kernel": "apply_kernel<double> (fused block stencil, FP64)", "bound": "alu",
+    kind = pc.pc_tuned_config(g, pc.PC_C128, 0, 4 * opt.block_size)[0]
+    kname = {0: "apply_kernel<double>", 1: "apply_tma_kernel<double>", 2: "apply_row_kernel"}[kind]
+    roofline = {"kernel": kname + " (fused block stencil, FP64, autotuned launch)", "bound": "alu",
                 "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
                 "launches": n_app, "avg_launch_us": app_ms * 1e3, "nodes_per_launch": nodes_per_launch,
@@ -442,9 +510,10 @@ def main():
     if rank == 0:
         compare = {}
         nk = min(args.steps, 3)
-        for name, o2 in (("mixed", pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED)),
-                         ("full_space_fp64", pc.pc_options_default(tol=TOL, full_space=1))):
+        for name, o2 in (("mixed", pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED, autotune=1)),
+                         ("full_space_fp64", pc.pc_options_default(tol=TOL, full_space=1, autotune=1))):
             o2.stream = stream.cuda_stream
+            pc.pc_eigs(g, kpoint(0), NEV, opt=o2)  # untimed: tunes this leg's launches, builds its state
             ms, err = [], 0.0
             for s in range(nk):
                 e0 = torch.cuda.Event(enable_timing=True)

@@ -238,6 +238,41 @@ int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const vo
 int pc_block_apply_dot_noalloc(pc_grid* g, int block, int dtype, const void* x, void* y, double shift,
                                double* dot, void* stream);
 
+/* ---- batches of grids and Bloch vectors -------------------------------- */
+
+/* A copy of grid `src` (same size, material, lattice and units; no Bloch vector set, no solver
+ * state).  Device memory of its own; destroy with pc_grid_destroy. */
+int pc_grid_clone(const pc_grid* src, pc_grid** out);
+
+typedef struct {
+    pc_grid* grid;          /* caller-owned; only read (workers solve on their own copies) */
+    int nk;                 /* Bloch vectors of this grid */
+    const double* kappas;   /* host [nk][3], reduced coordinates as in pc_set_k */
+    int nev;                /* eigenvalues per Bloch vector */
+    double sigma;           /* shift-invert target, NaN = pc_default_sigma of the grid */
+    double* evals;          /* host [nk][nev] output (SI, as pc_eigs) */
+    int* block_of;          /* host [nk][nev] output or NULL */
+    int* status;            /* host [nk] output (pc_eigs status per Bloch vector) or NULL */
+} pc_batch_job;
+
+typedef struct {
+    int workers;            /* host worker threads used */
+    int kpoints;            /* Bloch vectors solved */
+    int failed;             /* of which with a nonzero status */
+    long long pcg_iters;    /* total inner PCG iterations */
+    double max_rel_resid;   /* largest true relative residual over all reported pairs */
+    double seconds;         /* wall time */
+} pc_batch_info;
+
+/* Band solves for many (grid, Bloch vector) pairs (the batching of the parity-block method's
+ * independent subproblems, Sec. 6.3): every Bloch vector is solved as pc_eigs does (four
+ * blocks batched), by `workers` host threads (1..16), each with its own CUDA stream and its own
+ * copy of the grid it works on, taking items largest grid first.  With opt->autotune the
+ * launch shapes of every grid size are tuned before the workers start.  opt->stream, if set,
+ * is used for the tuning only.  Returns PC_OK, PC_ENOCONV when some Bloch vectors did not
+ * converge (their status says which, the others are valid), or the first hard error. */
+int pc_eigs_batch(pc_batch_job* jobs, int njobs, const pc_options* opt, int workers, pc_batch_info* info);
+
 /* ---- launch tuning ----------------------------------------------------- */
 
 /* Autotuner of the stencil apply (no counterpart in the paper: an implementation choice).

@@ -28,6 +28,7 @@ EXPORTED = [
     "pc_block_fourier", "pc_shift_invert_pcg", "pc_options_default", "pc_default_sigma",
     "pc_eigs", "pc_last_error", "pc_version", "pc_apply_batch", "pc_stats_timing", "pc_stats_reset",
     "pc_stats_get", "pc_block_apply_dot_noalloc", "pc_eig_grad", "pc_autotune", "pc_tuned_config",
+    "pc_grid_clone", "pc_eigs_batch",
 ]
 
 
@@ -60,6 +61,17 @@ class c_options(ctypes.Structure):
                 ("full_space", ctypes.c_int), ("block_size", ctypes.c_int), ("max_basis", ctypes.c_int),
                 ("max_restarts", ctypes.c_int), ("inner_maxit", ctypes.c_int), ("guard", ctypes.c_int),
                 ("verbose", ctypes.c_int), ("stream", ctypes.c_void_p), ("autotune", ctypes.c_int)]
+
+
+class c_batch_job(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_void_p), ("nk", ctypes.c_int), ("kappas", ctypes.POINTER(ctypes.c_double)),
+                ("nev", ctypes.c_int), ("sigma", ctypes.c_double), ("evals", ctypes.POINTER(ctypes.c_double)),
+                ("block_of", ctypes.POINTER(ctypes.c_int)), ("status", ctypes.POINTER(ctypes.c_int))]
+
+
+class c_batch_info(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int), ("kpoints", ctypes.c_int), ("failed", ctypes.c_int),
+                ("pcg_iters", ctypes.c_longlong), ("max_rel_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
 
 
 class c_stats(ctypes.Structure):
@@ -102,6 +114,9 @@ def _load():
         "pc_block_apply_dot_noalloc": ([vp, ci, ci, vp, vp, cd, vp, vp], ci),
         "pc_eig_grad": ([vp, ci, ci, vp, dp, dp, vp, vp, vp], ci),
         "pc_autotune": ([vp, ci, ci, ci, vp], ci),
+        "pc_grid_clone": ([vp, ctypes.POINTER(vp)], ci),
+        "pc_eigs_batch": ([ctypes.POINTER(c_batch_job), ci, ctypes.POINTER(c_options), ci,
+                           ctypes.POINTER(c_batch_info)], ci),
         "pc_tuned_config": ([vp, ci, ci, ci] + [ctypes.POINTER(ci)] * 4, ci),
         "pc_stats_timing": ([ci], ci),
         "pc_stats_reset": ([], ci),
@@ -305,6 +320,45 @@ def pc_eig_grad(g, block, X, lambdas, weights, dC, drho, stream=None):
                            lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                            w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(dC), _ptr(drho),
                            _stream(stream)))
+
+
+def pc_grid_clone(g):
+    h = ctypes.c_void_p()
+    _check(lib.pc_grid_clone(g, ctypes.byref(h)))
+    return h.value
+
+
+def pc_eigs_batch(grids, kappas, nev, opt=None, workers=4, sigma=float("nan"), raise_on_noconv=True):
+    """Solve every (grid, Bloch vector): grids is a list of handles, kappas a list of [nk][3] arrays.
+    Returns (evals list of [nk][nev] arrays, block_of list, status list, info dict)."""
+    n = len(grids)
+    jobs = (c_batch_job * n)()
+    keep = []
+    out_ev, out_bl, out_st = [], [], []
+    for j, (g, ks) in enumerate(zip(grids, kappas)):
+        ks = np.ascontiguousarray(np.asarray(ks, dtype=np.float64).reshape(-1, 3))
+        ev = np.zeros((ks.shape[0], nev))
+        bl = np.zeros((ks.shape[0], nev), dtype=np.int32)
+        st = np.zeros(ks.shape[0], dtype=np.int32)
+        keep += [ks, ev, bl, st]
+        out_ev.append(ev)
+        out_bl.append(bl)
+        out_st.append(st)
+        jobs[j].grid = g
+        jobs[j].nk = ks.shape[0]
+        jobs[j].kappas = ks.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        jobs[j].nev = int(nev)
+        jobs[j].sigma = float(sigma)
+        jobs[j].evals = ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        jobs[j].block_of = bl.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        jobs[j].status = st.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    o = opt if opt is not None else pc_options_default()
+    info = c_batch_info()
+    rc = lib.pc_eigs_batch(jobs, n, ctypes.byref(o), int(workers), ctypes.byref(info))
+    if rc != PC_OK and (rc != PC_ENOCONV or raise_on_noconv):
+        _check(rc)
+    d = {f[0]: getattr(info, f[0]) for f in c_batch_info._fields_}
+    return out_ev, out_bl, out_st, d
 
 
 def pc_autotune(g, dtype, layout, nitems, stream=None):

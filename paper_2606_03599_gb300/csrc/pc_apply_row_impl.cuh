@@ -2,6 +2,8 @@
 // host launcher.  Included by the complex64 translation unit.
 #pragma once
 
+#include <mutex>
+
 #include "pc_apply_row.cuh"
 
 namespace pc {
@@ -185,11 +187,16 @@ static int launch_row_t(const StencilParams<float>& P, const ApplyItem* items, c
     auto kern = apply_row_kernel<CUBIC, MATK, XC>;
     const int smem = G.total + 128;  // + alignment slack of the dynamic window
     if (smem + 1024 > 227 * 1024) return fail(PC_EINVAL, "apply_row: shared memory layout exceeds 227 KB");
-    static int attr_bytes = 0;  // largest dynamic size granted so far
-    if (smem > attr_bytes) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply_row)");
-        attr_bytes = smem;
+    {
+        // grids of different sizes may launch this kernel from several host threads at once
+        static std::mutex mu;
+        static int attr_bytes = 0;  // largest dynamic size granted so far
+        std::lock_guard<std::mutex> lk(mu);
+        if (smem > attr_bytes) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(apply_row)");
+            attr_bytes = smem;
+        }
     }
     if (G.NT > kRowMaxThreads) return fail(PC_EINVAL, "apply_row: too many threads per CTA");
     if (dp != nullptr && ctas > ds) return fail(PC_EINVAL, "apply: launch has more CTAs than partial-sum slots");

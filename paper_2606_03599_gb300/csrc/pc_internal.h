@@ -125,6 +125,7 @@ void timing_capture_end(TimedSet* t);
 void timing_replayed(TimedSet* t);
 void timing_free(TimedSet* t);
 long long launch_count();
+long long apply_launch_count();
 
 // Per-k rebuild of the preconditioner tables; release of solver workspaces.
 int precond_set_k(pc_grid* g);

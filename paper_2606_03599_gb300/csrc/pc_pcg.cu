@@ -231,6 +231,7 @@ void PcgWork::drop_graph() {
     gexec = nullptr;
     gkey.clear();
     glaunches = 0;
+    gapply = 0;
     timing_free(gtimed);
     gtimed = nullptr;
 }
@@ -400,7 +401,7 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
             w->drop_graph();
             cudaGraph_t graph = nullptr;
             PC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            const long long n0 = launch_count();
+            const long long n0 = launch_count(), a0 = apply_launch_count();
             TimedSet* ts = timing_enabled() ? timing_capture_begin() : nullptr;
             int rc = PC_OK;
             for (int c = 0; c < chunk && rc == PC_OK; ++c) rc = iterate();
@@ -419,12 +420,15 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
                 return cuda_fail(e, "cudaGraphInstantiate(pcg)");
             }
             w->glaunches = launch_count() - n0;
+            w->gapply = apply_launch_count() - a0;
             note_launch(-(int)w->glaunches);  // the capture launched nothing; replays are counted below
+            note_apply_launch(-(int)w->gapply);
             w->gtimed = ts;
             w->gkey = key;
         }
         PC_CUDA_TRY(cudaGraphLaunch(w->gexec, s));
         note_launch((int)w->glaunches);
+        note_apply_launch((int)w->gapply);
         return PC_OK;
     };
     int it = 0;

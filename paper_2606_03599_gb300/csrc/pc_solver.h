@@ -45,6 +45,7 @@ struct PcgWork {
     cudaGraphExec_t gexec = nullptr;
     std::vector<double> gkey;
     long long glaunches = 0;       // library kernel launches inside the graph
+    long long gapply = 0;          // of which stencil applies
     struct TimedSet* gtimed = nullptr;
     void drop_graph();
     void release();

@@ -36,18 +36,28 @@ static cudaEvent_t take_event() {
     return e;
 }
 
+// Inside a stream capture a plain event record only orders the captured work; an external
+// record becomes a node that records the event every time the graph runs.
+static void record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (s != nullptr && cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
+
 void* timing_begin(cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);
     TimedLaunch* t = new TimedLaunch();
     t->a = take_event();
     t->b = take_event();
-    cudaEventRecord(t->a, s);
+    record(t->a, s);
     return t;
 }
 
 void timing_end(void* h, cudaStream_t s, int kind, double nodes) {
     TimedLaunch* t = static_cast<TimedLaunch*>(h);
-    cudaEventRecord(t->b, s);
+    record(t->b, s);
     t->kind = kind;
     t->nodes = nodes;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -86,6 +96,8 @@ void timing_replayed(TimedSet* t) {
             g_ms[r.kind] += ms;
             g_timed[r.kind] += 1;
             g_nodes[r.kind] += r.nodes;
+        } else {
+            cudaGetLastError();  // an unreadable timing is dropped, not reported to later calls
         }
     }
 }
@@ -101,6 +113,7 @@ void timing_free(TimedSet* t) {
 }
 
 long long launch_count() { return g_launches.load(); }
+long long apply_launch_count() { return g_apply_launches.load(); }
 
 static void drain() {
     for (auto& t : g_pending) {
@@ -110,6 +123,8 @@ static void drain() {
             g_ms[t.kind] += ms;
             g_timed[t.kind] += 1;
             g_nodes[t.kind] += t.nodes;
+        } else {
+            cudaGetLastError();
         }
         g_pool.push_back(t.a);
         g_pool.push_back(t.b);

@@ -107,3 +107,28 @@ def test_autotune_errors(pc):
                 pc.pc_autotune(g, *args)
     finally:
         pc.pc_grid_destroy(g)
+
+
+def test_apply_timing_through_graph_replays(pc):
+    """With event timing on, the stencil applies replayed inside the PCG's CUDA graphs are timed
+    and counted like eager ones, and the eigenvalues do not change."""
+    N = 24
+    cell = two_phase_sphere(N, 0.35, 4)
+    g = pc.pc_grid_create(N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+    try:
+        opt = pc.pc_options_default()
+        ev0, _, _ = pc.pc_eigs(g, [0.1, 0.3, 0.0], 8, opt=opt)
+        pc.pc_stats_reset()
+        pc.pc_stats_timing(1)
+        try:
+            ev1, _, info = pc.pc_eigs(g, [0.1, 0.3, 0.0], 8, opt=opt)
+        finally:
+            pc.pc_stats_timing(0)
+        st = pc.pc_stats_get()
+        assert np.allclose(ev0, ev1, rtol=1e-12, atol=0)
+        assert st["apply_launches"] > 20
+        # one timing per batched apply call; a call of more items than one launch holds may launch twice
+        assert 0.5 * st["apply_launches"] <= st["apply_timed"][1] <= st["apply_launches"]
+        assert st["apply_ms"][1] > 0
+    finally:
+        pc.pc_grid_destroy(g)

@@ -107,6 +107,11 @@ typedef struct {
     void* stream;        /* cudaStream_t for all of the solve's work, or NULL for an internal stream */
     int autotune;        /* 1 = time the stencil launch shapes for this grid's batches before solving
                             (pc_autotune); 0 = built-in choice.  Default 0 */
+    int precond_fp32;    /* PC_PREC_FP64 only: 1 = the FP64 inner PCG applies its Fourier preconditioner
+                            in complex64 (transforms, symbol solve) and uses the flexible CG beta; the
+                            iterates, the stencil and the residuals stay FP64, so the solve reaches the
+                            same inner_tol (the preconditioner only changes the iteration count).
+                            0 = preconditioner in FP64.  Default 1 */
 } pc_options;
 
 /* Statistics of one pc_eigs call. */

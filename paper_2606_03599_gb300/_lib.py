@@ -60,7 +60,8 @@ class c_options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("inner_tol", ctypes.c_double), ("precision", ctypes.c_int),
                 ("full_space", ctypes.c_int), ("block_size", ctypes.c_int), ("max_basis", ctypes.c_int),
                 ("max_restarts", ctypes.c_int), ("inner_maxit", ctypes.c_int), ("guard", ctypes.c_int),
-                ("verbose", ctypes.c_int), ("stream", ctypes.c_void_p), ("autotune", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("stream", ctypes.c_void_p), ("autotune", ctypes.c_int),
+                ("precond_fp32", ctypes.c_int)]
 
 
 class c_batch_job(ctypes.Structure):

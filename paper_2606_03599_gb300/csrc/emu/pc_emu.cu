@@ -31,6 +31,7 @@ static void emu_run(const StencilParams<R>& P, int block, const void* x, void* y
             c.y = static_cast<C*>(y);
             c.mat = mat;
             c.shift = (R)shift;
+            c.dot = true;
             c.a0 = (tile % ntx) * TX;
             c.b0 = (tile / ntx) * TY;
             c.k0 = ch * tz;

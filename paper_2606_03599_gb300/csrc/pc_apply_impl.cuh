@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(TX * TY)
     c.y = static_cast<C*>(it.y);
     c.mat = it.mat;
     c.shift = (R)it.shift;
+    c.dot = dot_partials != nullptr && it.dot_slot >= 0;
     c.a0 = (blockIdx.x % ntx) * TX;
     c.b0 = (blockIdx.x / ntx) * TY;
     c.k0 = blockIdx.y * tz;

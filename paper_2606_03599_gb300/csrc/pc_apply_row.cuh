@@ -264,13 +264,26 @@ struct RowTile {
         e[5] = cadd(G[1][0], G[0][1]);
         C t[6];
         if (MATK == 0) {
-            const float2* Cq = sh.cp() + (m != 0.f ? 36 : 0);
+            const int ph = m != 0.f ? 1 : 0;
+            const float2* Cq = sh.cp() + 36 * ph;
+            if (warp_all(P.ortho[ph] != 0)) {  // every node of the warp: normal block and shear diagonal only
 #pragma unroll
-            for (int p = 0; p < 6; ++p) {
-                C acc = czero(0.f);
+                for (int p = 0; p < 3; ++p) {
+                    C acc = czero(0.f);
 #pragma unroll
-                for (int q = 0; q < 6; ++q) acc = stiff_fma_pair(Cq[p * 6 + q], e[q], acc);
-                t[p] = acc;
+                    for (int q = 0; q < 3; ++q) acc = stiff_fma_pair(Cq[p * 6 + q], e[q], acc);
+                    t[p] = acc;
+                }
+#pragma unroll
+                for (int p = 3; p < 6; ++p) t[p] = stiff_fma_pair(Cq[p * 6 + p], e[p], czero(0.f));
+            } else {
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    C acc = czero(0.f);
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) acc = stiff_fma_pair(Cq[p * 6 + q], e[q], acc);
+                    t[p] = acc;
+                }
             }
         } else {
 #pragma unroll

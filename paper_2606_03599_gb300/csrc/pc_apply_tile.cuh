@@ -29,8 +29,11 @@
 //
 // Tiling.  A CTA owns an a-b tile of TX x TY columns and marches through a
 // chunk of tz planes in k.  Shared memory holds a ring of four x planes over
-// the tile plus a halo (TX+2) x (TY+4), and one plane of fluxes F over
-// (TX+1) x (TY+2) columns.  Step kf computes F(kf), then finishes y(kf-1)
+// the tile plus a halo (TX+2) x (TY+4), and one plane of fluxes F.  The flux
+// columns of plane kf are those of the tile's own nodes (for the local term)
+// and those the outputs of planes kf +- 1 read, which sit at a fixed offset
+// (i0, j0 - 1 + {0, 1}) of the same parity: (TX + i0) x (TY + 1) columns for a
+// parity block, (TX+1) x (TY+2) for the full grid.  Step kf computes F(kf), then finishes y(kf-1)
 // (the s3 = +1 neighbours are in plane kf), adds the local term to y(kf) and
 // starts y(kf+1) with its s3 = -1 neighbours (also in plane kf).  x planes are
 // prefetched one step ahead through registers; Bloch phases of wrapped halo
@@ -39,6 +42,8 @@
 
 #include <math.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "pc_complex.cuh"
 #include "pc_internal.h"
@@ -67,16 +72,21 @@ struct ApplyTile {
     using C = typename CT<R>::T;
     static constexpr int NT = TX * TY;
     static constexpr int XW = TX + 2, XH = TY + 4, XR = XW * XH;  // x region
-    static constexpr int FW = TX + 1, FH = TY + 2, FR = FW * FH;  // flux region
+    static constexpr int FW = TX + 1, FH = TY + 2, FR = FW * FH;  // flux region (largest; stride FW)
     static constexpr int NXC = (3 * XR + NT - 1) / NT;            // x cells per thread
     static constexpr int NFC = (FR + NT - 1) / NT;                // flux columns per thread
     static constexpr int NSLOT = 4;
 
+    // material value of a node: phase id (MATK 0, kept as an integer so that FP64 kernels spend no
+    // FP64 instruction on it) or inclusion fraction (MATK 1)
+    using MT = typename std::conditional<MATK == 0, int, R>::type;
+
     struct Shared {
         C xs[NSLOT][3][XR];
-        C fs[5][3][FR];  // F_l for l = 0..3, slot 4 = sum_l F_l
+        C fs[5][3][FR];  // F_l for l = 0..3, slot 4 = P_0 (sum_l F_l = 4 P_0)
         R Ct[2][36];
         R rho[2];
+        R srho[2];  // shift * rho per phase
     };
 
     struct Ctx {
@@ -85,6 +95,7 @@ struct ApplyTile {
         C* y;
         const void* mat;
         R shift;
+        bool dot;  // accumulate Re<x, y> for the partial sums
         int a0, b0, k0, tz;
         int p12, p13;
         int64_t plane;  // X * Y
@@ -96,12 +107,12 @@ struct ApplyTile {
         int xoff[NXC];   // wrapped in-plane offset, -1 = no cell
         int xcomp[NXC];  // component
         int xwa[NXC], xwb[NXC];
-        int foff[NFC];   // wrapped in-plane offset of flux column, -1 = none
-        R fmat_cur[NFC], fmat_nxt[NFC];
+        int foff[2][NFC];  // wrapped in-plane offset of flux column per plane parity, -1 = none
+        MT fmat_cur[NFC], fmat_nxt[NFC];
         int ty, tx;
         bool yvalid;
         int yoff;  // in-plane offset of the output column
-        R ymat_cur, ymat_nxt;
+        MT ymat_cur, ymat_nxt;
         C acc_prev[3], acc_cur[3], acc_next[3];
         R dot;
     };
@@ -114,10 +125,26 @@ struct ApplyTile {
         return v;
     }
 
-    static PC_HD R read_mat(const void* mat, int64_t idx) {
+    static PC_HD MT read_mat(const void* mat, int64_t idx) {
         PC_IDX(idx, 1LL << 40);
-        if (MATK == 0) return (R)(static_cast<const uint8_t*>(mat)[idx]);
-        return (R)(static_cast<const float*>(mat)[idx]);
+        if (MATK == 0) return (MT)(static_cast<const uint8_t*>(mat)[idx]);
+        return (MT)(static_cast<const float*>(mat)[idx]);
+    }
+
+    // Flux region of plane kf: columns (a0 + fa, b0 + ob + fb), fa < fw, fb < fh; the outputs of
+    // planes kf +- 1 read their neighbours at a-offset oa.
+    static PC_HD void flux_region(const Ctx& c, int kf, int& oa, int& ob, int& fw, int& fh) {
+        if (FULL) {
+            oa = 1;
+            ob = -1;
+            fw = TX + 1;
+            fh = TY + 2;
+        } else {
+            oa = (kf + 1 + c.p13) & 1;               // i0 of planes kf +- 1
+            ob = ((kf + 1 + c.p12 + c.p13) & 1) - 1;  // j0 of planes kf +- 1, minus 1
+            fw = TX + oa;
+            fh = TY + 1;
+        }
     }
 
     // exp(i (wa phi1 + wb phi2 + wk phi3)) for integer period counts
@@ -153,14 +180,19 @@ struct ApplyTile {
             }
         }
 #pragma unroll
-        for (int i = 0; i < NFC; ++i) {
-            int col = tid + i * NT;
-            r.foff[i] = -1;
-            if (col < FR) {
-                int fa = col % FW, fb = col / FW, wa, wb;
-                int a = wrapc(c.a0 + fa, P.X, wa);
-                int b = wrapc(c.b0 - 1 + fb, P.Y, wb);
-                r.foff[i] = a + P.X * b;
+        for (int q = 0; q < 2; ++q) {
+            int oa, ob, fw, fh;
+            flux_region(c, q, oa, ob, fw, fh);  // the region depends on the plane's parity only
+#pragma unroll
+            for (int i = 0; i < NFC; ++i) {
+                int col = tid + i * NT;
+                r.foff[q][i] = -1;
+                if (col < fw * fh) {
+                    int fa = col % fw, fb = col / fw, wa, wb;
+                    int a = wrapc(c.a0 + fa, P.X, wa);
+                    int b = wrapc(c.b0 + ob + fb, P.Y, wb);
+                    r.foff[q][i] = a + P.X * b;
+                }
             }
         }
         r.tx = tid % TX;
@@ -170,7 +202,7 @@ struct ApplyTile {
         r.yoff = r.yvalid ? ya + P.X * yb : 0;
         for (int a = 0; a < 3; ++a) r.acc_prev[a] = r.acc_cur[a] = r.acc_next[a] = czero((R)0);
         r.dot = (R)0;
-        r.ymat_cur = r.ymat_nxt = (R)0;
+        r.ymat_cur = r.ymat_nxt = (MT)0;
     }
 
     // Read plane kp (any integer, Bloch-extended) of the x region into registers.
@@ -200,24 +232,28 @@ struct ApplyTile {
         }
     }
 
-    static PC_HD void load_fmat(const Ctx& c, Regs& r, int kp, R* dst) {
+    static PC_HD void load_fmat(const Ctx& c, Regs& r, int kp, MT* dst) {
         int wk;
         int k = wrapc(kp, c.P->Z, wk);
+        const int q = kp & 1;
 #pragma unroll
-        for (int i = 0; i < NFC; ++i)
-            dst[i] = (r.foff[i] >= 0) ? read_mat(c.mat, (int64_t)k * c.plane + r.foff[i]) : (R)0;
+        for (int i = 0; i < NFC; ++i) {
+            const int off = q ? r.foff[1][i] : r.foff[0][i];  // selected, not indexed: stays in registers
+            dst[i] = (off >= 0) ? read_mat(c.mat, (int64_t)k * c.plane + off) : (MT)0;
+        }
     }
 
-    static PC_HD R load_ymat(const Ctx& c, const Regs& r, int kp) {
-        if (!r.yvalid || kp < c.k0 || kp >= c.k0 + c.tz) return (R)0;
+    static PC_HD MT load_ymat(const Ctx& c, const Regs& r, int kp) {
+        if (!r.yvalid || kp < c.k0 || kp >= c.k0 + c.tz) return (MT)0;
         return read_mat(c.mat, (int64_t)kp * c.plane + r.yoff);
     }
 
     // Fluxes at one column of plane kf.
-    static PC_HD void flux_column(const Ctx& c, const Shared& sh, int col, int kf, R m, C* fout /*15*/) {
+    static PC_HD void flux_column(const Ctx& c, const Shared& sh, int fa, int fb, int ob, int kf, MT m,
+                                  C* fout /*15*/) {
         const StencilParams<R>& P = *c.P;
-        const int fa = col % FW, fb = col / FW;
-        const int own = (fa + 1) + XW * (fb + 1);
+        const int xb = fb + ob + 2;  // x-region row of the flux node
+        const int own = (fa + 1) + XW * xb;
         int i0 = 0, j0 = 0;
         if (!FULL) {
             i0 = (kf + c.p13) & 1;
@@ -231,9 +267,9 @@ struct ApplyTile {
             int da, db;
             if (FULL) { da = -1; db = -s2; }
             else { da = i0 - 1; db = j0 - ((s2 + 1) >> 1); }
-            const int nb = (fa + 1 + da) + XW * (fb + 1 + db);
+            const int nb = (fa + 1 + da) + XW * (xb + db);
             PC_IDX(fa + 1 + da, XW);
-            PC_IDX(fb + 1 + db, XH);
+            PC_IDX(xb + db, XH);
             const int slot = (s3 > 0) ? sm : sp;  // backward step moves k by -s3
 #pragma unroll
             for (int a = 0; a < 3; ++a) g[l][a] = csub(sh.xs[slot][a][nb], sh.xs[sc][a][own]);
@@ -275,13 +311,25 @@ struct ApplyTile {
         // tau = C_node e
         C t[6];
         if (MATK == 0) {
-            const R* Cp = sh.Ct[m != (R)0 ? 1 : 0];
+            const int ph = m != 0 ? 1 : 0;
+            const R* Cp = sh.Ct[ph];
+            if (warp_all(P.ortho[ph] != 0)) {  // every node of the warp: normal block and shear diagonal only
 #pragma unroll
-            for (int p = 0; p < 6; ++p) {
-                C acc = cscale(Cp[p * 6 + 0], e[0]);
+                for (int p = 0; p < 3; ++p) {
+                    C acc = cscale(Cp[p * 6 + 0], e[0]);
+                    acc = cfma(Cp[p * 6 + 1], e[1], acc);
+                    t[p] = cfma(Cp[p * 6 + 2], e[2], acc);
+                }
 #pragma unroll
-                for (int q = 1; q < 6; ++q) acc = cfma(Cp[p * 6 + q], e[q], acc);
-                t[p] = acc;
+                for (int p = 3; p < 6; ++p) t[p] = cscale(Cp[p * 6 + p], e[p]);
+            } else {
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    C acc = cscale(Cp[p * 6 + 0], e[0]);
+#pragma unroll
+                    for (int q = 1; q < 6; ++q) acc = cfma(Cp[p * 6 + q], e[q], acc);
+                    t[p] = acc;
+                }
             }
         } else {
 #pragma unroll
@@ -317,7 +365,7 @@ struct ApplyTile {
                     Pm[s][a] = cfma(P.Mmix[s * 3 + 2], S[a][2], acc);
                 }
         }
-        // F_l = sum_s c_{s l} P_s and the local sum 4 P_0
+        // F_l = sum_s c_{s l} P_s, and P_0 (the local sum is 4 P_0)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             C u = cadd(Pm[0][a], Pm[1][a]), v = csub(Pm[0][a], Pm[1][a]);
@@ -325,22 +373,26 @@ struct ApplyTile {
             fout[1 * 3 + a] = csub(u, Pm[2][a]);
             fout[2 * 3 + a] = cadd(v, Pm[2][a]);
             fout[3 * 3 + a] = csub(v, Pm[2][a]);
-            fout[4 * 3 + a] = cscale((R)4, Pm[0][a]);
+            fout[4 * 3 + a] = Pm[0][a];
         }
     }
 
     // Phase A of step kf: fluxes of plane kf; stage x plane kf+2; prefetch kf+3 and materials.
     static PC_HD void phaseA(const Ctx& c, Shared& sh, Regs& r, int tid, int kf) {
+        int oa, ob, fw, fh;
+        flux_region(c, kf, oa, ob, fw, fh);
 #pragma unroll
         for (int i = 0; i < NFC; ++i) {
             int col = tid + i * NT;
-            if (col >= FR) continue;
+            if (col >= fw * fh) continue;
+            const int fa = col % fw, fb = col / fw, fidx = fa + FW * fb;
+            PC_IDX(fidx, FR);
             C f[15];
-            flux_column(c, sh, col, kf, r.fmat_cur[i], f);
+            flux_column(c, sh, fa, fb, ob, kf, r.fmat_cur[i], f);
 #pragma unroll
             for (int l = 0; l < 5; ++l)
 #pragma unroll
-                for (int a = 0; a < 3; ++a) sh.fs[l][a][col] = f[l * 3 + a];
+                for (int a = 0; a < 3; ++a) sh.fs[l][a][fidx] = f[l * 3 + a];
         }
         load_fmat(c, r, kf + 1, r.fmat_nxt);
         r.ymat_nxt = load_ymat(c, r, kf);
@@ -364,11 +416,15 @@ struct ApplyTile {
                     db[l] = j0 + ((s2 - 1) >> 1);
                 }
             }
-            const int fbase = r.tx + FW * (r.ty + 1);
+            int oa, ob, fw, fh;
+            flux_region(c, kf, oa, ob, fw, fh);
+            const int fbase = r.tx + FW * (r.ty - ob);  // own column in the flux region of plane kf
 #if !defined(__CUDA_ARCH__) && defined(PC_EMU_CHECK)
+            PC_IDX(r.tx, fw);
+            PC_IDX(r.ty - ob, fh);
             for (int l = 0; l < 4; ++l) {
-                PC_IDX(r.tx + da[l], FW);
-                PC_IDX(r.ty + 1 + db[l], FH);
+                PC_IDX(r.tx + da[l], fw);
+                PC_IDX(r.ty - ob + db[l], fh);
             }
 #endif
             if (kf - 1 >= c.k0) {
@@ -376,24 +432,23 @@ struct ApplyTile {
                 const int nb2 = fbase + da[2] + FW * db[2];
                 const int xo = (r.tx + 1) + XW * (r.ty + 2);
                 const int sl = (kf - 1) & (NSLOT - 1);
-                R rho;
-                if (MATK == 0) rho = sh.rho[r.ymat_cur != (R)0 ? 1 : 0];
-                else rho = sh.rho[0] + r.ymat_cur * (sh.rho[1] - sh.rho[0]);
-                const R sr = c.shift * rho;
-                const int64_t ob = (int64_t)(kf - 1) * c.plane + r.yoff;
-                PC_IDX(ob, c.vstr);
+                R sr;
+                if (MATK == 0) sr = sh.srho[r.ymat_cur != 0 ? 1 : 0];
+                else sr = c.shift * (sh.rho[0] + r.ymat_cur * (sh.rho[1] - sh.rho[0]));
+                const int64_t obase = (int64_t)(kf - 1) * c.plane + r.yoff;
+                PC_IDX(obase, c.vstr);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     C v = cadd(r.acc_prev[a], cadd(sh.fs[0][a][nb0], sh.fs[2][a][nb2]));
                     C xv = sh.xs[sl][a][xo];
                     v = cfma(-sr, xv, v);
-                    c.y[a * c.vstr + ob] = v;
-                    r.dot = cdotre(xv, v, r.dot);
+                    c.y[a * c.vstr + obase] = v;
+                    if (c.dot) r.dot = cdotre(xv, v, r.dot);
                 }
             }
             if (kf >= c.k0 && kf < c.k0 + c.tz) {
 #pragma unroll
-                for (int a = 0; a < 3; ++a) r.acc_cur[a] = csub(r.acc_cur[a], sh.fs[4][a][fbase]);
+                for (int a = 0; a < 3; ++a) r.acc_cur[a] = cfma((R)(-4), sh.fs[4][a][fbase], r.acc_cur[a]);
             }
             if (kf + 1 >= c.k0 && kf + 1 < c.k0 + c.tz) {
                 const int nb1 = fbase + da[1] + FW * db[1];
@@ -421,12 +476,15 @@ struct ApplyTile {
         }
         load_x(c, r, c.k0 + 1);
         load_fmat(c, r, c.k0 - 1, r.fmat_cur);
-        r.ymat_cur = (R)0;
+        r.ymat_cur = (MT)0;
     }
 
     static PC_HD void load_tables(const Ctx& c, Shared& sh, int tid) {
         for (int i = tid; i < 72; i += NT) sh.Ct[i / 36][i % 36] = c.P->C[i / 36][i % 36];
-        if (tid < 2) sh.rho[tid] = c.P->rho[tid];
+        if (tid < 2) {
+            sh.rho[tid] = c.P->rho[tid];
+            sh.srho[tid] = c.shift * c.P->rho[tid];
+        }
     }
 };
 

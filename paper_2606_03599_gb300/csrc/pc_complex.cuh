@@ -79,6 +79,16 @@ template <> PC_HD double2 make_c<double2>(double re, double im) { return make_do
 PC_HD float2 czero(float) { return make_float2(0.f, 0.f); }
 PC_HD double2 czero(double) { return make_double2(0.0, 0.0); }
 
+// True on every active lane of the warp when v holds on all of them (a warp-uniform branch
+// condition: both sides of a per-thread branch would otherwise be issued for the whole warp).
+PC_HD bool warp_all(bool v) {
+#if defined(__CUDA_ARCH__)
+    return __all_sync(__activemask(), v);
+#else
+    return v;
+#endif
+}
+
 // acc + Re(conj(a) * b)
 PC_HD float cdotre(float2 a, float2 b, float acc) { return fmaf(a.x, b.x, fmaf(a.y, b.y, acc)); }
 PC_HD double cdotre(double2 a, double2 b, double acc) { return fma(a.x, b.x, fma(a.y, b.y, acc)); }

@@ -271,7 +271,6 @@ struct Eigs {
     pc_grid* g = nullptr;
     const pc_options* o = nullptr;
     cudaStream_t s = nullptr;
-    cublasHandle_t blas = nullptr;
     double sigma = 0;
     int bs = 4, mmax = 32, mcap = 36;
     std::vector<Space> sp;
@@ -282,6 +281,8 @@ struct Eigs {
     double* dpart = nullptr;
     double* dscale = nullptr;
     cd* dsmall = nullptr;  // device scratch for small GEMM results
+    double* gpart = nullptr;  // partial sums of the Gram kernels
+    size_t gpart_cap = 0;
     int ycap = 0;
     long long pcg_iters = 0;
     int max_pcg = 0, solves = 0, expansions = 0;
@@ -300,31 +301,25 @@ struct Eigs {
 
 static const cuDoubleComplex kOne = {1.0, 0.0}, kZero = {0.0, 0.0}, kMinusOne = {-1.0, 0.0};
 
-static int blas_ok(cublasStatus_t st, const char* what) {
-    if (st != CUBLAS_STATUS_SUCCESS) return fail(PC_ECUDA, std::string("cuBLAS ") + what + " failed");
-    return PC_OK;
+// dh (device, rows x cols) = A^H M B in the mass inner product of space S.
+static int gram_m(Eigs& E, const Space& S, const double2* A, int rows, const double2* B, int cols, cd* dh) {
+    pc_grid* g = E.g;
+    return ts_gram(A, rows, B, cols, S.m, grid_mat(g, S.block), g->matkind, g->rhohat[0], g->rhohat[1],
+                   reinterpret_cast<double2*>(dh), E.gpart, E.gpart_cap, E.s);
 }
 
-// C (rows x cols) = A^H B with A (vs x rows), B (vs x cols), all column-major with ld vs; result to host.
-static int gemm_hn(Eigs& E, const double2* A, int rows, const double2* B, int cols, int64_t vs, std::vector<cd>& out) {
-    PC_TRY(blas_ok(cublasZgemm(E.blas, CUBLAS_OP_C, CUBLAS_OP_N, rows, cols, (int)vs, &kOne,
-                               (const cuDoubleComplex*)A, (int)vs, (const cuDoubleComplex*)B, (int)vs, &kZero,
-                               (cuDoubleComplex*)E.dsmall, rows),
-                   "zgemm(H)"));
-    out.resize((size_t)rows * cols);
-    PC_CUDA_TRY(cudaMemcpyAsync(out.data(), E.dsmall, sizeof(cd) * rows * cols, cudaMemcpyDeviceToHost, E.s));
+static int to_host(Eigs& E, const cd* d, size_t n, std::vector<cd>& out) {
+    out.resize(n);
+    PC_CUDA_TRY(cudaMemcpyAsync(out.data(), d, sizeof(cd) * n, cudaMemcpyDeviceToHost, E.s));
     PC_CUDA_TRY(cudaStreamSynchronize(E.s));
     return PC_OK;
 }
 
-// Cout (vs x cols) = beta Cout + alpha A (vs x k) * Hs (k x cols, host)
+// Cout (vs x cols) = beta Cout + alpha A (vs x k) * Hs (k x cols, host); alpha and beta real.
 static int gemm_nn_host(Eigs& E, const double2* A, int k, const std::vector<cd>& Hs, int cols, double2* Cout,
                         int64_t vs, cuDoubleComplex alpha, cuDoubleComplex beta) {
     PC_CUDA_TRY(cudaMemcpyAsync(E.dsmall, Hs.data(), sizeof(cd) * k * cols, cudaMemcpyHostToDevice, E.s));
-    PC_TRY(blas_ok(cublasZgemm(E.blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)vs, cols, k, &alpha, (const cuDoubleComplex*)A,
-                               (int)vs, (const cuDoubleComplex*)E.dsmall, k, &beta, (cuDoubleComplex*)Cout, (int)vs),
-                   "zgemm(V h)"));
-    return PC_OK;
+    return ts_update(A, k, reinterpret_cast<const double2*>(E.dsmall), cols, Cout, vs, alpha.x, beta.x, E.s);
 }
 
 static int mass(Eigs& E, const Space& S, const double2* x, double2* y, int nvec) {
@@ -332,13 +327,11 @@ static int mass(Eigs& E, const Space& S, const double2* x, double2* y, int nvec)
     return launch_mass(PC_C128, x, y, grid_mat(g, S.block), g->matkind, g->rhohat[0], g->rhohat[1], S.m, E.s, nvec);
 }
 
-// W -= Z (Z^H M W)  (exact M-orthogonal projection off the null basis)
+// W -= Z (Z^H M W)  (exact M-orthogonal projection off the null basis), device-resident
 static int project_null(Eigs& E, Space& S, double2* Wv, int cols) {
     if (S.nz == 0) return PC_OK;
-    PC_TRY(mass(E, S, Wv, E.MW, cols));
-    std::vector<cd> h;
-    PC_TRY(gemm_hn(E, S.Z, S.nz, E.MW, cols, S.vs, h));
-    return gemm_nn_host(E, S.Z, S.nz, h, cols, Wv, S.vs, kMinusOne, kOne);
+    PC_TRY(gram_m(E, S, S.Z, S.nz, Wv, cols, E.dsmall));
+    return ts_update(S.Z, S.nz, reinterpret_cast<const double2*>(E.dsmall), cols, Wv, S.vs, -1.0, 1.0, E.s);
 }
 
 // M-orthonormalise the cols columns of Wv in place (CholQR2); returns R (cols x cols, upper) with
@@ -348,20 +341,19 @@ static int cholqr2(Eigs& E, Space& S, double2* Wv, int cols, int nv, std::vector
     Rtot.assign((size_t)cols * cols, cd(0, 0));
     for (int i = 0; i < cols; ++i) Rtot[i + i * cols] = 1.0;
     for (int pass = 0; pass < 2; ++pass) {
-        PC_TRY(mass(E, S, Wv, E.MW, cols));
         std::vector<cd> G, R, Ri;
-        PC_TRY(gemm_hn(E, Wv, cols, E.MW, cols, S.vs, G));
+        PC_TRY(gram_m(E, S, Wv, cols, Wv, cols, E.dsmall));
+        PC_TRY(to_host(E, E.dsmall, (size_t)cols * cols, G));
         if (!chol_upper(cols, G, R)) {
             if (pass == 1) return fail(PC_ENOCONV, "eigensolver: Krylov block lost rank twice");
             // replace the block by fresh random directions (breakdown of the Krylov space)
             fill_random<<<ctas_for(cols * S.vs), 256, 0, E.s>>>(Wv, cols * S.vs, seed);
             note_launch();
             PC_TRY(project_null(E, S, Wv, cols));
-            for (int rep = 0; rep < 2; ++rep) {
-                PC_TRY(mass(E, S, Wv, E.MW, cols));
-                std::vector<cd> h;
-                PC_TRY(gemm_hn(E, S.V, nv, E.MW, cols, S.vs, h));
-                PC_TRY(gemm_nn_host(E, S.V, nv, h, cols, Wv, S.vs, kMinusOne, kOne));
+            for (int rep = 0; rep < 2 && nv > 0; ++rep) {
+                PC_TRY(gram_m(E, S, S.V, nv, Wv, cols, E.dsmall));
+                PC_TRY(ts_update(S.V, nv, reinterpret_cast<const double2*>(E.dsmall), cols, Wv, S.vs, -1.0, 1.0,
+                                 E.s));
             }
             Rtot.assign((size_t)cols * cols, cd(0, 0));
             pass = -1;  // restart both passes on the new block; R of a replaced block is zero
@@ -392,7 +384,7 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t v
     std::vector<PcgResult> res(nsys);
     if (o.precision == PC_PREC_FP64) {
         PC_TRY(pcg_solve(g, PC_C128, nsys, blocks.data(), E.sigma, E.RHS, E.W, o.inner_tol, o.inner_maxit, res.data(),
-                         E.s));
+                         E.s, o.precond_fp32 != 0));
         for (auto& r : res) {
             E.pcg_iters += r.iters;
             E.max_pcg = std::max(E.max_pcg, r.iters);
@@ -557,13 +549,17 @@ static int expand(Eigs& E, std::vector<int>& active, double tol) {
         double2* Wv = E.W + (int64_t)a * bs * vs;
         PC_TRY(project_null(E, S, Wv, bs));
         const int nv = S.m_exp + bs;  // columns of V present
+        // CGS2 on the device: both passes' coefficients stay in device scratch, one copy to the host
         std::vector<cd> h(nv * bs, cd(0, 0));
         for (int rep = 0; rep < 2; ++rep) {
-            PC_TRY(mass(E, S, Wv, E.MW, bs));
+            cd* dh = E.dsmall + (size_t)rep * nv * bs;
+            PC_TRY(gram_m(E, S, S.V, nv, Wv, bs, dh));
+            PC_TRY(ts_update(S.V, nv, reinterpret_cast<const double2*>(dh), bs, Wv, vs, -1.0, 1.0, E.s));
+        }
+        {
             std::vector<cd> hh;
-            PC_TRY(gemm_hn(E, S.V, nv, E.MW, bs, vs, hh));
-            PC_TRY(gemm_nn_host(E, S.V, nv, hh, bs, Wv, vs, kMinusOne, kOne));
-            for (size_t i = 0; i < h.size(); ++i) h[i] += hh[i];
+            PC_TRY(to_host(E, E.dsmall, (size_t)2 * nv * bs, hh));
+            for (size_t i = 0; i < h.size(); ++i) h[i] = hh[i] + hh[h.size() + i];
         }
         std::vector<cd> R;
         PC_TRY(cholqr2(E, S, Wv, bs, nv, R, 0xC0FFEEull + 7919ull * (uint64_t)E.expansions + (uint64_t)a));
@@ -645,9 +641,9 @@ static int build_null(Eigs& E, Space& S) {
             }
     }
     // M-orthonormalise the null columns
-    PC_TRY(mass(E, S, S.Z, E.Y, S.nz));
     std::vector<cd> G, R, Ri;
-    PC_TRY(gemm_hn(E, S.Z, S.nz, E.Y, S.nz, S.vs, G));
+    PC_TRY(gram_m(E, S, S.Z, S.nz, S.Z, S.nz, E.dsmall));
+    PC_TRY(to_host(E, E.dsmall, (size_t)S.nz * S.nz, G));
     if (!chol_upper(S.nz, G, R)) return fail(PC_ECUDA, "null basis is rank deficient");
     upper_inverse(S.nz, R, Ri);
     PC_TRY(gemm_nn_host(E, S.Z, S.nz, Ri, S.nz, E.AY, S.vs, kOne, kZero));
@@ -660,7 +656,6 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
     auto t0 = std::chrono::steady_clock::now();
     PC_TRY(pc_set_k(g, kappa));
     if (!g->sol) g->sol = new Solver();
-    Solver* SV = g->sol;
     Eigs E;
     E.g = g;
     E.o = opt;
@@ -678,16 +673,6 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
             if (own) cudaStreamDestroy(s);
         }
     } sg{E.s, own_stream};
-    if (!SV->blas) {
-        if (cublasCreate(&SV->blas) != CUBLAS_STATUS_SUCCESS) return fail(PC_ECUDA, "cublasCreate failed");
-        // FP64 GEMMs of the orthogonalisation and Rayleigh-Ritz steps may run on cuBLAS's fixed-point
-        // emulation of FP64 (tensor cores), which keeps FP64 accuracy; PC_GEMM_EMULATION=0 turns it off.
-        const char* em = std::getenv("PC_GEMM_EMULATION");
-        if (!(em && std::string(em) == "0")) cublasSetMathMode(SV->blas, CUBLAS_FP64_EMULATED_FIXEDPOINT_MATH);
-    }
-    E.blas = SV->blas;
-    cublasSetStream(E.blas, E.s);
-    cublasSetPointerMode(E.blas, CUBLAS_POINTER_MODE_HOST);
 
     const bool full = opt->full_space != 0;
     const int nspace = full ? 1 : 4;
@@ -711,7 +696,9 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
     PC_TRY(E.alloc(&E.AY, (size_t)ymax * vs));
     PC_TRY(E.alloc(&E.dpart, (size_t)std::max(ymax * 5, E.bs * nspace) * 304));
     PC_TRY(E.alloc(&E.dscale, (size_t)E.bs * nspace));
-    PC_TRY(E.alloc(&E.dsmall, (size_t)E.mcap * std::max(E.mcap, ymax)));
+    PC_TRY(E.alloc(&E.dsmall, (size_t)2 * E.mcap * std::max(E.mcap, ymax)));
+    E.gpart_cap = (size_t)2 * E.mcap * std::max(E.mcap, 16) * 160;
+    PC_TRY(E.alloc(&E.gpart, E.gpart_cap));
     if (opt->precision == PC_PREC_MIXED) {
         PC_TRY(E.alloc(&E.X32, (size_t)2 * E.bs * nspace * vs));
         PC_TRY(E.alloc(&E.R32, (size_t)2 * E.bs * nspace * vs));
@@ -813,6 +800,7 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
         // recompute Ritz vectors for the merged values and write them in full-space layout
         double2* out = static_cast<double2*>(evecs);
         PC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double2) * (size_t)nev * 3 * g->n, E.s));
+        std::vector<char> used(nev, 0);  // equal eigenvalues of one block get distinct slots
         for (int i = 0; i < nspace; ++i) {
             Space& S = E.sp[i];
             ritz(E, S);
@@ -825,9 +813,10 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
             PC_TRY(gemm_nn_host(E, S.V, mm, Sk, ncand, E.Y, S.vs, kOne, kZero));
             for (int j = 0; j < ncand; ++j) {
                 int slot = -1;
-                for (int q = 0; q < nev; ++q)
-                    if (mblock[q] == S.block && merged[q] == S.lam[j]) slot = q;
+                for (int q = 0; q < nev && slot < 0; ++q)
+                    if (!used[q] && mblock[q] == S.block && merged[q] == S.lam[j]) slot = q;
                 if (slot < 0) continue;
+                used[slot] = 1;
                 double2* dst = out + (size_t)slot * 3 * g->n;
                 if (S.block < 0)
                     PC_CUDA_TRY(cudaMemcpyAsync(dst, E.Y + (int64_t)j * S.vs, sizeof(double2) * S.vs,
@@ -882,6 +871,7 @@ int pc_options_default(pc_options* o) {
     o->verbose = 0;
     o->stream = nullptr;
     o->autotune = 0;
+    o->precond_fp32 = 1;
     return PC_OK;
 }
 

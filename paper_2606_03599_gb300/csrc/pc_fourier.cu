@@ -56,9 +56,17 @@ __device__ __forceinline__ double block_sum(double v) {
     return t;
 }
 
-// Pack: w[comp][k][b][a] * pre-twiddle -> W[comp][par][k'][b][a]; optional scale.
-template <typename C>
-__global__ void fourier_pack(const C* __restrict__ w, C* __restrict__ W, const double2* __restrict__ twa,
+template <typename C> __device__ __forceinline__ C cvt_c(float2 v);
+template <typename C> __device__ __forceinline__ C cvt_c(double2 v);
+template <> __device__ __forceinline__ float2 cvt_c<float2>(float2 v) { return v; }
+template <> __device__ __forceinline__ double2 cvt_c<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 cvt_c<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+template <> __device__ __forceinline__ double2 cvt_c<double2>(float2 v) { return make_double2(v.x, v.y); }
+
+// Pack: w[comp][k][b][a] * pre-twiddle -> W[comp][par][k'][b][a]; optional scale.  The work
+// buffer W may be of lower precision than w (complex64 preconditioning of complex128 vectors).
+template <typename C, typename Ci = C>
+__global__ void fourier_pack(const Ci* __restrict__ w, C* __restrict__ W, const double2* __restrict__ twa,
                              const double2* __restrict__ twb, const double2* __restrict__ twk, int X, int Y,
                              int Z, int nsys, int64_t sys_stride_in, int64_t sys_stride_out, double scale,
                              int conj_tw) {
@@ -75,7 +83,7 @@ __global__ void fourier_pack(const C* __restrict__ w, C* __restrict__ W, const d
         const int par = k & 1, kk = k >> 1;
         C tw = cmul(cmul(ld<C>(twa, a), ld<C>(twb, b)), ld<C>(twk, kk));
         if (conj_tw) tw = conjc(tw);
-        C v = cmul(w[s * sys_stride_in + comp * nb + t], tw);
+        C v = cmul(cvt_c<C>(w[s * sys_stride_in + comp * nb + t]), tw);
         v = cscale((R)scale, v);
         W[s * sys_stride_out + comp * nb + par * (nb / 2) + (int64_t)kk * plane + (int64_t)b * X + a] = v;
     }
@@ -104,8 +112,9 @@ __global__ void fourier_unpack(const C* __restrict__ W, C* __restrict__ z, const
 }
 
 // Unpack with fused partial sums of Re<r_s, z_s> (one partial per CTA) and per-system skip flags.
-template <typename C>
-__global__ void fourier_unpack_dot(const C* __restrict__ W, C* __restrict__ z, const C* __restrict__ r,
+// z and r (type Co) may be of higher precision than the work buffer W.
+template <typename C, typename Co = C>
+__global__ void fourier_unpack_dot(const C* __restrict__ W, Co* __restrict__ z, const Co* __restrict__ r,
                                    const double2* __restrict__ twa, const double2* __restrict__ twb,
                                    const double2* __restrict__ twk, int X, int Y, int Z, int64_t sys_stride,
                                    const int* __restrict__ skip, double* __restrict__ part, int npart) {
@@ -120,9 +129,10 @@ __global__ void fourier_unpack_dot(const C* __restrict__ W, C* __restrict__ z, c
         const int a = (int)(t % X), b = (int)((t / X) % Y), k = (int)(t / plane);
         const int par = k & 1, kk = k >> 1;
         C tw = conjc(cmul(cmul(ld<C>(twa, a), ld<C>(twb, b)), ld<C>(twk, kk)));
-        C v = cmul(W[s * sys_stride + comp * nb + par * (nb / 2) + (int64_t)kk * plane + (int64_t)b * X + a], tw);
+        const Co v = cvt_c<Co>(
+            cmul(W[s * sys_stride + comp * nb + par * (nb / 2) + (int64_t)kk * plane + (int64_t)b * X + a], tw));
         z[s * sys_stride + e] = v;
-        C rv = r[s * sys_stride + e];
+        const Co rv = r[s * sys_stride + e];
         acc += (double)rv.x * (double)v.x + (double)rv.y * (double)v.y;
     }
     acc = block_sum(acc);
@@ -450,17 +460,33 @@ int precond_workspace(pc_grid* g, int dtype, int nsys, void** W) {
 
 // z_s = P_ref r_s for nsys systems (vectors contiguous with stride 3 n_b), blocks in d_sys_block.
 int precond_apply(pc_grid* g, int dtype, int nsys, const void* r, void* z, const int* d_sys_block,
-                  const int* d_skip, double sigma, cudaStream_t s, double* d_part, int* npart_out) {
+                  const int* d_skip, double sigma, cudaStream_t s, double* d_part, int* npart_out, bool fp32_inner) {
     if (!g->pre || !g->k.set) return fail(PC_ESTATE, "preconditioner: pc_set_k first");
     Precond* P = g->pre;
+    const bool lower = dtype == PC_C128 && fp32_inner;  // complex128 vectors, complex64 transforms
+    const int wdt = lower ? PC_C64 : dtype;
     void* W;
-    PC_TRY(precond_workspace(g, dtype, nsys, &W));
+    PC_TRY(precond_workspace(g, wdt, nsys, &W));
     cufftHandle plan;
-    PC_TRY(get_plan(P, g, dtype, nsys, &plan));
+    PC_TRY(get_plan(P, g, wdt, nsys, &plan));
     const int64_t vs = 3 * g->nb;
     const double inv_nb = 1.0 / (double)g->nb;
     const double shift_rho = -sigma * P->rho_ref;
-    if (dtype == PC_C64) {
+    if (lower) {
+        fourier_pack<float2, double2><<<nblocks_for(nsys * vs), 256, 0, s>>>(
+            (const double2*)r, (float2*)W, P->twa, P->twb, P->twk, g->X, g->Y, g->Z, nsys, vs, vs, 1.0, 0);
+        note_launch();
+        PC_TRY(exec_fft(plan, wdt, W, CUFFT_FORWARD, s));
+        precond_symbol_solve<float2, float><<<dim3(nblocks_for(g->nb / 2), nsys), 256, 0, s>>>(
+            (float2*)W, P->d_Aref32, P->ea, P->eb, P->egh, d_sys_block, d_skip, g->X, g->Y, g->Z, vs, shift_rho, inv_nb);
+        note_launch();
+        PC_TRY(exec_fft(plan, wdt, W, CUFFT_INVERSE, s));
+        if (!d_part) return fail(PC_EINVAL, "preconditioner: complex64 transforms need the fused dot");
+        fourier_unpack_dot<float2, double2><<<dim3(unpack_ctas(vs), nsys), 256, 0, s>>>(
+            (const float2*)W, (double2*)z, (const double2*)r, P->twa, P->twb, P->twk, g->X, g->Y, g->Z, vs, d_skip,
+            d_part, unpack_ctas(vs));
+        note_launch();
+    } else if (dtype == PC_C64) {
         fourier_pack<float2><<<nblocks_for(nsys * vs), 256, 0, s>>>((const float2*)r, (float2*)W, P->twa, P->twb,
                                                                   P->twk, g->X, g->Y, g->Z, nsys, vs, vs, 1.0, 0);
         note_launch();

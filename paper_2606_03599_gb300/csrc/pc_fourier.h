@@ -49,9 +49,11 @@ int precond_workspace(pc_grid* g, int dtype, int nsys, void** W);
 // d_skip: optional per-system skip flags (nonzero = leave z_s untouched).
 // With d_part non-null, also writes per-CTA partial sums of Re<r_s, z_s> at d_part[s * npart + cta]
 // (npart returned in *npart_out, equal to unpack_ctas(3 n_b)).
+// fp32_inner (complex128 vectors only, d_part required): the transforms and the symbol solve run
+// in complex64; r is rounded once on the way in and z widened on the way out.
 int precond_apply(pc_grid* g, int dtype, int nsys, const void* r, void* z, const int* d_sys_block,
                   const int* d_skip, double sigma, cudaStream_t s, double* d_part = nullptr,
-                  int* npart_out = nullptr);
+                  int* npart_out = nullptr, bool fp32_inner = false);
 int unpack_ctas(int64_t vs);
 int block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* in, void* out, cudaStream_t s);
 }  // namespace pc

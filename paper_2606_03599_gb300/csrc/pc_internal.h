@@ -3,7 +3,6 @@
 
 #include <cuda_runtime.h>
 #include <cufft.h>
-#include <cublas_v2.h>
 
 #include <cmath>
 #include <cstdint>
@@ -40,6 +39,8 @@ struct StencilParams {
     R rho[2];     // density per phase in hat units
     R Mmix[9];    // Mmix[s*3+m] = (A_hat^-1)_{s m} / (4 h_s); unused when cubic
     R ph[3][2];   // (cos phi_l, sin phi_l)
+    int ortho[2]; // 1 if phase p's C couples no normal strain to a shear stress and no two shears
+                  // (orthotropic in the lattice axes: isotropic, cubic, ...): 12 of 36 entries non-zero
     int N;        // grid size
     int X, Y, Z;  // lattice extents of the vector layout (N/2, N/2, N) or (N, N, N)
 };
@@ -101,6 +102,15 @@ inline void make_stencil_params(StencilParams<R>& P, const double Chat[2][36], c
     for (int p = 0; p < 2; ++p)
         for (int e = 0; e < 36; ++e) P.C[p][e] = (R)(Chat[p][e] * (cubic ? q * q : 1.0));
     for (int p = 0; p < 2; ++p) P.rho[p] = (R)rhohat[p];
+    for (int p = 0; p < 2; ++p) {
+        bool o = true;
+        for (int i = 0; i < 6; ++i)
+            for (int j = 0; j < 6; ++j) {
+                const bool keep = (i < 3 && j < 3) || i == j;
+                if (!keep && Chat[p][i * 6 + j] != 0.0) o = false;
+            }
+        P.ortho[p] = o ? 1 : 0;
+    }
     for (int e = 0; e < 9; ++e) P.Mmix[e] = (R)(Ainv[e] * q);
     for (int l = 0; l < 3; ++l) {
         P.ph[l][0] = (R)std::cos(phi[l]);

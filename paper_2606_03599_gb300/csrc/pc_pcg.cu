@@ -113,32 +113,46 @@ __global__ void pcg_alpha(PcgScal* sc, int* done, const double* part_pq, int spq
     }
 }
 
+// x += alpha p, r -= alpha q with partials of ||r||^2; with zold non-null also partials of
+// Re<r_new, z_old> (flexible CG: the preconditioner is applied in lower precision).
 template <typename C>
 __global__ void pcg_update_xr(C* __restrict__ x, C* __restrict__ r, const C* __restrict__ p, const C* __restrict__ q,
                               const PcgScal* __restrict__ sc, const int* __restrict__ done, int64_t vs,
-                              double* __restrict__ part, int npart) {
+                              double* __restrict__ part, int npart, const C* __restrict__ zold,
+                              double* __restrict__ part_d) {
     const int s = blockIdx.y;
     if (done[s]) return;
     using R = decltype(x[0].x);
     const R a = (R)sc[s].alpha;
-    double acc = 0.0;
+    double acc = 0.0, accd = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = s * vs + e;
         x[i] = cfma(a, p[i], x[i]);
         C rv = cfma(-a, q[i], r[i]);
         r[i] = rv;
         acc += (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
+        if (zold != nullptr) {
+            const C zv = zold[i];
+            accd += (double)rv.x * (double)zv.x + (double)rv.y * (double)zv.y;
+        }
     }
     acc = block_sum_pcg(acc);
     if (threadIdx.x == 0) part[(int64_t)s * npart + blockIdx.x] = acc;
+    if (zold != nullptr) {
+        accd = block_sum_pcg(accd);
+        if (threadIdx.x == 0) part_d[(int64_t)s * npart + blockIdx.x] = accd;
+    }
 }
 
+// beta = rz_new / rz_old (Fletcher-Reeves form), or with part_d non-null the flexible
+// (Polak-Ribiere) form beta = (rz_new - Re<r_new, z_old>) / rz_old.
 __global__ void pcg_beta(PcgScal* sc, int* done, const double* part_rr, int srr, int nrr, const double* part_rz,
-                         int nrz, double tol2, int maxit) {
+                         int nrz, double tol2, int maxit, const double* part_d) {
     const int s = blockIdx.x;
     if (done[s]) return;
     double rr = reduce_partials(part_rr + (int64_t)s * srr, nrr);
     double rz = reduce_partials(part_rz + (int64_t)s * nrz, nrz);
+    double rzd = part_d != nullptr ? reduce_partials(part_d + (int64_t)s * srr, nrr) : 0.0;
     if (threadIdx.x == 0) {
         PcgScal v = sc[s];
         v.iters += 1;
@@ -156,7 +170,7 @@ __global__ void pcg_beta(PcgScal* sc, int* done, const double* part_rr, int srr,
             v.status = PC_EBREAKDOWN;
             v.done = 1;
         } else {
-            v.beta = rz / v.rz;
+            v.beta = (rz - rzd) / v.rz;
             v.rz = rz;
         }
         sc[s] = v;
@@ -283,7 +297,7 @@ static int pcg_work(pc_grid* g, int dtype, int nsys, int64_t vs, bool full, PcgW
     PC_CUDA_TRY(cudaMalloc(&w.Z, vb));
     PC_CUDA_TRY(cudaMalloc(&w.P, vb));
     PC_CUDA_TRY(cudaMalloc(&w.Q, vb));
-    PC_CUDA_TRY(cudaMalloc(&w.part, sizeof(double) * 3 * (size_t)nsys * npm));
+    PC_CUDA_TRY(cudaMalloc(&w.part, sizeof(double) * 4 * (size_t)nsys * npm));
     PC_CUDA_TRY(cudaMalloc(&w.sc, sizeof(PcgScal) * nsys));
     PC_CUDA_TRY(cudaMalloc(&w.done, sizeof(int) * nsys));
     PC_CUDA_TRY(cudaMalloc(&w.blocks, sizeof(int) * 4 * nsys));
@@ -295,7 +309,7 @@ static int pcg_work(pc_grid* g, int dtype, int nsys, int64_t vs, bool full, PcgW
 
 template <typename C>
 static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* Bv, void* Xv,
-                       double tol, int maxit, PcgResult* res, cudaStream_t s) {
+                       double tol, int maxit, PcgResult* res, cudaStream_t s, bool pre32) {
     const bool full = blocks[0] < 0;
     for (int i = 0; i < nsys; ++i)
         if ((blocks[i] < 0) != full) return fail(PC_EINVAL, "pcg: mixing full-space and block systems");
@@ -307,6 +321,9 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
     double* part_a = w->part;                           // stencil <p,q> / ||b||^2
     double* part_b = w->part + (size_t)nsys * npm;      // ||r||^2
     double* part_c = w->part + (size_t)2 * nsys * npm;  // <r,z>
+    // flexible CG when a complex128 solve is preconditioned in complex64: Re<r_new, z_old>
+    const bool flex = pre32 && dtype == PC_C128;
+    double* part_d = flex ? w->part + (size_t)3 * nsys * npm : nullptr;
     const C* B = static_cast<const C*>(Bv);
     C* X = static_cast<C*>(Xv);
     C* R = static_cast<C*>(w->R);
@@ -334,12 +351,12 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
     }
     int nrz = 0;
     auto precondition = [&](const int* skip) -> int {
-        if (!full) return precond_apply(g, dtype, nsys, R, Z, w->blocks, skip, sigma, s, part_c, &nrz);
+        if (!full) return precond_apply(g, dtype, nsys, R, Z, w->blocks, skip, sigma, s, part_c, &nrz, flex);
         const int gb = (int)std::min<int64_t>((nsys * vs + 255) / 256, 152 * 16);
         full_to_blocks<C><<<gb, 256, 0, s>>>(R, static_cast<C*>(Rb), g->N, nsys);
         note_launch();
         int np = 0;
-        PC_TRY(precond_apply(g, dtype, 4 * nsys, Rb, Zb, w->blocks, nullptr, sigma, s, part_c, &np));
+        PC_TRY(precond_apply(g, dtype, 4 * nsys, Rb, Zb, w->blocks, nullptr, sigma, s, part_c, &np, flex));
         nrz = 4 * np;  // the four block partials of a full system are contiguous
         blocks_to_full<C><<<gb, 256, 0, s>>>(static_cast<C*>(Zb), Z, g->N, nsys);
         note_launch();
@@ -376,11 +393,12 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
         PC_TRY(grid_apply(g, dtype, full, items.data(), nsys, part_a, npm, s, &cfg));
         pcg_alpha<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, napc);
         note_launch();
-        pcg_update_xr<C><<<vgrid, 256, 0, s>>>(X, R, P, Q, w->sc, w->done, vs, part_b, npm);
+        pcg_update_xr<C><<<vgrid, 256, 0, s>>>(X, R, P, Q, w->sc, w->done, vs, part_b, npm, flex ? Z : nullptr,
+                                                part_d);
         note_launch();
         PC_CUDA_TRY(cudaGetLastError());
         PC_TRY(precondition(full ? nullptr : w->done));
-        pcg_beta<<<nsys, 256, 0, s>>>(w->sc, w->done, part_b, npm, vc, part_c, nrz, tol2, maxit);
+        pcg_beta<<<nsys, 256, 0, s>>>(w->sc, w->done, part_b, npm, vc, part_c, nrz, tol2, maxit, part_d);
         note_launch();
         pcg_update_p<C><<<vgrid, 256, 0, s>>>(P, Z, w->sc, w->done, vs);
         note_launch();
@@ -395,7 +413,8 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
     auto chunk_graph = [&]() -> int {
         std::vector<double> key = {(double)g->k.version, (double)dtype, (double)nsys, sigma, tol2, (double)maxit,
                                    (double)(uintptr_t)B, (double)(uintptr_t)X, (double)(uintptr_t)g->pre->d_work,
-                                   (double)(uintptr_t)w->R, (double)(timing_enabled() ? 1 : 0), (double)npm};
+                                   (double)(uintptr_t)w->R, (double)(timing_enabled() ? 1 : 0), (double)npm,
+                                   (double)flex};
         for (int i = 0; i < nsys; ++i) key.push_back((double)blocks[i]);
         if (w->gexec == nullptr || w->gkey != key) {
             w->drop_graph();
@@ -464,12 +483,12 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
 }
 
 int pcg_solve(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* B, void* X, double tol,
-              int maxit, PcgResult* res, cudaStream_t s) {
+              int maxit, PcgResult* res, cudaStream_t s, bool pre32) {
     if (nsys <= 0) return PC_OK;
     if (!g->k.set) return fail(PC_ESTATE, "pcg: call pc_set_k first");
     if (!(tol > 0) || maxit < 1) return fail(PC_EINVAL, "pcg: tol must be > 0 and maxit >= 1");
-    if (dtype == PC_C64) return pcg_solve_t<float2>(g, dtype, nsys, blocks, sigma, B, X, tol, maxit, res, s);
-    return pcg_solve_t<double2>(g, dtype, nsys, blocks, sigma, B, X, tol, maxit, res, s);
+    if (dtype == PC_C64) return pcg_solve_t<float2>(g, dtype, nsys, blocks, sigma, B, X, tol, maxit, res, s, false);
+    return pcg_solve_t<double2>(g, dtype, nsys, blocks, sigma, B, X, tol, maxit, res, s, pre32);
 }
 
 }  // namespace pc
@@ -477,5 +496,4 @@ int pcg_solve(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, 
 Solver::~Solver() {
     pcg[0].release();
     pcg[1].release();
-    if (blas) cublasDestroy(blas);
 }

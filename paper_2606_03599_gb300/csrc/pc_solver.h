@@ -1,8 +1,6 @@
 // Solver-side declarations: batched PCG and the shift-invert Krylov-Schur driver.
 #pragma once
 
-#include <cublas_v2.h>
-
 #include <vector>
 
 #include "pc_fourier.h"
@@ -53,9 +51,11 @@ struct PcgWork {
 
 // Solve (A - sigma M) x_s = b_s for nsys systems of the same grid, stacked contiguously
 // (stride 3 m elements); blocks[s] in -1..3 (all full-space or all blocks).  x starts at
-// zero.  Per-system results in res (host, nsys entries).
+// zero.  Per-system results in res (host, nsys entries).  pre32 (complex128 only): apply the
+// preconditioner in complex64 and use the flexible (Polak-Ribiere) beta, which keeps CG
+// convergent under the preconditioner's rounding; the iterates stay complex128.
 int pcg_solve(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* B, void* X,
-              double tol, int maxit, PcgResult* res, cudaStream_t s);
+              double tol, int maxit, PcgResult* res, cudaStream_t s, bool pre32 = false);
 
 // Launch one batch of stencil applies on grid g (items share the layout kind).
 int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nitems, double* dot_partials,
@@ -65,10 +65,21 @@ int launch_mass(int dtype, const void* x, void* y, const void* mat, int matkind,
                 int64_t m, cudaStream_t s, int nvec);
 int launch_transfer(int dtype, const void* src, void* dst, int N, int b, int dir, cudaStream_t s);
 
+// Tall-skinny complex128 products of the outer loop (pc_blas.cu).  Columns are consecutive
+// vectors of 3 m elements (component-major, m nodes).
+// d_out (device, rows x cols, column-major) = A^H W B with W = the nodal mass (node densities
+// rho0 + theta (rho1 - rho0) from mat, repeated over the components) when mat is non-null, else
+// the identity.  d_part: scratch of part_cap doubles for the partial sums.
+int ts_gram(const double2* A, int rows, const double2* B, int cols, int64_t m, const void* mat, int matkind,
+            double rho0, double rho1, double2* d_out, double* d_part, size_t part_cap, cudaStream_t s);
+// C (vs x cols) = beta C + alpha A h with A (vs x k) and h (device, k x cols, column-major);
+// C must not overlap A; with beta == 0 C is only written.
+int ts_update(const double2* A, int k, const double2* d_h, int cols, double2* C, int64_t vs, double alpha,
+              double beta, cudaStream_t s);
+
 }  // namespace pc
 
 struct Solver {
     pc::PcgWork pcg[2];  // complex64 / complex128 workspaces
-    cublasHandle_t blas = nullptr;
     ~Solver();
 };

@@ -119,13 +119,15 @@ def test_pcg_status_codes(pc):
 
 
 @pytest.mark.parametrize("kappa", [[0.3, 0.1, 0.2], [0.0, 0.0, 0.0], [0.5, 0.5, 0.5]])
-@pytest.mark.parametrize("mode", ["blocked", "full", "mixed"])
+@pytest.mark.parametrize("mode", ["blocked", "blocked-pre64", "full", "mixed"])
 def test_eigs_tiny_vs_dense(pc, kappa, mode):
-    """Tiny two-phase cell (N = 8, R = 0.35, seed 1): lowest 12 non-zero eigenvalues."""
+    """Tiny two-phase cell (N = 8, R = 0.35, seed 1): lowest 12 non-zero eigenvalues.
+    blocked-pre64: the FP64 inner PCG with its preconditioner in FP64 too (default: complex64)."""
     g = Grid(pc, two_phase_sphere(8, 0.35, 1))
     try:
         opt = pc.pc_options_default(full_space=int(mode == "full"),
-                                    precision=pc.PC_PREC_MIXED if mode == "mixed" else pc.PC_PREC_FP64)
+                                    precision=pc.PC_PREC_MIXED if mode == "mixed" else pc.PC_PREC_FP64,
+                                    precond_fp32=int(mode != "blocked-pre64"))
         ev, blocks, info = pc.pc_eigs(g.h, kappa, 12, opt=opt)
         dense = O.lowest_nonzero(O.dense_eigvals(g.pb, kappa), 12) * g.to_si
         rel = np.abs(ev - dense) / dense
@@ -189,5 +191,24 @@ def test_eigs_argument_errors(pc):
             pc.pc_eigs(g.h, [0, 0, 0], 0)
         with pytest.raises(pc.PcError):
             pc.pc_eigs(g.h, [0, 0, 0], 10 ** 6)
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("kappa", [[0.5, 0.0, 0.0], [0.0, 0.0, 0.0]])
+def test_eigs_n48_preconditioner_precision_neutral(pc, kappa):
+    """N = 48 two-phase cell: the FP64 solve with the complex64 preconditioner (flexible CG) and
+    with the FP64 preconditioner give the same 20 eigenvalues to 1e-10 relative."""
+    g = Grid(pc, two_phase_sphere(48, 0.35, 2))
+    try:
+        out = {}
+        for p32 in (1, 0):
+            opt = pc.pc_options_default(precond_fp32=p32)
+            ev, _, info = pc.pc_eigs(g.h, kappa, 20, opt=opt)
+            assert info["max_rel_resid"] <= 1e-8
+            out[p32] = (ev, info["pcg_iters"])
+        assert np.abs(out[1][0] - out[0][0]).max() / out[0][0].max() <= 1e-10
+        # complex64 rounding of the preconditioner costs at most a few iterations
+        assert out[1][1] <= 1.3 * out[0][1]
     finally:
         g.close()

@@ -484,7 +484,8 @@ def main():
     nodes_per_launch = st["apply_nodes"][1] / max(1, n_app)
     achieved_tflops = nodes_per_launch * FLOPS_PER_NODE / (app_ms / 1e3) / 1e12
     kind = pc.pc_tuned_config(g, pc.PC_C128, 0, 4 * opt.block_size)[0]
-    kname = {0: "apply_kernel<double>", 1: "apply_tma_kernel<double>", 2: "apply_row_kernel"}[kind]
+    kname = {0: "apply_kernel<double>", 1: "apply_tma_kernel<double>", 2: "apply_row_kernel",
+             3: "split_fill_x + split_flux + split_fill_f + split_gather (two-pass FP64)"}[kind]
     roofline = {"kernel": kname + " (fused block stencil, FP64, autotuned launch)", "bound": "alu",
                 "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,

@@ -11,6 +11,7 @@
 #include "../pc_apply_tile.cuh"
 #include "../pc_apply_tma.cuh"
 #include "../pc_apply_row.cuh"
+#include "../pc_apply_split.cuh"
 
 using namespace pc;
 
@@ -195,11 +196,36 @@ static void emu_row_x(const StencilParams<float>& P, int block, const void* x, v
     emu_run_row<CUBIC, MATK, 0>(P, block, x, y, mat, shift, ctas);
 }
 
+// Same four passes as the two-pass complex128 kernels, scratch poisoned with NaN first so that
+// a read of a cell no pass wrote shows up in the output.
+template <typename R, bool FULL, bool CUBIC, int MATK>
+static void emu_run_split(const StencilParams<R>& P, int block, const void* x, void* y, const void* mat,
+                          double shift) {
+    using T = SplitApply<R, FULL, CUBIC, MATK>;
+    using C = typename CT<R>::T;
+    const SplitGeom G = make_split_geom(P.X, P.Y, P.Z);
+    std::vector<C> xe(3 * G.ne), fe(15 * G.ne);
+    std::memset((void*)xe.data(), 0xFF, sizeof(C) * xe.size());
+    std::memset((void*)fe.data(), 0xFF, sizeof(C) * fe.size());
+    const int p12 = FULL ? 0 : (block >> 1), p13 = FULL ? 0 : (block & 1);
+    const C* xv = static_cast<const C*>(x);
+    for (int c = 0; c < 3; ++c)
+        for (int64_t t = 0; t < G.m; ++t) T::fill_x_interior(G, xv, xe.data(), c, t);
+    for (int64_t gi = 0; gi < G.ghosts; ++gi) T::fill_x_ghost(P, G, xv, xe.data(), gi);
+    R Ct[2][36];
+    for (int i = 0; i < 72; ++i) Ct[i / 36][i % 36] = P.C[i / 36][i % 36];
+    for (int64_t t = 0; t < G.m; ++t) T::flux_node(P, Ct, G, p12, p13, xe.data(), mat, fe.data(), t, true);
+    for (int64_t gi = 0; gi < G.ghosts; ++gi) T::fill_f_ghost(P, G, fe.data(), gi);
+    for (int64_t t = 0; t < G.m; ++t)
+        T::gather_node(P, G, p12, p13, fe.data(), xv, static_cast<C*>(y), mat, (R)shift, t, true);
+}
+
 template <typename R, bool FULL, bool CUBIC, int MATK>
 static int emu_shape(int shape, const StencilParams<R>& P, int block, const void* x, void* y, const void* mat,
                      double shift, int tz) {
     constexpr bool F32 = sizeof(R) == 4;
     switch (shape) {
+        case 30: emu_run_split<R, FULL, CUBIC, MATK>(P, block, x, y, mat, shift); break;
         case 10: emu_run_tma<R, FULL, CUBIC, MATK, 16, (F32 ? 16 : 8)>(P, block, x, y, mat, shift, tz); break;
         case 11: emu_run_tma<R, FULL, CUBIC, MATK, 8, 8>(P, block, x, y, mat, shift, tz); break;
         case 0: emu_run<R, FULL, CUBIC, MATK, 32, 8>(P, block, x, y, mat, shift, tz); break;

@@ -53,8 +53,16 @@ int device_sm_count() {
     return n;
 }
 
-ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool blocks, int matkind) {
+ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool blocks, int matkind, bool scratch_ok) {
     ApplyConfig c;
+    if (dtype == PC_C128 && apply_kernel_mode() == 0 && scratch_ok) {
+        // complex128 is bound by GB300's FP64 pipe: fluxes once per node (two-pass kernels)
+        c.split = true;
+        c.shape = 0;
+        c.tz = Z;
+        c.ctas = split_apply_ctas((int64_t)X * Y * Z);
+        return c;
+    }
     if (apply_kernel_mode() == 0 && blocks && dtype == PC_C64 && X % 2 == 0 && row_geom_fits(X, Y, Z, matkind)) {
         // row-tile kernel: persistent, whole rows per tile
         c.row = true;
@@ -158,6 +166,7 @@ int pc_grid_destroy(pc_grid* g) {
     for (int b = 0; b < 4; ++b) cudaFree(g->d_mat_blk[b]);
     for (int b = 0; b < 4; ++b) cudaFree(g->d_mat_row[b]);
     cudaFree(g->d_dot);
+    cudaFree(g->d_split);
     cudaFree(g->d_err);
     delete g;
     return PC_OK;
@@ -331,6 +340,25 @@ int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nit
                                             dot_partials, dot_stride, g->d_err, s)
                      : launch_apply_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
                                         dot_stride, s);
+    } else if (cfg.split) {
+        StencilParams<double> P = g->P64;
+        P.X = X;
+        P.Y = Y;
+        P.Z = Z;
+        const size_t need = split_scratch_bytes(X, Y, Z, nitems);
+        rc = PC_OK;
+        if (g->split_bytes < need) {
+            // grown outside stream capture: the first launch of every batch shape runs eagerly
+            cudaFree(g->d_split);
+            g->d_split = nullptr;
+            g->split_bytes = 0;
+            cudaError_t e = cudaMalloc(&g->d_split, need);
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(split apply scratch)");
+            else g->split_bytes = need;
+        }
+        if (rc == PC_OK)
+            rc = launch_apply_split_f64(full, g->cubic, g->matkind, P, items, nitems, g->d_split, g->split_bytes,
+                                        dot_partials, dot_stride, s);
     } else {
         StencilParams<double> P = g->P64;
         P.X = X;

@@ -1,0 +1,167 @@
+// Two-pass complex128 stencil apply (see pc_apply_split.cuh): kernels and launcher.
+#include <algorithm>
+
+#include "pc_apply_split.cuh"
+
+namespace pc {
+
+namespace {
+
+constexpr int kSplitMaxItems = 64;
+constexpr int kSplitThreads = 128;
+
+struct SplitBatch {
+    ApplyItem it[kSplitMaxItems];
+    double2* xe[kSplitMaxItems];  // extended x of each item
+    double2* fe[kSplitMaxItems];  // extended fluxes of each item
+    int n;
+};
+
+__device__ __forceinline__ bool item_skipped(const ApplyItem& it) { return it.skip != nullptr && *it.skip; }
+
+// Pass 1: blockIdx.z = item; CTAs with blockIdx.x < nint copy interior cells (blockIdx.y = component),
+// the others (blockIdx.y = 0 only) write the ghost cells of all three components (the only FP64
+// work of the pass: the Bloch phase, computed once per cell).
+template <bool FULL, bool CUBIC, int MATK>
+__global__ void __launch_bounds__(kSplitThreads)
+    split_fill_x(const __grid_constant__ StencilParams<double> P, const __grid_constant__ SplitBatch B,
+                 const __grid_constant__ SplitGeom G, int nint) {
+    using T = SplitApply<double, FULL, CUBIC, MATK>;
+    const ApplyItem& it = B.it[blockIdx.z];
+    if (item_skipped(it)) return;
+    const double2* x = static_cast<const double2*>(it.x);
+    double2* xe = B.xe[blockIdx.z];
+    const int c = blockIdx.y;
+    if ((int)blockIdx.x < nint) {
+        for (int64_t t = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; t < G.m; t += (int64_t)nint * kSplitThreads)
+            T::fill_x_interior(G, x, xe, c, t);
+    } else if (c == 0) {
+        const int nghost = gridDim.x - nint;
+        for (int64_t gi = (blockIdx.x - nint) * (int64_t)kSplitThreads + threadIdx.x; gi < G.ghosts;
+             gi += (int64_t)nghost * kSplitThreads)
+            T::fill_x_ghost(P, G, x, xe, gi);
+    }
+}
+
+// Pass 2: fluxes of every interior node; blockIdx.y = item.
+template <bool FULL, bool CUBIC, int MATK>
+__global__ void __launch_bounds__(kSplitThreads)
+    split_flux(const __grid_constant__ StencilParams<double> P, const __grid_constant__ SplitBatch B,
+               const __grid_constant__ SplitGeom G) {
+    using T = SplitApply<double, FULL, CUBIC, MATK>;
+    __shared__ double Ct[2][36];
+    for (int i = threadIdx.x; i < 72; i += kSplitThreads) Ct[i / 36][i % 36] = P.C[i / 36][i % 36];
+    __syncthreads();
+    const ApplyItem& it = B.it[blockIdx.y];
+    if (item_skipped(it)) return;
+    const int p12 = FULL ? 0 : (it.block >> 1), p13 = FULL ? 0 : (it.block & 1);
+    for (int64_t t = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; t < G.m;
+         t += (int64_t)gridDim.x * kSplitThreads)
+        T::flux_node(P, Ct, G, p12, p13, B.xe[blockIdx.y], it.mat, B.fe[blockIdx.y], t, true);
+}
+
+// Pass 3: ghost cells of F_0..F_3 (12 arrays per cell); blockIdx.y = item.
+template <bool FULL, bool CUBIC, int MATK>
+__global__ void __launch_bounds__(kSplitThreads)
+    split_fill_f(const __grid_constant__ StencilParams<double> P, const __grid_constant__ SplitBatch B,
+                 const __grid_constant__ SplitGeom G) {
+    using T = SplitApply<double, FULL, CUBIC, MATK>;
+    const ApplyItem& it = B.it[blockIdx.y];
+    if (item_skipped(it)) return;
+    for (int64_t gi = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; gi < G.ghosts;
+         gi += (int64_t)gridDim.x * kSplitThreads)
+        T::fill_f_ghost(P, G, B.fe[blockIdx.y], gi);
+}
+
+// Pass 4: outputs and optional Re<x, y> partials (one per CTA, fixed order); blockIdx.y = item.
+template <bool FULL, bool CUBIC, int MATK>
+__global__ void __launch_bounds__(kSplitThreads)
+    split_gather(const __grid_constant__ StencilParams<double> P, const __grid_constant__ SplitBatch B,
+                 const __grid_constant__ SplitGeom G, double* __restrict__ dot_partials, int dot_stride) {
+    using T = SplitApply<double, FULL, CUBIC, MATK>;
+    const ApplyItem& it = B.it[blockIdx.y];
+    if (item_skipped(it)) return;
+    const bool want_dot = dot_partials != nullptr && it.dot_slot >= 0;
+    const int p12 = FULL ? 0 : (it.block >> 1), p13 = FULL ? 0 : (it.block & 1);
+    double dot = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; t < G.m;
+         t += (int64_t)gridDim.x * kSplitThreads)
+        dot += T::gather_node(P, G, p12, p13, B.fe[blockIdx.y], static_cast<const double2*>(it.x),
+                              static_cast<double2*>(it.y), it.mat, it.shift, t, want_dot);
+    if (want_dot) {
+        __shared__ double red[kSplitThreads / 32];
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dot;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int w = 0; w < kSplitThreads / 32; ++w) s += red[w];
+            dot_partials[(int64_t)it.dot_slot * dot_stride + blockIdx.x] = s;
+        }
+    }
+}
+
+template <bool FULL, bool CUBIC, int MATK>
+int launch_split_t(const StencilParams<double>& P, const SplitBatch& B, const SplitGeom& G, double* dp, int ds,
+                   cudaStream_t s) {
+    const int sm = device_sm_count();
+    // interior copy and ghost fill share one launch: CTAs in proportion to their cells
+    const int nint = (int)std::max<int64_t>(1, std::min<int64_t>((G.m + kSplitThreads - 1) / kSplitThreads, 2LL * sm));
+    const int ngh = (int)std::max<int64_t>(1, std::min<int64_t>((G.ghosts + kSplitThreads - 1) / kSplitThreads, sm));
+    split_fill_x<FULL, CUBIC, MATK><<<dim3(nint + ngh, 3, B.n), kSplitThreads, 0, s>>>(P, B, G, nint);
+    note_launch();
+    const int nflux = split_apply_ctas(G.m);
+    split_flux<FULL, CUBIC, MATK><<<dim3(nflux, B.n), kSplitThreads, 0, s>>>(P, B, G);
+    note_launch();
+    split_fill_f<FULL, CUBIC, MATK><<<dim3(ngh, B.n), kSplitThreads, 0, s>>>(P, B, G);
+    note_launch();
+    split_gather<FULL, CUBIC, MATK><<<dim3(nflux, B.n), kSplitThreads, 0, s>>>(P, B, G, dp, ds);
+    note_launch();
+    note_apply_launch();
+    PC_CUDA_TRY(cudaGetLastError());
+    return PC_OK;
+}
+
+}  // namespace
+
+int split_apply_ctas(int64_t m) {
+    // one node per thread up to eight CTAs of 128 threads per SM, grid-stride beyond
+    return (int)std::max<int64_t>(1, std::min<int64_t>((m + kSplitThreads - 1) / kSplitThreads,
+                                                       8LL * device_sm_count()));
+}
+
+size_t split_scratch_bytes(int X, int Y, int Z, int nitems) {
+    const SplitGeom G = make_split_geom(X, Y, Z);
+    return (size_t)std::min(nitems, kSplitMaxItems) * split_item_elems(G) * sizeof(double2);
+}
+
+int launch_apply_split_f64(bool full, bool cubic, int matkind, const StencilParams<double>& P, const ApplyItem* items,
+                           int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s) {
+    const SplitGeom G = make_split_geom(P.X, P.Y, P.Z);
+    const int64_t per = split_item_elems(G);
+    if (dp != nullptr && split_apply_ctas(G.m) > ds)
+        return fail(PC_EINVAL, "apply: launch has more CTAs than partial-sum slots");
+    for (int base = 0; base < nitems; base += kSplitMaxItems) {
+        SplitBatch B;
+        B.n = std::min(nitems - base, kSplitMaxItems);
+        if ((size_t)B.n * per * sizeof(double2) > scratch_bytes) return fail(PC_EINVAL, "apply: split scratch too small");
+        for (int i = 0; i < B.n; ++i) {
+            B.it[i] = items[base + i];
+            double2* w = static_cast<double2*>(scratch) + (int64_t)i * per;
+            B.xe[i] = w;
+            B.fe[i] = w + 3 * G.ne;
+        }
+        int rc;
+        if (full) {
+            if (cubic) rc = matkind ? launch_split_t<true, true, 1>(P, B, G, dp, ds, s) : launch_split_t<true, true, 0>(P, B, G, dp, ds, s);
+            else rc = matkind ? launch_split_t<true, false, 1>(P, B, G, dp, ds, s) : launch_split_t<true, false, 0>(P, B, G, dp, ds, s);
+        } else {
+            if (cubic) rc = matkind ? launch_split_t<false, true, 1>(P, B, G, dp, ds, s) : launch_split_t<false, true, 0>(P, B, G, dp, ds, s);
+            else rc = matkind ? launch_split_t<false, false, 1>(P, B, G, dp, ds, s) : launch_split_t<false, false, 0>(P, B, G, dp, ds, s);
+        }
+        PC_TRY(rc);
+    }
+    return PC_OK;
+}
+
+}  // namespace pc

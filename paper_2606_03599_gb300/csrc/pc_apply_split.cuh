@@ -1,0 +1,313 @@
+// Two-pass stencil apply for complex128 (FP64), written as per-node functions so that
+// the CUDA kernels and a host emulator share the index arithmetic.
+//
+// Operator and layouts as in pc_apply_tile.cuh (Sec. 3: y = (A - shift M) x with the
+// fluxes F_l of the adjoint differences).  On GB300 the FP64 pipe (2 lanes per cycle per
+// SM) bounds a complex128 apply, not memory; the fused tile kernels compute the fluxes of
+// every halo column again in each neighbouring tile and k-chunk, and leave lanes idle where
+// a flux region is not a multiple of the warp width.  Here each node's fluxes are computed
+// exactly once, by one lane, and go through memory (L2 at the solver's grid sizes):
+//
+//   1. fill:   x -> x_e, the Bloch-extended copy of x with one ghost layer on every side
+//              (ghost = wrapped node times exp(i w.phi)); interior cells are a plain copy;
+//   2. flux:   per node, g_l = x_e(node - d_l) - x_e(node), the strain, the stress and the
+//              fluxes F_l and P_0 (sum_l F_l = 4 P_0) -> f_e;
+//   3. fill:   ghost cells of f_e (F_0..F_3) from their wrapped nodes, times exp(i w.phi);
+//   4. gather: y(node) = sum_l F_l(node + d_l) - 4 P_0(node) - shift rho x(node), with
+//              optional partial sums of Re<x, y>.
+//
+// Extended cell (a, b, k), a in [-1, X], b in [-1, Y], k in [-1, Z], has index
+// (a + 1) + Xe ((b + 1) + Ye (k + 1)) with Xe = X + 2, Ye = Y + 2; each of the 3 components
+// of x_e and the 15 values of f_e (F_l of component c at l * 3 + c, P_0 of c at 12 + c) is a
+// separate array of Xe Ye Ze cells.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "pc_apply_tile.cuh"  // PC_IDX (index checks in the host emulator)
+#include "pc_complex.cuh"
+#include "pc_internal.h"
+
+namespace pc {
+
+struct SplitGeom {
+    int X, Y, Z;       // interior extents of the vector layout
+    int Xe, Ye, Ze;    // X + 2, Y + 2, Z + 2
+    int64_t ne;        // cells per extended array
+    int64_t m;         // interior nodes X Y Z
+    int64_t ghosts;    // ghost cells per extended array
+};
+
+inline SplitGeom make_split_geom(int X, int Y, int Z) {
+    SplitGeom G;
+    G.X = X;
+    G.Y = Y;
+    G.Z = Z;
+    G.Xe = X + 2;
+    G.Ye = Y + 2;
+    G.Ze = Z + 2;
+    G.ne = (int64_t)G.Xe * G.Ye * G.Ze;
+    G.m = (int64_t)X * Y * Z;
+    G.ghosts = G.ne - G.m;
+    return G;
+}
+
+// Complex values of scratch per item: x_e (3 arrays) and f_e (15 arrays).
+inline int64_t split_item_elems(const SplitGeom& G) { return 18 * G.ne; }
+
+template <typename R, bool FULL, bool CUBIC, int MATK>
+struct SplitApply {
+    using C = typename CT<R>::T;
+    using MT = typename std::conditional<MATK == 0, int, R>::type;
+
+    static PC_HD int64_t eidx(const SplitGeom& G, int a, int b, int k) {
+        return (a + 1) + (int64_t)G.Xe * ((b + 1) + (int64_t)G.Ye * (k + 1));
+    }
+
+    static PC_HD C phase(const StencilParams<R>& P, int wa, int wb, int wk) {
+        C ph = cmk((R)1, (R)0);
+        const int w[3] = {wa, wb, wk};
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+            if (w[l] != 0) ph = cmul(ph, cmk(P.ph[l][0], w[l] < 0 ? -P.ph[l][1] : P.ph[l][1]));
+        return ph;
+    }
+
+    static PC_HD int wrap1(int v, int n, int& w) {
+        w = v < 0 ? -1 : (v >= n ? 1 : 0);
+        return v - w * n;
+    }
+
+    // Ghost cell number gi (0 <= gi < G.ghosts) -> extended coordinates.  Order: the planes
+    // k = -1 and k = Z (Xe Ye cells each), then for k in [0, Z) the rows b = -1 and b = Y
+    // (Xe cells each), then for k in [0, Z), b in [0, Y) the columns a = -1 and a = X.
+    static PC_HD void ghost_cell(const SplitGeom& G, int64_t gi, int& a, int& b, int& k) {
+        const int64_t pl = (int64_t)G.Xe * G.Ye;
+        if (gi < 2 * pl) {
+            k = gi < pl ? -1 : G.Z;
+            const int64_t r = gi % pl;
+            a = (int)(r % G.Xe) - 1;
+            b = (int)(r / G.Xe) - 1;
+            return;
+        }
+        gi -= 2 * pl;
+        const int64_t rows = 2LL * G.Xe * G.Z;
+        if (gi < rows) {
+            const int64_t row = gi / G.Xe;  // 2 rows per plane
+            k = (int)(row / 2);
+            b = (row & 1) ? G.Y : -1;
+            a = (int)(gi % G.Xe) - 1;
+            return;
+        }
+        gi -= rows;
+        const int64_t col = gi / 2;  // (b, k) pairs
+        a = (gi & 1) ? G.X : -1;
+        b = (int)(col % G.Y);
+        k = (int)(col / G.Y);
+    }
+
+    // Pass 1, interior cell t of component c: plain copy.
+    static PC_HD void fill_x_interior(const SplitGeom& G, const C* x, C* xe, int c, int64_t t) {
+        const int a = (int)(t % G.X), b = (int)((t / G.X) % G.Y), k = (int)(t / ((int64_t)G.X * G.Y));
+        PC_IDX(c * G.m + t, 3 * G.m);
+        xe[c * G.ne + eidx(G, a, b, k)] = x[c * G.m + t];
+    }
+
+    // Pass 1, ghost cell gi (all three components): the wrapped node times its Bloch phase.
+    static PC_HD void fill_x_ghost(const StencilParams<R>& P, const SplitGeom& G, const C* x, C* xe, int64_t gi) {
+        int a, b, k, wa, wb, wk;
+        ghost_cell(G, gi, a, b, k);
+        const int aw = wrap1(a, G.X, wa), bw = wrap1(b, G.Y, wb), kw = wrap1(k, G.Z, wk);
+        const int64_t src = aw + (int64_t)G.X * (bw + (int64_t)G.Y * kw), dst = eidx(G, a, b, k);
+        PC_IDX(src, G.m);
+        PC_IDX(dst, G.ne);
+        const C ph = phase(P, wa, wb, wk);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xe[c * G.ne + dst] = cmul(x[c * G.m + src], ph);
+    }
+
+    // Pass 3, ghost cell gi of the flux arrays F_0..F_3 (12 arrays).
+    static PC_HD void fill_f_ghost(const StencilParams<R>& P, const SplitGeom& G, C* fe, int64_t gi) {
+        int a, b, k, wa, wb, wk;
+        ghost_cell(G, gi, a, b, k);
+        if (a < 0) return;  // the gather reads a in [0, X] only
+        const int aw = wrap1(a, G.X, wa), bw = wrap1(b, G.Y, wb), kw = wrap1(k, G.Z, wk);
+        const int64_t src = eidx(G, aw, bw, kw), dst = eidx(G, a, b, k);
+        PC_IDX(src, G.ne);
+        const C ph = phase(P, wa, wb, wk);
+#pragma unroll
+        for (int f = 0; f < 12; ++f) fe[f * G.ne + dst] = cmul(fe[f * G.ne + src], ph);
+    }
+
+    static PC_HD MT read_mat(const void* mat, int64_t t) {
+        if (MATK == 0) return (MT)(static_cast<const uint8_t*>(mat)[t]);
+        return (MT)(static_cast<const float*>(mat)[t]);
+    }
+
+    // Pass 2, interior node t: fluxes F_l (l = 0..3) and P_0 of the three components.
+    // Ct: the two stiffness tables (shared memory on the device).
+    static PC_HD void flux_node(const StencilParams<R>& P, const R (*Ct)[36], const SplitGeom& G, int p12, int p13,
+                                const C* xe, const void* mat, C* fe, int64_t t, bool uniform_ortho_ok) {
+        const int a = (int)(t % G.X), b = (int)((t / G.X) % G.Y), k = (int)(t / ((int64_t)G.X * G.Y));
+        const int64_t own = eidx(G, a, b, k);
+        int da = -1, j0 = 0;
+        if (!FULL) {
+            da = ((k + p13) & 1) - 1;
+            j0 = (k + p12 + p13) & 1;
+        }
+        C g[4][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const C* xc = xe + c * G.ne;
+            const C xo = xc[own];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int s2 = (l < 2) ? 1 : -1, s3 = (l & 1) ? -1 : 1;
+                const int db = FULL ? -s2 : j0 - ((s2 + 1) >> 1);
+                const int64_t nb = eidx(G, a + da, b + db, k - s3);
+                PC_IDX(nb, G.ne);
+                g[l][c] = csub(xc[nb], xo);
+            }
+        }
+        C H[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const C u = cadd(g[0][c], g[1][c]), v = cadd(g[2][c], g[3][c]);
+            const C w = csub(g[0][c], g[1][c]), z = csub(g[2][c], g[3][c]);
+            H[0][c] = cadd(u, v);
+            H[1][c] = csub(u, v);
+            H[2][c] = cadd(w, z);
+        }
+        C Gm[3][3];
+        if (CUBIC) {
+#pragma unroll
+            for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Gm[mm][c] = H[mm][c];
+        } else {
+#pragma unroll
+            for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    C acc = cscale(P.Mmix[0 * 3 + mm], H[0][c]);
+                    acc = cfma(P.Mmix[1 * 3 + mm], H[1][c], acc);
+                    Gm[mm][c] = cfma(P.Mmix[2 * 3 + mm], H[2][c], acc);
+                }
+        }
+        C e[6];
+        e[0] = Gm[0][0];
+        e[1] = Gm[1][1];
+        e[2] = Gm[2][2];
+        e[3] = cadd(Gm[2][1], Gm[1][2]);
+        e[4] = cadd(Gm[2][0], Gm[0][2]);
+        e[5] = cadd(Gm[1][0], Gm[0][1]);
+        const MT mv = read_mat(mat, t);
+        C tt[6];
+        if (MATK == 0) {
+            const int ph = mv != 0 ? 1 : 0;
+            const R* Cp = Ct[ph];
+            if (uniform_ortho_ok && warp_all(P.ortho[ph] != 0)) {  // normal block and shear diagonal only
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                    C acc = cscale(Cp[p * 6 + 0], e[0]);
+                    acc = cfma(Cp[p * 6 + 1], e[1], acc);
+                    tt[p] = cfma(Cp[p * 6 + 2], e[2], acc);
+                }
+#pragma unroll
+                for (int p = 3; p < 6; ++p) tt[p] = cscale(Cp[p * 6 + p], e[p]);
+            } else {
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    C acc = cscale(Cp[p * 6 + 0], e[0]);
+#pragma unroll
+                    for (int q = 1; q < 6; ++q) acc = cfma(Cp[p * 6 + q], e[q], acc);
+                    tt[p] = acc;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int p = 0; p < 6; ++p) {
+                const R c0 = Ct[0][p * 6 + 0];
+                C acc = cscale(c0 + (R)mv * (Ct[1][p * 6 + 0] - c0), e[0]);
+#pragma unroll
+                for (int q = 1; q < 6; ++q) {
+                    const R cq = Ct[0][p * 6 + q];
+                    acc = cfma(cq + (R)mv * (Ct[1][p * 6 + q] - cq), e[q], acc);
+                }
+                tt[p] = acc;
+            }
+        }
+        C S[3][3];
+        S[0][0] = tt[0]; S[0][1] = tt[5]; S[0][2] = tt[4];
+        S[1][0] = tt[5]; S[1][1] = tt[1]; S[1][2] = tt[3];
+        S[2][0] = tt[4]; S[2][1] = tt[3]; S[2][2] = tt[2];
+        C Pm[3][3];
+        if (CUBIC) {
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Pm[s][c] = S[c][s];
+        } else {
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    C acc = cscale(P.Mmix[s * 3 + 0], S[c][0]);
+                    acc = cfma(P.Mmix[s * 3 + 1], S[c][1], acc);
+                    Pm[s][c] = cfma(P.Mmix[s * 3 + 2], S[c][2], acc);
+                }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const C u = cadd(Pm[0][c], Pm[1][c]), v = csub(Pm[0][c], Pm[1][c]);
+            fe[(0 * 3 + c) * G.ne + own] = cadd(u, Pm[2][c]);
+            fe[(1 * 3 + c) * G.ne + own] = csub(u, Pm[2][c]);
+            fe[(2 * 3 + c) * G.ne + own] = cadd(v, Pm[2][c]);
+            fe[(3 * 3 + c) * G.ne + own] = csub(v, Pm[2][c]);
+            fe[(12 + c) * G.ne + own] = Pm[0][c];
+        }
+    }
+
+    // Pass 4, interior node t: y = sum_l F_l(node + d_l) - 4 P_0 - shift rho x; returns Re<x, y>
+    // of the node when want_dot.
+    static PC_HD R gather_node(const StencilParams<R>& P, const SplitGeom& G, int p12, int p13, const C* fe,
+                               const C* x, C* y, const void* mat, R shift, int64_t t, bool want_dot) {
+        const int a = (int)(t % G.X), b = (int)((t / G.X) % G.Y), k = (int)(t / ((int64_t)G.X * G.Y));
+        int da = 1, j0 = 0;
+        if (!FULL) {
+            da = (k + p13) & 1;
+            j0 = (k + p12 + p13) & 1;
+        }
+        const MT mv = read_mat(mat, t);
+        R rho;
+        if (MATK == 0) rho = P.rho[mv != 0 ? 1 : 0];
+        else rho = P.rho[0] + (R)mv * (P.rho[1] - P.rho[0]);
+        const R sr = shift * rho;
+        const int64_t own = eidx(G, a, b, k);
+        int64_t nb[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int s2 = (l < 2) ? 1 : -1, s3 = (l & 1) ? -1 : 1;
+            const int db = FULL ? s2 : j0 + ((s2 - 1) >> 1);
+            nb[l] = eidx(G, a + da, b + db, k + s3);
+            PC_IDX(nb[l], G.ne);
+        }
+        R dot = (R)0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            C v = cadd(cadd(fe[(0 * 3 + c) * G.ne + nb[0]], fe[(1 * 3 + c) * G.ne + nb[1]]),
+                       cadd(fe[(2 * 3 + c) * G.ne + nb[2]], fe[(3 * 3 + c) * G.ne + nb[3]]));
+            v = cfma((R)(-4), fe[(12 + c) * G.ne + own], v);
+            const C xv = x[c * G.m + t];
+            v = cfma(-sr, xv, v);
+            y[c * G.m + t] = v;
+            if (want_dot) dot = cdotre(xv, v, dot);
+        }
+        return dot;
+    }
+};
+
+}  // namespace pc

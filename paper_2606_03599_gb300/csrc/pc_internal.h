@@ -74,15 +74,23 @@ bool row_geom_fits(int X, int Y, int Z, int matkind);
 int device_sm_count();
 int launch_apply_tma_f64(bool full, bool cubic, int matkind, int shape, const StencilParams<double>& P,
                          const ApplyItem* items, int nitems, int tz, double* dp, int ds, int* err, cudaStream_t s);
+// Two-pass complex128 apply (fluxes once per node through memory): scratch of split_scratch_bytes.
+int launch_apply_split_f64(bool full, bool cubic, int matkind, const StencilParams<double>& P, const ApplyItem* items,
+                           int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s);
+size_t split_scratch_bytes(int X, int Y, int Z, int nitems);
+int split_apply_ctas(int64_t m);
 
 struct ApplyConfig {
-    int shape;  // tile code (of the TMA kernel when tma, else of the register-staged kernel)
-    int tz;     // planes per CTA
-    int ctas;   // CTAs per item (row kernel: CTAs of the persistent launch)
-    bool tma;   // TMA-staged kernel (quarter grids of even width >= 8)
+    int shape = 0;     // tile code (of the TMA kernel when tma, else of the register-staged kernel)
+    int tz = 1;        // planes per CTA
+    int ctas = 1;      // CTAs per item (row kernel: CTAs of the persistent launch)
+    bool tma = false;  // TMA-staged kernel (quarter grids of even width >= 8)
     bool row = false;  // row-tile kernel (complex64 parity blocks, X even)
+    bool split = false;  // two-pass complex128 kernels (flux, then gather)
 };
-ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool blocks = false, int matkind = 0);
+// scratch_ok = false: only kernels that need no scratch memory of their own (no two-pass apply).
+ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool blocks = false, int matkind = 0,
+                                bool scratch_ok = true);
 // Launch configuration for a grid layout: the autotuned one when present, else the heuristic.
 ApplyConfig apply_config_for(const pc_grid* g, bool full, int nitems, int dtype);
 bool tuned_config(int X, int Y, int Z, int dtype, bool full, int matkind, bool cubic, int nitems, ApplyConfig* out);
@@ -175,6 +183,8 @@ struct pc_grid {
     int items_cap = 0;
     double* d_dot = nullptr;
     int dot_cap = 0;
+    void* d_split = nullptr;  // scratch of the two-pass complex128 apply (extended x and fluxes)
+    size_t split_bytes = 0;
     // preconditioner / solver workspaces are attached by their modules
     struct Precond* pre = nullptr;
     struct Solver* sol = nullptr;

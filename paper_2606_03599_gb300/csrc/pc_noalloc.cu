@@ -79,7 +79,8 @@ extern "C" int pc_block_apply_dot_noalloc(pc_grid* g, int block, int dtype, cons
     if (nodes > kNoAllocMaxNodes)
         return fail(PC_EINVAL, "pc_block_apply_dot_noalloc: " + std::to_string(nodes) +
                                    " nodes exceed the static-scratch limit of " + std::to_string(kNoAllocMaxNodes));
-    const ApplyConfig cfg = choose_apply_config(full ? g->N : g->X, full ? g->N : g->Y, g->Z, 1, dtype);
+    const ApplyConfig cfg = choose_apply_config(full ? g->N : g->X, full ? g->N : g->Y, g->Z, 1, dtype, false, 0,
+                                                false /* no kernel that needs scratch of its own */);
     if (cfg.ctas > kNoAllocPartials)
         return fail(PC_EINVAL, "pc_block_apply_dot_noalloc: launch needs " + std::to_string(cfg.ctas) +
                                    " partial sums, static scratch holds " + std::to_string(kNoAllocPartials));

@@ -66,13 +66,14 @@ void load_locked() {
         if (std::sscanf(line.c_str() + q1 + 1, " : {\"kind\": %d, \"shape\": %d, \"tz\": %d, \"ctas\": %d", &kind, &shape,
                         &tz, &ctas) != 4)
             continue;
-        if (kind < 0 || kind > 2 || ctas < 1) continue;
+        if (kind < 0 || kind > 3 || ctas < 1) continue;
         ApplyConfig c;
         c.shape = shape;
         c.tz = tz;
         c.ctas = ctas;
         c.tma = kind == 1;
         c.row = kind == 2;
+        c.split = kind == 3;
         g_tuned[key] = c;
     }
 }
@@ -82,7 +83,7 @@ void append_locked(const std::string& key, const ApplyConfig& c, double us) {
     if (!path) return;
     std::ofstream f(path, std::ios::app);
     if (!f) return;
-    f << "\"" << key << "\": {\"kind\": " << (c.row ? 2 : (c.tma ? 1 : 0)) << ", \"shape\": " << c.shape
+    f << "\"" << key << "\": {\"kind\": " << (c.split ? 3 : (c.row ? 2 : (c.tma ? 1 : 0))) << ", \"shape\": " << c.shape
       << ", \"tz\": " << c.tz << ", \"ctas\": " << c.ctas << ", \"us\": " << us << "}\n";
 }
 
@@ -95,7 +96,9 @@ bool tuned_config(int X, int Y, int Z, int dtype, bool full, int matkind, bool c
     if (it == g_tuned.end()) return false;
     *out = it->second;
     // a tuned chunking for a bucket is reused for every batch size in it: recount the CTAs
-    if (out->row) {
+    if (out->split) {
+        out->ctas = split_apply_ctas((int64_t)X * Y * Z);
+    } else if (out->row) {
         out->ctas = row_apply_ctas(X, Y, Z, matkind, nitems, out->tz);
     } else {
         const int tx = out->tma ? ((out->shape == 0) ? 16 : 8) : tile_tx(out->shape);
@@ -136,6 +139,15 @@ static int time_candidate(pc_grid* g, int dtype, bool full, std::vector<ApplyIte
 static std::vector<ApplyConfig> candidates(int X, int Y, int Z, int dtype, bool full, int matkind, int nitems) {
     std::vector<ApplyConfig> out;
     const int sm = device_sm_count();
+    if (dtype == PC_C128) {
+        ApplyConfig c;
+        c.split = true;
+        c.tma = false;
+        c.shape = 0;
+        c.tz = Z;
+        c.ctas = split_apply_ctas((int64_t)X * Y * Z);
+        out.push_back(c);
+    }
     auto chunkings = [&](int tiles, int per_sm, ApplyConfig base, int minplanes) {
         const long target = (long)sm * per_sm;
         long nch = (target + (long)tiles * nitems - 1) / ((long)tiles * nitems);
@@ -224,7 +236,7 @@ int autotune_layout(pc_grid* g, int dtype, bool full, int nitems, cudaStream_t s
         if (rc != PC_OK) break;
         if (verbose)
             std::fprintf(stderr, "[pcband tune] %s kind=%s shape=%d tz=%d ctas=%d: %.1f us\n", key.c_str(),
-                         c.row ? "row" : (c.tma ? "tma" : "regs"), c.shape, c.tz, c.ctas, us);
+                         c.split ? "split" : (c.row ? "row" : (c.tma ? "tma" : "regs")), c.shape, c.tz, c.ctas, us);
         if (us < best_us) {
             best_us = us;
             best = c;
@@ -266,7 +278,7 @@ extern "C" int pc_tuned_config(const pc_grid* g, int dtype, int layout, int nite
     if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_tuned_config: bad dtype");
     if (layout != 0 && layout != 1) return fail(PC_EINVAL, "pc_tuned_config: layout must be 0 or 1");
     const ApplyConfig c = apply_config_for(g, layout == 1, nitems < 1 ? 1 : nitems, dtype);
-    *kind = c.row ? 2 : (c.tma ? 1 : 0);
+    *kind = c.split ? 3 : (c.row ? 2 : (c.tma ? 1 : 0));
     *shape = c.shape;
     *tz = c.tz;
     *ctas = c.ctas;

@@ -158,26 +158,25 @@ struct SplitApply {
             da = ((k + p13) & 1) - 1;
             j0 = (k + p12 + p13) & 1;
         }
-        C g[4][3];
+        // H_s = sum_l c_{s l} g_l with g_l = n_l - x(node): the own value cancels from H_1 and H_2
+        // (their sign rows sum to zero) and enters H_0 as -4 x(node), so the four differences are
+        // never formed (16 instead of 22 FP64 operations per component).
+        C H[3][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const C* xc = xe + c * G.ne;
-            const C xo = xc[own];
+            C n[4];
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
                 const int s2 = (l < 2) ? 1 : -1, s3 = (l & 1) ? -1 : 1;
                 const int db = FULL ? -s2 : j0 - ((s2 + 1) >> 1);
                 const int64_t nb = eidx(G, a + da, b + db, k - s3);
                 PC_IDX(nb, G.ne);
-                g[l][c] = csub(xc[nb], xo);
+                n[l] = xc[nb];
             }
-        }
-        C H[3][3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const C u = cadd(g[0][c], g[1][c]), v = cadd(g[2][c], g[3][c]);
-            const C w = csub(g[0][c], g[1][c]), z = csub(g[2][c], g[3][c]);
-            H[0][c] = cadd(u, v);
+            const C u = cadd(n[0], n[1]), v = cadd(n[2], n[3]);
+            const C w = csub(n[0], n[1]), z = csub(n[2], n[3]);
+            H[0][c] = cfma((R)(-4), xc[own], cadd(u, v));
             H[1][c] = csub(u, v);
             H[2][c] = cadd(w, z);
         }

@@ -85,33 +85,35 @@ struct SplitApply {
     // k = -1 and k = Z (Xe Ye cells each), then for k in [0, Z) the rows b = -1 and b = Y
     // (Xe cells each), then for k in [0, Z), b in [0, Y) the columns a = -1 and a = X.
     static PC_HD void ghost_cell(const SplitGeom& G, int64_t gi, int& a, int& b, int& k) {
-        const int64_t pl = (int64_t)G.Xe * G.Ye;
-        if (gi < 2 * pl) {
-            k = gi < pl ? -1 : G.Z;
-            const int64_t r = gi % pl;
-            a = (int)(r % G.Xe) - 1;
-            b = (int)(r / G.Xe) - 1;
+        uint32_t g = (uint32_t)gi;  // 32-bit arithmetic: ghost counts are far below 2^32
+        const uint32_t pl = (uint32_t)G.Xe * (uint32_t)G.Ye, xe = (uint32_t)G.Xe;
+        if (g < 2 * pl) {
+            k = g < pl ? -1 : G.Z;
+            const uint32_t r = g < pl ? g : g - pl, rq = r / xe;
+            a = (int)(r - rq * xe) - 1;
+            b = (int)rq - 1;
             return;
         }
-        gi -= 2 * pl;
-        const int64_t rows = 2LL * G.Xe * G.Z;
-        if (gi < rows) {
-            const int64_t row = gi / G.Xe;  // 2 rows per plane
-            k = (int)(row / 2);
+        g -= 2 * pl;
+        const uint32_t rows = 2u * xe * (uint32_t)G.Z;
+        if (g < rows) {
+            const uint32_t row = g / xe;  // 2 rows per plane
+            k = (int)(row >> 1);
             b = (row & 1) ? G.Y : -1;
-            a = (int)(gi % G.Xe) - 1;
+            a = (int)(g - row * xe) - 1;
             return;
         }
-        gi -= rows;
-        const int64_t col = gi / 2;  // (b, k) pairs
-        a = (gi & 1) ? G.X : -1;
-        b = (int)(col % G.Y);
-        k = (int)(col / G.Y);
+        g -= rows;
+        const uint32_t col = g >> 1, cq = col / (uint32_t)G.Y;  // (b, k) pairs
+        a = (g & 1) ? G.X : -1;
+        b = (int)(col - cq * (uint32_t)G.Y);
+        k = (int)cq;
     }
 
     // Pass 1, interior cell t of component c: plain copy.
     static PC_HD void fill_x_interior(const SplitGeom& G, const C* x, C* xe, int c, int64_t t) {
-        const int a = (int)(t % G.X), b = (int)((t / G.X) % G.Y), k = (int)(t / ((int64_t)G.X * G.Y));
+        int a, b, k;
+        split3(t, G.X, G.Y, a, b, k);
         PC_IDX(c * G.m + t, 3 * G.m);
         xe[c * G.ne + eidx(G, a, b, k)] = x[c * G.m + t];
     }
@@ -151,7 +153,8 @@ struct SplitApply {
     // Ct: the two stiffness tables (shared memory on the device).
     static PC_HD void flux_node(const StencilParams<R>& P, const R (*Ct)[36], const SplitGeom& G, int p12, int p13,
                                 const C* xe, const void* mat, C* fe, int64_t t, bool uniform_ortho_ok) {
-        const int a = (int)(t % G.X), b = (int)((t / G.X) % G.Y), k = (int)(t / ((int64_t)G.X * G.Y));
+        int a, b, k;
+        split3(t, G.X, G.Y, a, b, k);
         const int64_t own = eidx(G, a, b, k);
         int da = -1, j0 = 0;
         if (!FULL) {
@@ -274,7 +277,8 @@ struct SplitApply {
     // of the node when want_dot.
     static PC_HD R gather_node(const StencilParams<R>& P, const SplitGeom& G, int p12, int p13, const C* fe,
                                const C* x, C* y, const void* mat, R shift, int64_t t, bool want_dot) {
-        const int a = (int)(t % G.X), b = (int)((t / G.X) % G.Y), k = (int)(t / ((int64_t)G.X * G.Y));
+        int a, b, k;
+        split3(t, G.X, G.Y, a, b, k);
         int da = 1, j0 = 0;
         if (!FULL) {
             da = (k + p13) & 1;

@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace pc {
 
@@ -84,6 +85,24 @@ PC_HD double2 czero(double) { return make_double2(0.0, 0.0); }
 PC_HD bool warp_all(bool v) {
 #if defined(__CUDA_ARCH__)
     return __all_sync(__activemask(), v);
+#else
+    return v;
+#endif
+}
+
+// (a, b, k) of the linear index t = a + X (b + Y k) in 32-bit unsigned arithmetic (every
+// per-vector index of the library is below 2^32; 64-bit division is a long software sequence).
+PC_HD void split3(int64_t t, int X, int Y, int& a, int& b, int& k) {
+    const uint32_t u = (uint32_t)t, q = u / (uint32_t)X;
+    a = (int)(u - q * (uint32_t)X);
+    k = (int)(q / (uint32_t)Y);
+    b = (int)(q - (uint32_t)k * (uint32_t)Y);
+}
+
+// True on every active lane when v holds on at least one of them.
+PC_HD bool warp_any(bool v) {
+#if defined(__CUDA_ARCH__)
+    return __any_sync(__activemask(), v);
 #else
     return v;
 #endif

@@ -37,12 +37,12 @@ template <> struct CR<float2> { using R = float; };
 template <> struct CR<double2> { using R = double; };
 
 template <typename C> __device__ __forceinline__ C conjc(C a) { a.y = -a.y; return a; }
-template <typename C> __device__ __forceinline__ C ld(const double2* t, int i);
-template <> __device__ __forceinline__ double2 ld<double2>(const double2* t, int i) { return t[i]; }
-template <> __device__ __forceinline__ float2 ld<float2>(const double2* t, int i) {
-    double2 v = t[i];
-    return make_float2((float)v.x, (float)v.y);
-}
+// Phase tables in the working precision of the transform (complex64 transforms read tables
+// rounded once on the host: no per-use FP64 conversion, which runs on GB300's narrow FP64 pipe).
+template <typename C> struct TabT;
+template <> struct TabT<float2> { using T = float2; };
+template <> struct TabT<double2> { using T = double2; };
+template <typename C> __device__ __forceinline__ C ld(const typename TabT<C>::T* t, int i) { return t[i]; }
 
 // Sum over the CTA (any blockDim multiple of 32 up to 1024); result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v) {
@@ -66,8 +66,8 @@ template <> __device__ __forceinline__ double2 cvt_c<double2>(float2 v) { return
 // Pack: w[comp][k][b][a] * pre-twiddle -> W[comp][par][k'][b][a]; optional scale.  The work
 // buffer W may be of lower precision than w (complex64 preconditioning of complex128 vectors).
 template <typename C, typename Ci = C>
-__global__ void fourier_pack(const Ci* __restrict__ w, C* __restrict__ W, const double2* __restrict__ twa,
-                             const double2* __restrict__ twb, const double2* __restrict__ twk, int X, int Y,
+__global__ void fourier_pack(const Ci* __restrict__ w, C* __restrict__ W, const typename TabT<C>::T* __restrict__ twa,
+                             const typename TabT<C>::T* __restrict__ twb, const typename TabT<C>::T* __restrict__ twk, int X, int Y,
                              int Z, int nsys, int64_t sys_stride_in, int64_t sys_stride_out, double scale,
                              int conj_tw) {
     const int64_t plane = (int64_t)X * Y, nb = plane * Z;
@@ -75,11 +75,13 @@ __global__ void fourier_pack(const Ci* __restrict__ w, C* __restrict__ W, const 
     using R = typename CR<C>::R;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = e / (3 * nb);
-        const int64_t rem = e - s * 3 * nb;
-        const int comp = (int)(rem / nb);
-        const int64_t t = rem - comp * nb;
-        const int a = (int)(t % X), b = (int)((t / X) % Y), k = (int)(t / plane);
+        const uint32_t e32 = (uint32_t)e, nb32 = (uint32_t)nb;  // every index here is below 2^32
+        const uint32_t q3 = e32 / nb32;  // s * 3 + comp
+        const int64_t s = q3 / 3u;
+        const int comp = (int)(q3 - 3u * (uint32_t)s);
+        const int64_t t = e32 - q3 * nb32;
+        int a, b, k;
+        split3(t, X, Y, a, b, k);
         const int par = k & 1, kk = k >> 1;
         C tw = cmul(cmul(ld<C>(twa, a), ld<C>(twb, b)), ld<C>(twk, kk));
         if (conj_tw) tw = conjc(tw);
@@ -92,17 +94,18 @@ __global__ void fourier_pack(const Ci* __restrict__ w, C* __restrict__ W, const 
 // Unpack: W[comp][par][k'][b][a] * post-twiddle -> z[comp][k][b][a]; optional fused
 // Re<r, z> partial sums per system (one partial per CTA, partial index blockIdx.x).
 template <typename C>
-__global__ void fourier_unpack(const C* __restrict__ W, C* __restrict__ z, const double2* __restrict__ twa,
-                               const double2* __restrict__ twb, const double2* __restrict__ twk, int X, int Y,
+__global__ void fourier_unpack(const C* __restrict__ W, C* __restrict__ z, const typename TabT<C>::T* __restrict__ twa,
+                               const typename TabT<C>::T* __restrict__ twb, const typename TabT<C>::T* __restrict__ twk, int X, int Y,
                                int Z, int64_t sys_stride_in, int64_t sys_stride_out, double scale, int conj_tw) {
     const int64_t plane = (int64_t)X * Y, nb = plane * Z;
     const int s = blockIdx.y;
     using R = typename CR<C>::R;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * nb;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int comp = (int)(e / nb);
+        const int comp = (int)((uint32_t)e / (uint32_t)nb);
         const int64_t t = e - comp * nb;
-        const int a = (int)(t % X), b = (int)((t / X) % Y), k = (int)(t / plane);
+        int a, b, k;
+        split3(t, X, Y, a, b, k);
         const int par = k & 1, kk = k >> 1;
         C tw = cmul(cmul(ld<C>(twa, a), ld<C>(twb, b)), ld<C>(twk, kk));
         if (conj_tw) tw = conjc(tw);
@@ -115,8 +118,8 @@ __global__ void fourier_unpack(const C* __restrict__ W, C* __restrict__ z, const
 // z and r (type Co) may be of higher precision than the work buffer W.
 template <typename C, typename Co = C>
 __global__ void fourier_unpack_dot(const C* __restrict__ W, Co* __restrict__ z, const Co* __restrict__ r,
-                                   const double2* __restrict__ twa, const double2* __restrict__ twb,
-                                   const double2* __restrict__ twk, int X, int Y, int Z, int64_t sys_stride,
+                                   const typename TabT<C>::T* __restrict__ twa, const typename TabT<C>::T* __restrict__ twb,
+                                   const typename TabT<C>::T* __restrict__ twk, int X, int Y, int Z, int64_t sys_stride,
                                    const int* __restrict__ skip, double* __restrict__ part, int npart) {
     const int64_t plane = (int64_t)X * Y, nb = plane * Z;
     const int s = blockIdx.y;
@@ -124,9 +127,10 @@ __global__ void fourier_unpack_dot(const C* __restrict__ W, Co* __restrict__ z, 
     double acc = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * nb;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int comp = (int)(e / nb);
+        const int comp = (int)((uint32_t)e / (uint32_t)nb);
         const int64_t t = e - comp * nb;
-        const int a = (int)(t % X), b = (int)((t / X) % Y), k = (int)(t / plane);
+        int a, b, k;
+        split3(t, X, Y, a, b, k);
         const int par = k & 1, kk = k >> 1;
         C tw = conjc(cmul(cmul(ld<C>(twa, a), ld<C>(twb, b)), ld<C>(twk, kk)));
         const Co v = cvt_c<Co>(
@@ -141,7 +145,7 @@ __global__ void fourier_unpack_dot(const C* __restrict__ W, Co* __restrict__ z, 
 
 // Twiddle T_par(p,q,r) for r < Z2.
 template <typename C>
-__device__ __forceinline__ C t_par(const double2* ea, const double2* eb, const double2* eg, int p, int q, int r,
+__device__ __forceinline__ C t_par(const typename TabT<C>::T* ea, const typename TabT<C>::T* eb, const typename TabT<C>::T* eg, int p, int q, int r,
                                    int par, int p12, int p13) {
     const int i0 = (par + p13) & 1, j0 = (par + p12 + p13) & 1;
     C t = make_c<C>(1, 0);
@@ -153,16 +157,17 @@ __device__ __forceinline__ C t_par(const double2* ea, const double2* eb, const d
 
 // Butterfly between parity halves: forward (W -> what, mode order [comp][r][q][p]) or inverse.
 template <typename C>
-__global__ void fourier_butterfly(const C* __restrict__ in, C* __restrict__ out, const double2* __restrict__ ea,
-                                  const double2* __restrict__ eb, const double2* __restrict__ eg, int X, int Y,
+__global__ void fourier_butterfly(const C* __restrict__ in, C* __restrict__ out, const typename TabT<C>::T* __restrict__ ea,
+                                  const typename TabT<C>::T* __restrict__ eb, const typename TabT<C>::T* __restrict__ eg, int X, int Y,
                                   int Z, int p12, int p13, double scale, int inverse) {
     const int64_t plane = (int64_t)X * Y, nb = plane * Z, half = nb / 2;
     using R = typename CR<C>::R;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * half;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int comp = (int)(e / half);
+        const int comp = (int)((uint32_t)e / (uint32_t)half);
         const int64_t u = e - comp * half;
-        const int p = (int)(u % X), q = (int)((u / X) % Y), r = (int)(u / plane);
+        int p, q, r;
+        split3(u, X, Y, p, q, r);
         const C T0 = t_par<C>(ea, eb, eg, p, q, r, 0, p12, p13);
         const C T1 = t_par<C>(ea, eb, eg, p, q, r, 1, p12, p13);
         const int64_t i_lo = comp * nb + (int64_t)r * plane + (int64_t)q * X + p;  // mode r (or parity 0 plane)
@@ -183,8 +188,8 @@ __global__ void fourier_butterfly(const C* __restrict__ in, C* __restrict__ out,
 // forward butterfly, per-mode (A_ref(m) - sigma rho_ref)^-1 in the working precision R,
 // inverse butterfly.  Aref holds 9 reals per mode (diag, then a01, a02, a12 as re/im).
 template <typename C, typename R>
-__global__ void precond_symbol_solve(C* __restrict__ W, const R* __restrict__ Aref, const double2* __restrict__ ea,
-                                     const double2* __restrict__ eb, const double2* __restrict__ eg,
+__global__ void precond_symbol_solve(C* __restrict__ W, const R* __restrict__ Aref, const typename TabT<C>::T* __restrict__ ea,
+                                     const typename TabT<C>::T* __restrict__ eb, const typename TabT<C>::T* __restrict__ eg,
                                      const int* __restrict__ sys_block, const int* __restrict__ skip, int X, int Y,
                                      int Z, int64_t sys_stride, double shift_rho_d, double scale_d) {
     const int s = blockIdx.y;
@@ -195,7 +200,8 @@ __global__ void precond_symbol_solve(C* __restrict__ W, const R* __restrict__ Ar
     const R shift_rho = (R)shift_rho_d, scale = (R)scale_d;
     C* Ws = W + s * sys_stride;
     for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < half; u += (int64_t)gridDim.x * blockDim.x) {
-        const int p = (int)(u % X), q = (int)((u / X) % Y), r = (int)(u / plane);
+        int p, q, r;
+        split3(u, X, Y, p, q, r);
         const C T0 = t_par<C>(ea, eb, eg, p, q, r, 0, p12, p13);
         const C T1 = t_par<C>(ea, eb, eg, p, q, r, 1, p12, p13);
         C lo[3], hi[3];
@@ -341,6 +347,7 @@ static int nblocks_for(int64_t work) {
 Precond::~Precond() {
     for (auto& pl : plans) cufftDestroy(pl.h);
     cudaFree(d_tabs);
+    cudaFree(d_tabs32);
     cudaFree(d_Aref);
     cudaFree(d_Aref32);
     cudaFree(d_null);
@@ -358,6 +365,7 @@ int precond_create(pc_grid* g) {
     // tables: ea[X], eb[Y], egh[Z2], egf[Z], twa[X], twb[Y], twk[Z2]
     P->tab_len = X + Y + Z / 2 + Z + X + Y + Z / 2;
     PC_CUDA_TRY(cudaMalloc(&P->d_tabs, sizeof(double2) * P->tab_len));
+    PC_CUDA_TRY(cudaMalloc(&P->d_tabs32, sizeof(float2) * P->tab_len));
     PC_CUDA_TRY(cudaMalloc(&P->d_Aref, sizeof(double) * 9 * g->nb));
     PC_CUDA_TRY(cudaMalloc(&P->d_Aref32, sizeof(float) * 9 * g->nb));
     PC_CUDA_TRY(cudaMalloc(&P->d_null, sizeof(int) * 65));
@@ -390,6 +398,15 @@ int precond_set_k(pc_grid* g) {
     for (int b = 0; b < Y; ++b) twb[b] = ex(b * phi[1] / Y);
     for (int k = 0; k < Z2; ++k) twk[k] = ex(k * phi[2] / Z2);
     PC_CUDA_TRY(cudaMemcpy(P->d_tabs, h.data(), sizeof(double2) * P->tab_len, cudaMemcpyHostToDevice));
+    std::vector<float2> h32(P->tab_len);
+    for (int i = 0; i < P->tab_len; ++i) h32[i] = make_float2((float)h[i].x, (float)h[i].y);
+    PC_CUDA_TRY(cudaMemcpy(P->d_tabs32, h32.data(), sizeof(float2) * P->tab_len, cudaMemcpyHostToDevice));
+    P->ea32 = P->d_tabs32;
+    P->eb32 = P->ea32 + X;
+    P->egh32 = P->eb32 + Y;
+    P->twa32 = P->egh32 + Z2 + Z;
+    P->twb32 = P->twa32 + X;
+    P->twk32 = P->twb32 + Y;
     P->ea = P->d_tabs;
     P->eb = P->ea + X;
     P->egh = P->eb + Y;
@@ -474,34 +491,34 @@ int precond_apply(pc_grid* g, int dtype, int nsys, const void* r, void* z, const
     const double shift_rho = -sigma * P->rho_ref;
     if (lower) {
         fourier_pack<float2, double2><<<nblocks_for(nsys * vs), 256, 0, s>>>(
-            (const double2*)r, (float2*)W, P->twa, P->twb, P->twk, g->X, g->Y, g->Z, nsys, vs, vs, 1.0, 0);
+            (const double2*)r, (float2*)W, P->twa32, P->twb32, P->twk32, g->X, g->Y, g->Z, nsys, vs, vs, 1.0, 0);
         note_launch();
         PC_TRY(exec_fft(plan, wdt, W, CUFFT_FORWARD, s));
         precond_symbol_solve<float2, float><<<dim3(nblocks_for(g->nb / 2), nsys), 256, 0, s>>>(
-            (float2*)W, P->d_Aref32, P->ea, P->eb, P->egh, d_sys_block, d_skip, g->X, g->Y, g->Z, vs, shift_rho, inv_nb);
+            (float2*)W, P->d_Aref32, P->ea32, P->eb32, P->egh32, d_sys_block, d_skip, g->X, g->Y, g->Z, vs, shift_rho, inv_nb);
         note_launch();
         PC_TRY(exec_fft(plan, wdt, W, CUFFT_INVERSE, s));
         if (!d_part) return fail(PC_EINVAL, "preconditioner: complex64 transforms need the fused dot");
         fourier_unpack_dot<float2, double2><<<dim3(unpack_ctas(vs), nsys), 256, 0, s>>>(
-            (const float2*)W, (double2*)z, (const double2*)r, P->twa, P->twb, P->twk, g->X, g->Y, g->Z, vs, d_skip,
+            (const float2*)W, (double2*)z, (const double2*)r, P->twa32, P->twb32, P->twk32, g->X, g->Y, g->Z, vs, d_skip,
             d_part, unpack_ctas(vs));
         note_launch();
     } else if (dtype == PC_C64) {
-        fourier_pack<float2><<<nblocks_for(nsys * vs), 256, 0, s>>>((const float2*)r, (float2*)W, P->twa, P->twb,
-                                                                  P->twk, g->X, g->Y, g->Z, nsys, vs, vs, 1.0, 0);
+        fourier_pack<float2><<<nblocks_for(nsys * vs), 256, 0, s>>>((const float2*)r, (float2*)W, P->twa32, P->twb32,
+                                                                  P->twk32, g->X, g->Y, g->Z, nsys, vs, vs, 1.0, 0);
         note_launch();
         PC_TRY(exec_fft(plan, dtype, W, CUFFT_FORWARD, s));
         precond_symbol_solve<float2, float><<<dim3(nblocks_for(g->nb / 2), nsys), 256, 0, s>>>(
-            (float2*)W, P->d_Aref32, P->ea, P->eb, P->egh, d_sys_block, d_skip, g->X, g->Y, g->Z, vs, shift_rho, inv_nb);
+            (float2*)W, P->d_Aref32, P->ea32, P->eb32, P->egh32, d_sys_block, d_skip, g->X, g->Y, g->Z, vs, shift_rho, inv_nb);
         note_launch();
         PC_TRY(exec_fft(plan, dtype, W, CUFFT_INVERSE, s));
         if (d_part)
             { fourier_unpack_dot<float2><<<dim3(unpack_ctas(vs), nsys), 256, 0, s>>>(
-                (const float2*)W, (float2*)z, (const float2*)r, P->twa, P->twb, P->twk, g->X, g->Y, g->Z, vs, d_skip,
+                (const float2*)W, (float2*)z, (const float2*)r, P->twa32, P->twb32, P->twk32, g->X, g->Y, g->Z, vs, d_skip,
                 d_part, unpack_ctas(vs)); note_launch(); }
         else
-            { fourier_unpack<float2><<<dim3(nblocks_for(vs), nsys), 256, 0, s>>>((const float2*)W, (float2*)z, P->twa,
-                                                                              P->twb, P->twk, g->X, g->Y, g->Z, vs,
+            { fourier_unpack<float2><<<dim3(nblocks_for(vs), nsys), 256, 0, s>>>((const float2*)W, (float2*)z, P->twa32,
+                                                                              P->twb32, P->twk32, g->X, g->Y, g->Z, vs,
                                                                               vs, 1.0, 1); note_launch(); }
     } else {
         fourier_pack<double2><<<nblocks_for(nsys * vs), 256, 0, s>>>((const double2*)r, (double2*)W, P->twa,
@@ -542,20 +559,20 @@ int block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* in,
     const int gb = nblocks_for(vs);
     if (dtype == PC_C64) {
         if (!inverse) {
-            fourier_pack<float2><<<gb, 256, 0, s>>>((const float2*)in, (float2*)W, P->twa, P->twb, P->twk, g->X,
+            fourier_pack<float2><<<gb, 256, 0, s>>>((const float2*)in, (float2*)W, P->twa32, P->twb32, P->twk32, g->X,
                                                      g->Y, g->Z, 1, vs, vs, 1.0, 0);
             note_launch();
             PC_TRY(exec_fft(plan, dtype, W, CUFFT_FORWARD, s));
-            fourier_butterfly<float2><<<gb, 256, 0, s>>>((const float2*)W, (float2*)out, P->ea, P->eb, P->egh,
+            fourier_butterfly<float2><<<gb, 256, 0, s>>>((const float2*)W, (float2*)out, P->ea32, P->eb32, P->egh32,
                                                           g->X, g->Y, g->Z, p12, p13, sc, 0);
             note_launch();
         } else {
-            fourier_butterfly<float2><<<gb, 256, 0, s>>>((const float2*)in, (float2*)W, P->ea, P->eb, P->egh,
+            fourier_butterfly<float2><<<gb, 256, 0, s>>>((const float2*)in, (float2*)W, P->ea32, P->eb32, P->egh32,
                                                           g->X, g->Y, g->Z, p12, p13, 1.0, 1);
             note_launch();
             PC_TRY(exec_fft(plan, dtype, W, CUFFT_INVERSE, s));
-            fourier_unpack<float2><<<dim3(gb, 1), 256, 0, s>>>((const float2*)W, (float2*)out, P->twa, P->twb,
-                                                                P->twk, g->X, g->Y, g->Z, vs, vs, sc, 1);
+            fourier_unpack<float2><<<dim3(gb, 1), 256, 0, s>>>((const float2*)W, (float2*)out, P->twa32, P->twb32,
+                                                                P->twk32, g->X, g->Y, g->Z, vs, vs, sc, 1);
             note_launch();
         }
     } else {

@@ -31,6 +31,9 @@ struct Precond {
     double2* d_tabs = nullptr;  // phase tables (device)
     const double2 *ea = nullptr, *eb = nullptr, *egh = nullptr, *egf = nullptr;
     const double2 *twa = nullptr, *twb = nullptr, *twk = nullptr;
+    float2* d_tabs32 = nullptr;  // the same tables rounded to complex64 (complex64 transforms)
+    const float2 *ea32 = nullptr, *eb32 = nullptr, *egh32 = nullptr;
+    const float2 *twa32 = nullptr, *twb32 = nullptr, *twk32 = nullptr;
     double* d_Aref = nullptr;  // 9 reals per mode (Hermitian 3x3 reference symbol)
     float* d_Aref32 = nullptr; // the same table rounded to FP32 (complex64 preconditioning)
     int* d_null = nullptr;     // [0] = count, [1..64] = modes with a vanishing symbol

@@ -161,7 +161,7 @@ static void emu_run_row(const StencilParams<float>& P, int block, const void* x,
             S.shift = (float)shift;
             for (int t = 0; t < G.NT; ++t) T::seg_begin(regs[t]);
             const int kfirst = ks - 2;
-            auto slot_of = [&](int kp) { return (int)((gseq + (uint32_t)(kp - kfirst)) % NS); };
+            auto slot_of = [&](int kp) { return (int)((gseq + (uint32_t)(kp - kfirst)) & (NS - 1)); };
             for (int kp = kfirst; kp <= ke + 1 && kp < kfirst + (int)NS; ++kp)
                 T::host_copy_plane(G, S, sh, slot_of(kp), kp);
             for (int kp = kfirst; kp <= ks; ++kp)

@@ -55,7 +55,8 @@ struct RowGeom {
     int SR;      // rows per plane slot = TY + 2
     int Xp;      // material row pitch in elements (16-byte rows)
     int matsz;   // material element size (1 = uint8 phase id, 4 = float theta)
-    int ns;      // plane slots in the ring
+    int ns;      // plane slots in the ring (8 or 4: a power of two, so that ring positions are masks)
+    int ns_log2;
     // dynamic shared memory layout (byte offsets from a 128-byte aligned base)
     int slot_bytes, off_mat, off_flux, off_cp, off_rho, off_bar, off_abort, total;
 };
@@ -88,7 +89,8 @@ inline RowGeom make_row_geom(int X, int Y, int Z, int matkind) {
     G.slot_bytes = al(G.off_mat + G.SR * G.Xp * G.matsz);
     const int fixed = al(2 * 12 * G.SR * X * 8) + al(2 * 36 * 8 + 2 * 4) + al(kRowMaxSlots * 8 + 4);
     G.ns = kRowMaxSlots;
-    while (G.ns > 4 && G.ns * G.slot_bytes + fixed + 128 + 1024 > 227 * 1024) --G.ns;
+    if (G.ns * G.slot_bytes + fixed + 128 + 1024 > 227 * 1024) G.ns = 4;
+    G.ns_log2 = G.ns == 8 ? 3 : 2;
     G.off_flux = G.ns * G.slot_bytes;                        // fluxes [2 buffers][4][3][SR][X] float2
     G.off_cp = al(G.off_flux + 2 * 12 * G.SR * X * 8);       // stiffness pairs [2][36] float2
     G.off_rho = G.off_cp + 2 * 36 * 8;

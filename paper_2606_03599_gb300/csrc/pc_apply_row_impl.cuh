@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kRowMaxThreads, 1)
 
         auto issue = [&](int kp) {
             const uint32_t q = gseq + (uint32_t)(kp - kfirst);
-            const int slot = (int)(q % NS);
+            const int slot = (int)(q & (NS - 1));
             uint64_t* bar = &bars[slot];
             const int kw = kp < 0 ? kp + G.Z : (kp >= G.Z ? kp - G.Z : kp);
             mbar_expect_tx(bar, rows * (3u * xrow + mrow));
@@ -126,13 +126,13 @@ __global__ void __launch_bounds__(kRowMaxThreads, 1)
         };
         auto wait = [&](int kp) -> bool {
             const uint32_t q = gseq + (uint32_t)(kp - kfirst);
-            uint64_t* bar = &bars[q % NS];
-            const uint32_t parity = (q / NS) & 1u;
+            uint64_t* bar = &bars[q & (NS - 1)];
+            const uint32_t parity = (q >> G.ns_log2) & 1u;
             for (uint32_t n = 0; n < kWaitLimit; ++n)
                 if (mbar_try_wait(bar, parity)) return true;
             return false;
         };
-        auto slot_of = [&](int kp) { return (int)((gseq + (uint32_t)(kp - kfirst)) % NS); };
+        auto slot_of = [&](int kp) { return (int)((gseq + (uint32_t)(kp - kfirst)) & (NS - 1)); };
 
         if (tid == 0) {
             fence_proxy_async();  // earlier generic accesses of the slots come before the new copies

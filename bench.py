@@ -46,6 +46,10 @@ TOL = 1e-8
 #   flops: 294 real flops (differences, reconstruction, 6x6 stiffness, fluxes, gather, shift)
 BYTES_PER_NODE = {"c64": 3 * 8 * 2 + 1, "c128": 3 * 16 * 2 + 1}
 FLOPS_PER_NODE = 294
+# DRAM bytes per node of the two-pass complex128 apply (the four kernels together), from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, cold cache, 8 block vectors of the
+# N=48 workload per launch); summary and command in profiles/split_flux_f64_n48.md.
+SPLIT_F64_DRAM_BYTES_PER_NODE = (10634752 + 2304 + 16088320 + 3559168 + 18640640 + 14592 + 68762624 + 59136) / 221184
 
 
 def peaks():
@@ -486,9 +490,12 @@ def main():
     kind = pc.pc_tuned_config(g, pc.PC_C128, 0, 4 * opt.block_size)[0]
     kname = {0: "apply_kernel<double>", 1: "apply_tma_kernel<double>", 2: "apply_row_kernel",
              3: "split_fill_x + split_flux + split_fill_f + split_gather (two-pass FP64)"}[kind]
-    roofline = {"kernel": kname + " (fused block stencil, FP64, autotuned launch)", "bound": "alu",
+    traffic = SPLIT_F64_DRAM_BYTES_PER_NODE * nodes_per_launch if kind == 3 else None
+    roofline = {"kernel": kname + " (block stencil, FP64, autotuned launch)", "bound": "alu",
                 "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_note": "bytes per launch, ncu cold-cache capture scaled by nodes per launch"
+                if traffic is not None else None,
                 "launches": n_app, "avg_launch_us": app_ms * 1e3, "nodes_per_launch": nodes_per_launch,
                 "flops_per_node": FLOPS_PER_NODE, "peak_source": "nominal FP64 dense rate of GB300"}
 

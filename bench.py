@@ -195,8 +195,10 @@ def run_reference(args):
     pb = O.problem_from_cell(cell, C0=1e9, rho0=1e3)
     threads = os.cpu_count() or 1
     x = complex_gaussian((3, cell.N ** 3 // 4), 7)
-    # one k-point solve of our arm performs about this many block applies (measured on GB300)
-    applies = int(os.environ.get("PC_APPLIES_PER_KPOINT", "24000"))
+    # block applies one k-point solve of the GPU arm performs (its apply statistics on GB300:
+    # 173.5 inner solves x ~27 PCG iterations plus residual checks = 5151); the same count
+    # scales the GPU arm's own cpu_baseline
+    applies = int(os.environ.get("PC_APPLIES_PER_KPOINT", "5151"))
     reps = 16
     for _ in range(args.warmup):
         O.apply_block(pb, [0.25, 0, 0], 0, x, 0.1, nthreads=threads)
@@ -394,6 +396,74 @@ def precision_run(args):
     print(json.dumps(line), flush=True)
 
 
+def differentiation_run(args):
+    """N = 64 two-phase cell (R = 0.35, seed 4): gradients of the lowest 12 eigenvalues at 10
+    Bloch vectors of the SC path and of the width of the gap between bands 6 and 7 over them,
+    with respect to the nodewise stiffness (21 entries) and density, by the adjoint kernel.
+    Reported: seconds per Bloch vector for solve + eigenvectors + adjoint, the gap gradient's
+    time, and central differences (step 2^-10 in the inclusion fraction) along seeded random
+    directions against the chain-ruled adjoint gradient."""
+    import numpy as np
+    import torch
+    import paper_2606_03599_gb300 as pc
+    from paper_2606_03599_gb300 import autodiff as ad
+    from workloads import config_cell
+    from workloads.kpath import sc_uniform_path
+    cell = config_cell("diff")
+    N, n = cell.N, cell.N ** 3
+    nev = 12
+    ks = sc_uniform_path(10)
+    # nearly binary fractions theta in [h, 1 - h], so that central differences stay in [0, 1]
+    h = 2.0 ** -10
+    theta0 = (h + (1 - 2 * h) * cell.phase.astype(np.float64)).astype(np.float32)
+    g = pc.pc_grid_create(N, cell.C, cell.rho, theta=theta0, a_lat=cell.a_lat)
+    opt = pc.pc_options_default(tol=TOL, autotune=1)
+    try:
+        ad.nodewise_gradients(g, N, ks[1], nev, opt=opt)  # untimed: tuning, workspaces
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grads = []
+        for k in ks:
+            grads.append(ad.nodewise_gradients(g, N, k, nev, opt=opt))
+        torch.cuda.synchronize()
+        t_grad = (time.perf_counter() - t0) / len(ks)
+        t0 = time.perf_counter()
+        gap, dCg, drg = ad.band_gap(g, N, ks, 5, opt=opt)
+        torch.cuda.synchronize()
+        t_gap = time.perf_counter() - t0
+        # directional derivatives of sum(lambda) at one Bloch vector along random theta directions
+        dC = np.asarray(cell.C[1] - cell.C[0])[ad.IU]
+        drho = float(cell.rho[1] - cell.rho[0])
+        ev0, gC, gr = grads[3]
+        dtheta_grad = gC @ dC + gr * drho
+        rng = np.random.default_rng(2024)
+        errs = []
+        for _ in range(max(1, args.fd_dirs)):
+            d = rng.choice([-1.0, 1.0], size=n)
+            vals = []
+            for sgn in (1.0, -1.0):
+                th = (theta0.astype(np.float64) + sgn * h * d).astype(np.float32)
+                g2 = pc.pc_grid_create(N, cell.C, cell.rho, theta=th, a_lat=cell.a_lat)
+                try:
+                    ev, _, _ = pc.pc_eigs(g2, ks[3], nev, opt=opt)
+                finally:
+                    pc.pc_grid_destroy(g2)
+                vals.append(float(np.sum(ev)))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = float(dtheta_grad @ d)
+            errs.append(abs(fd - an) / abs(fd))
+    finally:
+        pc.pc_grid_destroy(g)
+    line = {"metric": METRIC, "mode": "differentiation", "unit": "s/k-point", "dtype": "f64",
+            "config": {"workload": "two-phase SC cell N=64 (R=0.35, seed 4, theta in [2^-10, 1-2^-10]), 10 Bloch "
+                                   "vectors on the SC path, 12 bands, gap between bands 6 and 7, resid 1e-8",
+                       "fd_directions": max(1, args.fd_dirs), "fd_step_theta": h},
+            "grad_s_per_kpoint": t_grad, "gap_hz": gap, "gap_grad_s": t_gap,
+            "gap_grad_norm": float(np.sqrt(np.sum(dCg ** 2) + np.sum(drg ** 2))),
+            "fd_rel_err_sum_lambda": errs, "fd_rel_err_max": max(errs)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,6 +476,9 @@ def main():
     ap.add_argument("--batching", action="store_true",
                     help="run the ragged batching workload (N in {32..128}, --batch-k Bloch vectors each) instead")
     ap.add_argument("--batch-k", type=int, default=64, help="Bloch vectors per grid of --batching")
+    ap.add_argument("--differentiation", action="store_true",
+                    help="run the N=64 gradient workload (10 Bloch vectors, 12 bands, gap 6-7) instead")
+    ap.add_argument("--fd-dirs", type=int, default=4, help="finite-difference directions of --differentiation")
     ap.add_argument("--workers", type=int, default=4, help="host worker threads of --batching")
     ap.add_argument("--profile", default=None, choices=["kpoint", "kpoint-mixed", "apply-c64", "apply-c128"],
                     help="profiling aid for ncu: run only one k-point solve of the workload, or one "
@@ -422,6 +495,9 @@ def main():
         return
     if args.batching:
         batching_run(args)
+        return
+    if args.differentiation:
+        differentiation_run(args)
         return
     args.warmup = max(3, args.warmup)
 

@@ -134,24 +134,30 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(world, v):
+def max_over_ranks(world, v, device="cuda"):
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-def sum_over_ranks(world, v):
+def sum_over_ranks(world, v, device="cuda"):
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def kpoint_index(step, world, rank, nk):
+    """Bloch vector of a timed or warm-up step on one rank: the k-points are dealt round-robin
+    over the ranks (independent problems, no data exchange; weak scaling)."""
+    return (step * world + rank) % nk
 
 
 def cpu_oracle_sample(apply_count_per_kpoint, seconds_budget=15.0):
@@ -520,7 +526,7 @@ def main():
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
 
     def kpoint(step):
-        return kpts[(step * world + rank) % len(kpts)]
+        return kpts[kpoint_index(step, world, rank, len(kpts))]
 
     # warm-up (untimed)
     for w in range(args.warmup):

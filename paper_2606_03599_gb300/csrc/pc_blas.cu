@@ -180,10 +180,11 @@ int ts_gram(const double2* A, int rows, const double2* B, int cols, int64_t m, c
     const int RB = rows <= 2 ? 2 : (rows <= 4 ? 4 : 8);
     const int nrg = (rows + RB - 1) / RB, ngc = (cols + kGramCB - 1) / kGramCB;
     // chunks of the node range: about four CTAs per SM over all register blocks, at least
-    // 4 x 256 nodes per chunk, and as many partials as the scratch holds
+    // 128 nodes per chunk (small Gram blocks must still spread over every SM), and as many
+    // partials as the scratch holds
     const int64_t entries = (int64_t)rows * cols;
     int64_t nchunk = (4LL * device_sm_count() + nrg * ngc - 1) / (nrg * ngc);
-    nchunk = std::min<int64_t>(nchunk, std::max<int64_t>(1, m / (4 * kGramThreads)));
+    nchunk = std::min<int64_t>(nchunk, std::max<int64_t>(1, m / 128));
     nchunk = std::min<int64_t>(nchunk, (int64_t)(part_cap / (2 * entries)));
     if (nchunk < 1) return fail(PC_EINVAL, "ts_gram: partial-sum scratch too small");
     const double drho = rho1 - rho0;

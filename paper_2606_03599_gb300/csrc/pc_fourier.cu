@@ -124,7 +124,8 @@ __global__ void fourier_unpack_dot(const C* __restrict__ W, Co* __restrict__ z, 
     const int64_t plane = (int64_t)X * Y, nb = plane * Z;
     const int s = blockIdx.y;
     if (skip && skip[s]) return;
-    double acc = 0.0;
+    using Ro = decltype(z[0].x);
+    Ro acc = 0;  // per-thread sums in the output precision (complex64: FP32), FP64 across threads
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * nb;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int comp = (int)((uint32_t)e / (uint32_t)nb);
@@ -137,10 +138,10 @@ __global__ void fourier_unpack_dot(const C* __restrict__ W, Co* __restrict__ z, 
             cmul(W[s * sys_stride + comp * nb + par * (nb / 2) + (int64_t)kk * plane + (int64_t)b * X + a], tw));
         z[s * sys_stride + e] = v;
         const Co rv = r[s * sys_stride + e];
-        acc += (double)rv.x * (double)v.x + (double)rv.y * (double)v.y;
+        acc = cdotre(rv, v, acc);
     }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[(int64_t)s * npart + blockIdx.x] = acc;
+    const double sum = block_sum((double)acc);
+    if (threadIdx.x == 0) part[(int64_t)s * npart + blockIdx.x] = sum;
 }
 
 // Twiddle T_par(p,q,r) for r < Z2.

@@ -42,15 +42,16 @@ template <typename C>
 __global__ void pcg_start(const C* __restrict__ b, C* __restrict__ x, C* __restrict__ r, int64_t vs,
                           double* __restrict__ part, int npart) {
     const int s = blockIdx.y;
-    double acc = 0.0;
+    using R = decltype(b[0].x);
+    R acc = 0;  // per-thread sums in the working precision (complex64: FP32 accumulation), FP64 across threads
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
         C v = b[s * vs + e];
         r[s * vs + e] = v;
         x[s * vs + e] = make_c<C>(0, 0);
-        acc += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+        acc = cdotre(v, v, acc);
     }
-    acc = block_sum_pcg(acc);
-    if (threadIdx.x == 0) part[(int64_t)s * npart + blockIdx.x] = acc;
+    const double sum = block_sum_pcg((double)acc);
+    if (threadIdx.x == 0) part[(int64_t)s * npart + blockIdx.x] = sum;
 }
 
 // bb = sum part_bb, rz = sum part_rz; init flags.
@@ -124,23 +125,21 @@ __global__ void pcg_update_xr(C* __restrict__ x, C* __restrict__ r, const C* __r
     if (done[s]) return;
     using R = decltype(x[0].x);
     const R a = (R)sc[s].alpha;
-    double acc = 0.0, accd = 0.0;
+    // per-thread sums in the working precision (complex64: FP32 accumulation), FP64 across threads
+    R acc = 0, accd = 0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = s * vs + e;
         x[i] = cfma(a, p[i], x[i]);
         C rv = cfma(-a, q[i], r[i]);
         r[i] = rv;
-        acc += (double)rv.x * (double)rv.x + (double)rv.y * (double)rv.y;
-        if (zold != nullptr) {
-            const C zv = zold[i];
-            accd += (double)rv.x * (double)zv.x + (double)rv.y * (double)zv.y;
-        }
+        acc = cdotre(rv, rv, acc);
+        if (zold != nullptr) accd = cdotre(rv, zold[i], accd);
     }
-    acc = block_sum_pcg(acc);
-    if (threadIdx.x == 0) part[(int64_t)s * npart + blockIdx.x] = acc;
+    const double sum = block_sum_pcg((double)acc);
+    if (threadIdx.x == 0) part[(int64_t)s * npart + blockIdx.x] = sum;
     if (zold != nullptr) {
-        accd = block_sum_pcg(accd);
-        if (threadIdx.x == 0) part_d[(int64_t)s * npart + blockIdx.x] = accd;
+        const double sumd = block_sum_pcg((double)accd);
+        if (threadIdx.x == 0) part_d[(int64_t)s * npart + blockIdx.x] = sumd;
     }
 }
 

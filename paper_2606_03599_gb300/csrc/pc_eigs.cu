@@ -285,7 +285,7 @@ struct Eigs {
     size_t gpart_cap = 0;
     int ycap = 0;
     long long pcg_iters = 0;
-    int max_pcg = 0, solves = 0, expansions = 0;
+    int max_pcg = 0, solves = 0, expansions = 0, cholqr_single = 0;
     std::vector<void*> allocs;
     ~Eigs() {
         for (void* p : allocs) cudaFree(p);
@@ -359,6 +359,14 @@ static int cholqr2(Eigs& E, Space& S, double2* Wv, int cols, int nv, std::vector
             pass = -1;  // restart both passes on the new block; R of a replaced block is zero
             continue;
         }
+        // a block whose columns are already nearly M-orthogonal (every normalised off-diagonal
+        // Gram entry below 0.1, so its scaled condition number is below ~1.25) is orthonormal to
+        // working precision after one pass; the second pass is only needed otherwise
+        bool well_conditioned = pass == 0;
+        for (int j = 0; j < cols && well_conditioned; ++j)
+            for (int i = 0; i < j; ++i)
+                if (std::abs(G[i + j * cols]) > 0.1 * std::sqrt(G[i + i * cols].real() * G[j + j * cols].real()))
+                    well_conditioned = false;
         upper_inverse(cols, R, Ri);
         // Wv <- Wv R^-1  (through T)
         PC_TRY(gemm_nn_host(E, Wv, cols, Ri, cols, E.T, S.vs, kOne, kZero));
@@ -372,6 +380,10 @@ static int cholqr2(Eigs& E, Space& S, double2* Wv, int cols, int nv, std::vector
                 Rn[i + j * cols] = acc;
             }
         Rtot.swap(Rn);
+        if (well_conditioned) {
+            ++E.cholqr_single;
+            break;
+        }
     }
     return PC_OK;
 }
@@ -775,6 +787,9 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
                              E.sp[i].m_exp, E.sp[i].target, E.sp[i].nconv, (int)E.sp[i].done);
         }
     }
+    if (opt->verbose)
+        std::fprintf(stderr, "[pc_eigs] expansions=%d single-pass CholQR=%d solves=%d pcg=%lld\n", E.expansions,
+                     E.cholqr_single, E.solves, E.pcg_iters);
     double maxres = 0;
     const double to_si = g->C0 / (g->rho0 * g->L * g->L);
     if (status == PC_OK) {

@@ -31,11 +31,13 @@ int tile_ty(int shape) { return shape <= 2 ? 8 : 4; }
 
 static int apply_kernel_mode() {
     // PC_APPLY_KERNEL=legacy selects the register-staged kernel everywhere, =tma the TMA tile
-    // kernel in place of the row kernel (A/B comparisons)
+    // kernel in place of the row kernel, =split the two-pass kernels for both precisions (A/B
+    // comparisons)
     static int mode = -1;
     if (mode < 0) {
         const char* v = std::getenv("PC_APPLY_KERNEL");
-        mode = (v && std::string(v) == "legacy") ? 1 : ((v && std::string(v) == "tma") ? 2 : 0);
+        const std::string m = v ? v : "";
+        mode = m == "legacy" ? 1 : (m == "tma" ? 2 : (m == "split" ? 3 : 0));
     }
     return mode;
 }
@@ -55,7 +57,7 @@ int device_sm_count() {
 
 ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool blocks, int matkind, bool scratch_ok) {
     ApplyConfig c;
-    if (dtype == PC_C128 && apply_kernel_mode() == 0 && scratch_ok) {
+    if (scratch_ok && ((dtype == PC_C128 && apply_kernel_mode() == 0) || apply_kernel_mode() == 3)) {
         // complex128 is bound by GB300's FP64 pipe: fluxes once per node (two-pass kernels)
         c.split = true;
         c.shape = 0;
@@ -322,7 +324,34 @@ int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nit
     ApplyConfig cfg = cfg_in ? *cfg_in : apply_config_for(g, full, nitems, dtype);
     void* th = timing_enabled() ? timing_begin(s) : nullptr;
     int rc;
-    if (dtype == PC_C64 && cfg.row) {
+    if (cfg.split) {
+        const size_t need = split_scratch_bytes(X, Y, Z, nitems, dtype);
+        rc = PC_OK;
+        if (g->split_bytes < need) {
+            // grown outside stream capture: the first launch of every batch shape runs eagerly
+            cudaFree(g->d_split);
+            g->d_split = nullptr;
+            g->split_bytes = 0;
+            cudaError_t e = cudaMalloc(&g->d_split, need);
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(split apply scratch)");
+            else g->split_bytes = need;
+        }
+        if (rc == PC_OK && dtype == PC_C64) {
+            StencilParams<float> P = g->P32;
+            P.X = X;
+            P.Y = Y;
+            P.Z = Z;
+            rc = launch_apply_split_f32(full, g->cubic, g->matkind, P, items, nitems, g->d_split, g->split_bytes,
+                                        dot_partials, dot_stride, s);
+        } else if (rc == PC_OK) {
+            StencilParams<double> P = g->P64;
+            P.X = X;
+            P.Y = Y;
+            P.Z = Z;
+            rc = launch_apply_split_f64(full, g->cubic, g->matkind, P, items, nitems, g->d_split, g->split_bytes,
+                                        dot_partials, dot_stride, s);
+        }
+    } else if (dtype == PC_C64 && cfg.row) {
         StencilParams<float> P = g->P32;
         P.X = X;
         P.Y = Y;
@@ -340,25 +369,6 @@ int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nit
                                             dot_partials, dot_stride, g->d_err, s)
                      : launch_apply_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
                                         dot_stride, s);
-    } else if (cfg.split) {
-        StencilParams<double> P = g->P64;
-        P.X = X;
-        P.Y = Y;
-        P.Z = Z;
-        const size_t need = split_scratch_bytes(X, Y, Z, nitems);
-        rc = PC_OK;
-        if (g->split_bytes < need) {
-            // grown outside stream capture: the first launch of every batch shape runs eagerly
-            cudaFree(g->d_split);
-            g->d_split = nullptr;
-            g->split_bytes = 0;
-            cudaError_t e = cudaMalloc(&g->d_split, need);
-            if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(split apply scratch)");
-            else g->split_bytes = need;
-        }
-        if (rc == PC_OK)
-            rc = launch_apply_split_f64(full, g->cubic, g->matkind, P, items, nitems, g->d_split, g->split_bytes,
-                                        dot_partials, dot_stride, s);
     } else {
         StencilParams<double> P = g->P64;
         P.X = X;

@@ -1,4 +1,5 @@
-// Two-pass complex128 stencil apply (see pc_apply_split.cuh): kernels and launcher.
+// Two-pass stencil apply (see pc_apply_split.cuh): kernels and launchers.  Complex128 by default
+// (bound by the FP64 pipe); complex64 as an autotuner candidate for grids whose fluxes stay in L2.
 #include <algorithm>
 
 #include "pc_apply_split.cuh"
@@ -10,10 +11,12 @@ namespace {
 constexpr int kSplitMaxItems = 64;
 constexpr int kSplitThreads = 128;
 
+template <typename R>
 struct SplitBatch {
+    using C = typename CT<R>::T;
     ApplyItem it[kSplitMaxItems];
-    double2* xe[kSplitMaxItems];  // extended x of each item
-    double2* fe[kSplitMaxItems];  // extended fluxes of each item
+    C* xe[kSplitMaxItems];  // extended x of each item
+    C* fe[kSplitMaxItems];  // extended fluxes of each item
     int n;
 };
 
@@ -22,15 +25,16 @@ __device__ __forceinline__ bool item_skipped(const ApplyItem& it) { return it.sk
 // Pass 1: blockIdx.z = item; CTAs with blockIdx.x < nint copy interior cells (blockIdx.y = component),
 // the others (blockIdx.y = 0 only) write the ghost cells of all three components (the only FP64
 // work of the pass: the Bloch phase, computed once per cell).
-template <bool FULL, bool CUBIC, int MATK>
+template <typename R, bool FULL, bool CUBIC, int MATK>
 __global__ void __launch_bounds__(kSplitThreads)
-    split_fill_x(const __grid_constant__ StencilParams<double> P, const __grid_constant__ SplitBatch B,
+    split_fill_x(const __grid_constant__ StencilParams<R> P, const __grid_constant__ SplitBatch<R> B,
                  const __grid_constant__ SplitGeom G, int nint) {
-    using T = SplitApply<double, FULL, CUBIC, MATK>;
+    using T = SplitApply<R, FULL, CUBIC, MATK>;
+    using C = typename CT<R>::T;
     const ApplyItem& it = B.it[blockIdx.z];
     if (item_skipped(it)) return;
-    const double2* x = static_cast<const double2*>(it.x);
-    double2* xe = B.xe[blockIdx.z];
+    const C* x = static_cast<const C*>(it.x);
+    C* xe = B.xe[blockIdx.z];
     const int c = blockIdx.y;
     if ((int)blockIdx.x < nint) {
         for (int64_t t = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; t < G.m; t += (int64_t)nint * kSplitThreads)
@@ -44,12 +48,12 @@ __global__ void __launch_bounds__(kSplitThreads)
 }
 
 // Pass 2: fluxes of every interior node; blockIdx.y = item.
-template <bool FULL, bool CUBIC, int MATK>
+template <typename R, bool FULL, bool CUBIC, int MATK>
 __global__ void __launch_bounds__(kSplitThreads)
-    split_flux(const __grid_constant__ StencilParams<double> P, const __grid_constant__ SplitBatch B,
+    split_flux(const __grid_constant__ StencilParams<R> P, const __grid_constant__ SplitBatch<R> B,
                const __grid_constant__ SplitGeom G) {
-    using T = SplitApply<double, FULL, CUBIC, MATK>;
-    __shared__ double Ct[2][36];
+    using T = SplitApply<R, FULL, CUBIC, MATK>;
+    __shared__ R Ct[2][36];
     for (int i = threadIdx.x; i < 72; i += kSplitThreads) Ct[i / 36][i % 36] = P.C[i / 36][i % 36];
     __syncthreads();
     const ApplyItem& it = B.it[blockIdx.y];
@@ -61,11 +65,11 @@ __global__ void __launch_bounds__(kSplitThreads)
 }
 
 // Pass 3: ghost cells of F_0..F_3 (12 arrays per cell); blockIdx.y = item.
-template <bool FULL, bool CUBIC, int MATK>
+template <typename R, bool FULL, bool CUBIC, int MATK>
 __global__ void __launch_bounds__(kSplitThreads)
-    split_fill_f(const __grid_constant__ StencilParams<double> P, const __grid_constant__ SplitBatch B,
+    split_fill_f(const __grid_constant__ StencilParams<R> P, const __grid_constant__ SplitBatch<R> B,
                  const __grid_constant__ SplitGeom G) {
-    using T = SplitApply<double, FULL, CUBIC, MATK>;
+    using T = SplitApply<R, FULL, CUBIC, MATK>;
     const ApplyItem& it = B.it[blockIdx.y];
     if (item_skipped(it)) return;
     for (int64_t gi = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; gi < G.ghosts;
@@ -74,11 +78,12 @@ __global__ void __launch_bounds__(kSplitThreads)
 }
 
 // Pass 4: outputs and optional Re<x, y> partials (one per CTA, fixed order); blockIdx.y = item.
-template <bool FULL, bool CUBIC, int MATK>
+template <typename R, bool FULL, bool CUBIC, int MATK>
 __global__ void __launch_bounds__(kSplitThreads)
-    split_gather(const __grid_constant__ StencilParams<double> P, const __grid_constant__ SplitBatch B,
+    split_gather(const __grid_constant__ StencilParams<R> P, const __grid_constant__ SplitBatch<R> B,
                  const __grid_constant__ SplitGeom G, double* __restrict__ dot_partials, int dot_stride) {
-    using T = SplitApply<double, FULL, CUBIC, MATK>;
+    using T = SplitApply<R, FULL, CUBIC, MATK>;
+    using C = typename CT<R>::T;
     const ApplyItem& it = B.it[blockIdx.y];
     if (item_skipped(it)) return;
     const bool want_dot = dot_partials != nullptr && it.dot_slot >= 0;
@@ -86,8 +91,8 @@ __global__ void __launch_bounds__(kSplitThreads)
     double dot = 0.0;
     for (int64_t t = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; t < G.m;
          t += (int64_t)gridDim.x * kSplitThreads)
-        dot += T::gather_node(P, G, p12, p13, B.fe[blockIdx.y], static_cast<const double2*>(it.x),
-                              static_cast<double2*>(it.y), it.mat, it.shift, t, want_dot);
+        dot += (double)T::gather_node(P, G, p12, p13, B.fe[blockIdx.y], static_cast<const C*>(it.x),
+                                      static_cast<C*>(it.y), it.mat, (R)it.shift, t, want_dot);
     if (want_dot) {
         __shared__ double red[kSplitThreads / 32];
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
@@ -101,21 +106,21 @@ __global__ void __launch_bounds__(kSplitThreads)
     }
 }
 
-template <bool FULL, bool CUBIC, int MATK>
-int launch_split_t(const StencilParams<double>& P, const SplitBatch& B, const SplitGeom& G, double* dp, int ds,
+template <typename R, bool FULL, bool CUBIC, int MATK>
+int launch_split_t(const StencilParams<R>& P, const SplitBatch<R>& B, const SplitGeom& G, double* dp, int ds,
                    cudaStream_t s) {
     const int sm = device_sm_count();
     // interior copy and ghost fill share one launch: CTAs in proportion to their cells
     const int nint = (int)std::max<int64_t>(1, std::min<int64_t>((G.m + kSplitThreads - 1) / kSplitThreads, 2LL * sm));
     const int ngh = (int)std::max<int64_t>(1, std::min<int64_t>((G.ghosts + kSplitThreads - 1) / kSplitThreads, sm));
-    split_fill_x<FULL, CUBIC, MATK><<<dim3(nint + ngh, 3, B.n), kSplitThreads, 0, s>>>(P, B, G, nint);
+    split_fill_x<R, FULL, CUBIC, MATK><<<dim3(nint + ngh, 3, B.n), kSplitThreads, 0, s>>>(P, B, G, nint);
     note_launch();
     const int nflux = split_apply_ctas(G.m);
-    split_flux<FULL, CUBIC, MATK><<<dim3(nflux, B.n), kSplitThreads, 0, s>>>(P, B, G);
+    split_flux<R, FULL, CUBIC, MATK><<<dim3(nflux, B.n), kSplitThreads, 0, s>>>(P, B, G);
     note_launch();
-    split_fill_f<FULL, CUBIC, MATK><<<dim3(ngh, B.n), kSplitThreads, 0, s>>>(P, B, G);
+    split_fill_f<R, FULL, CUBIC, MATK><<<dim3(ngh, B.n), kSplitThreads, 0, s>>>(P, B, G);
     note_launch();
-    split_gather<FULL, CUBIC, MATK><<<dim3(nflux, B.n), kSplitThreads, 0, s>>>(P, B, G, dp, ds);
+    split_gather<R, FULL, CUBIC, MATK><<<dim3(nflux, B.n), kSplitThreads, 0, s>>>(P, B, G, dp, ds);
     note_launch();
     note_apply_launch();
     PC_CUDA_TRY(cudaGetLastError());
@@ -130,38 +135,50 @@ int split_apply_ctas(int64_t m) {
                                                        8LL * device_sm_count()));
 }
 
-size_t split_scratch_bytes(int X, int Y, int Z, int nitems) {
+size_t split_scratch_bytes(int X, int Y, int Z, int nitems, int dtype) {
     const SplitGeom G = make_split_geom(X, Y, Z);
-    return (size_t)std::min(nitems, kSplitMaxItems) * split_item_elems(G) * sizeof(double2);
+    return (size_t)std::min(nitems, kSplitMaxItems) * split_item_elems(G) * (dtype == PC_C64 ? 8 : 16);
 }
 
-int launch_apply_split_f64(bool full, bool cubic, int matkind, const StencilParams<double>& P, const ApplyItem* items,
-                           int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s) {
+template <typename R>
+static int launch_apply_split_t(bool full, bool cubic, int matkind, const StencilParams<R>& P, const ApplyItem* items,
+                                int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s) {
+    using C = typename CT<R>::T;
     const SplitGeom G = make_split_geom(P.X, P.Y, P.Z);
     const int64_t per = split_item_elems(G);
     if (dp != nullptr && split_apply_ctas(G.m) > ds)
         return fail(PC_EINVAL, "apply: launch has more CTAs than partial-sum slots");
     for (int base = 0; base < nitems; base += kSplitMaxItems) {
-        SplitBatch B;
+        SplitBatch<R> B;
         B.n = std::min(nitems - base, kSplitMaxItems);
-        if ((size_t)B.n * per * sizeof(double2) > scratch_bytes) return fail(PC_EINVAL, "apply: split scratch too small");
+        if ((size_t)B.n * per * sizeof(C) > scratch_bytes) return fail(PC_EINVAL, "apply: split scratch too small");
         for (int i = 0; i < B.n; ++i) {
             B.it[i] = items[base + i];
-            double2* w = static_cast<double2*>(scratch) + (int64_t)i * per;
+            C* w = static_cast<C*>(scratch) + (int64_t)i * per;
             B.xe[i] = w;
             B.fe[i] = w + 3 * G.ne;
         }
         int rc;
         if (full) {
-            if (cubic) rc = matkind ? launch_split_t<true, true, 1>(P, B, G, dp, ds, s) : launch_split_t<true, true, 0>(P, B, G, dp, ds, s);
-            else rc = matkind ? launch_split_t<true, false, 1>(P, B, G, dp, ds, s) : launch_split_t<true, false, 0>(P, B, G, dp, ds, s);
+            if (cubic) rc = matkind ? launch_split_t<R, true, true, 1>(P, B, G, dp, ds, s) : launch_split_t<R, true, true, 0>(P, B, G, dp, ds, s);
+            else rc = matkind ? launch_split_t<R, true, false, 1>(P, B, G, dp, ds, s) : launch_split_t<R, true, false, 0>(P, B, G, dp, ds, s);
         } else {
-            if (cubic) rc = matkind ? launch_split_t<false, true, 1>(P, B, G, dp, ds, s) : launch_split_t<false, true, 0>(P, B, G, dp, ds, s);
-            else rc = matkind ? launch_split_t<false, false, 1>(P, B, G, dp, ds, s) : launch_split_t<false, false, 0>(P, B, G, dp, ds, s);
+            if (cubic) rc = matkind ? launch_split_t<R, false, true, 1>(P, B, G, dp, ds, s) : launch_split_t<R, false, true, 0>(P, B, G, dp, ds, s);
+            else rc = matkind ? launch_split_t<R, false, false, 1>(P, B, G, dp, ds, s) : launch_split_t<R, false, false, 0>(P, B, G, dp, ds, s);
         }
         PC_TRY(rc);
     }
     return PC_OK;
+}
+
+int launch_apply_split_f64(bool full, bool cubic, int matkind, const StencilParams<double>& P, const ApplyItem* items,
+                           int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s) {
+    return launch_apply_split_t<double>(full, cubic, matkind, P, items, nitems, scratch, scratch_bytes, dp, ds, s);
+}
+
+int launch_apply_split_f32(bool full, bool cubic, int matkind, const StencilParams<float>& P, const ApplyItem* items,
+                           int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s) {
+    return launch_apply_split_t<float>(full, cubic, matkind, P, items, nitems, scratch, scratch_bytes, dp, ds, s);
 }
 
 }  // namespace pc

@@ -77,7 +77,9 @@ int launch_apply_tma_f64(bool full, bool cubic, int matkind, int shape, const St
 // Two-pass complex128 apply (fluxes once per node through memory): scratch of split_scratch_bytes.
 int launch_apply_split_f64(bool full, bool cubic, int matkind, const StencilParams<double>& P, const ApplyItem* items,
                            int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s);
-size_t split_scratch_bytes(int X, int Y, int Z, int nitems);
+int launch_apply_split_f32(bool full, bool cubic, int matkind, const StencilParams<float>& P, const ApplyItem* items,
+                           int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s);
+size_t split_scratch_bytes(int X, int Y, int Z, int nitems, int dtype);
 int split_apply_ctas(int64_t m);
 
 struct ApplyConfig {

@@ -413,7 +413,7 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
         std::vector<double> key = {(double)g->k.version, (double)dtype, (double)nsys, sigma, tol2, (double)maxit,
                                    (double)(uintptr_t)B, (double)(uintptr_t)X, (double)(uintptr_t)g->pre->d_work,
                                    (double)(uintptr_t)w->R, (double)(timing_enabled() ? 1 : 0), (double)npm,
-                                   (double)flex};
+                                   (double)flex, (double)(uintptr_t)g->d_split};  // the two-pass apply's scratch
         for (int i = 0; i < nsys; ++i) key.push_back((double)blocks[i]);
         if (w->gexec == nullptr || w->gkey != key) {
             w->drop_graph();

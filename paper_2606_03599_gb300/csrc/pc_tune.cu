@@ -139,7 +139,10 @@ static int time_candidate(pc_grid* g, int dtype, bool full, std::vector<ApplyIte
 static std::vector<ApplyConfig> candidates(int X, int Y, int Z, int dtype, bool full, int matkind, int nitems) {
     std::vector<ApplyConfig> out;
     const int sm = device_sm_count();
-    if (dtype == PC_C128) {
+    // two-pass kernels: the default for complex128; for complex64 a candidate while the batch's
+    // fluxes and extended copies (18 complex64 per extended cell) fit in L2 (126 MB on GB300)
+    const double split_mb = (double)split_scratch_bytes(X, Y, Z, nitems, dtype) / (1 << 20);
+    if (dtype == PC_C128 || split_mb <= 96.0) {
         ApplyConfig c;
         c.split = true;
         c.tma = false;

@@ -216,8 +216,9 @@ def test_block_apply_sampled_n160(pc, dtype):
 
 def test_register_staged_tma_and_row_kernels_agree(pc):
     """The register-staged kernel (PC_APPLY_KERNEL=legacy, used for odd quarter-grid widths), the
-    TMA tile kernel (PC_APPLY_KERNEL=tma) and the row-tile kernel (default for complex64 blocks)
-    give the same operator on a grid where all three apply."""
+    TMA tile kernel (PC_APPLY_KERNEL=tma), the row-tile kernel (default for complex64 blocks) and
+    the two-pass kernels (PC_APPLY_KERNEL=split, default for complex128) give the same operator,
+    in both precisions, on a grid where all of them apply."""
     import subprocess
     import sys
     import os
@@ -245,11 +246,11 @@ np.save(sys.argv[1], np.concatenate(out))
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     res = {}
     tmp = tempfile.mkdtemp()
-    for mode in ("legacy", "tma", "row"):
+    for mode in ("legacy", "tma", "row", "split"):
         path = os.path.join(tmp, "kernel_ab_%s.npy" % mode)
         env = dict(os.environ, PC_APPLY_KERNEL=mode)
         subprocess.run([sys.executable, "-c", code % root, path], check=True, env=env)
         res[mode] = np.load(path)
     a = res["legacy"]
-    for mode in ("tma", "row"):
+    for mode in ("tma", "row", "split"):
         assert np.abs(a - res[mode]).max() <= 2e-6 * np.abs(a).max(), mode

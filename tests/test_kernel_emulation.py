@@ -73,6 +73,7 @@ CASES = [
     # two-pass complex128 kernels (code 30): every block, the full grid, the smallest grids
     (4, 0, 2, 30, 0), (4, 3, 2, 30, 0), (4, -1, 2, 30, 0), (8, 1, 2, 30, 0), (8, 2, 2, 30, 0),
     (8, -1, 2, 30, 0), (12, 3, 2, 30, 0), (16, 0, 2, 30, 0),
+    (8, 1, 1, 30, 0), (12, -1, 1, 30, 0), (16, 2, 1, 30, 0),
 ]
 
 

@@ -103,16 +103,24 @@ __global__ void __launch_bounds__(kGramThreads)
     }
 }
 
-// out[e] = sum over chunks of part[e][chunk], in chunk order.
+// out[e] = sum over chunks of part[e][chunk]: one warp per entry, lane l sums the chunks
+// l, l + 32, ... in order, then the lanes' sums are combined by a fixed shuffle tree
+// (deterministic for a given chunk count).
 __global__ void ts_gram_reduce(const double* __restrict__ part, int nentries, int nchunk, double2* __restrict__ out) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (e >= nentries) return;
     double re = 0.0, im = 0.0;
-    for (int c = 0; c < nchunk; ++c) {
+    for (int c = lane; c < nchunk; c += 32) {
         re += part[((int64_t)e * 2 + 0) * nchunk + c];
         im += part[((int64_t)e * 2 + 1) * nchunk + c];
     }
-    out[e] = make_double2(re, im);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) out[e] = make_double2(re, im);
 }
 
 // C[:, j] = beta C[:, j] + alpha sum_k A[:, k] h(k, j) for the CB columns j0 .. j0 + CB - 1 of
@@ -179,12 +187,12 @@ int ts_gram(const double2* A, int rows, const double2* B, int cols, int64_t m, c
     if (!A || !B || !d_out || !d_part || m <= 0) return fail(PC_EINVAL, "ts_gram: bad argument");
     const int RB = rows <= 2 ? 2 : (rows <= 4 ? 4 : 8);
     const int nrg = (rows + RB - 1) / RB, ngc = (cols + kGramCB - 1) / kGramCB;
-    // chunks of the node range: about four CTAs per SM over all register blocks, at least
-    // 128 nodes per chunk (small Gram blocks must still spread over every SM), and as many
-    // partials as the scratch holds
+    // chunks of the node range: about two CTAs per SM over all register blocks, at least 512
+    // nodes (two per thread) per chunk so that the per-CTA reduction stays small next to the
+    // products, and as many partials as the scratch holds
     const int64_t entries = (int64_t)rows * cols;
-    int64_t nchunk = (4LL * device_sm_count() + nrg * ngc - 1) / (nrg * ngc);
-    nchunk = std::min<int64_t>(nchunk, std::max<int64_t>(1, m / 128));
+    int64_t nchunk = (2LL * device_sm_count() + nrg * ngc - 1) / (nrg * ngc);
+    nchunk = std::min<int64_t>(nchunk, std::max<int64_t>(1, m / 512));
     nchunk = std::min<int64_t>(nchunk, (int64_t)(part_cap / (2 * entries)));
     if (nchunk < 1) return fail(PC_EINVAL, "ts_gram: partial-sum scratch too small");
     const double drho = rho1 - rho0;
@@ -194,7 +202,7 @@ int ts_gram(const double2* A, int rows, const double2* B, int cols, int64_t m, c
         launch_gram_rb<4>(A, rows, B, cols, m, mat, matkind, rho0, drho, ngc, nrg, (int)nchunk, d_part, s);
     else
         launch_gram_rb<8>(A, rows, B, cols, m, mat, matkind, rho0, drho, ngc, nrg, (int)nchunk, d_part, s);
-    ts_gram_reduce<<<(int)((entries + 127) / 128), 128, 0, s>>>(d_part, (int)entries, (int)nchunk, d_out);
+    ts_gram_reduce<<<(int)((entries + 7) / 8), 256, 0, s>>>(d_part, (int)entries, (int)nchunk, d_out);
     note_launch();
     PC_CUDA_TRY(cudaGetLastError());
     return PC_OK;
@@ -214,13 +222,18 @@ int ts_update(const double2* A, int k, const double2* d_h, int cols, double2* C,
         return fail(PC_EINVAL, "ts_update: empty product with beta other than 0 or 1");
     }
     if (!A || !d_h) return fail(PC_EINVAL, "ts_update: bad argument");
-    constexpr int CB = 4;
+    // column blocks of 2 when cols <= 2 (the Gram-Schmidt updates of a 2-wide Krylov block:
+    // no FMAs on padding columns), else of 4
+    const int CB = cols <= 2 ? 2 : 4;
     const size_t smem = sizeof(double2) * (size_t)k * CB;
     if (smem > 48 * 1024) return fail(PC_EINVAL, "ts_update: too many basis columns");
     const int ngc = (cols + CB - 1) / CB;
     int64_t gx = (vs + 255) / 256;
     gx = std::min<int64_t>(gx, std::max<int64_t>(1, 8LL * device_sm_count() / ngc));
-    ts_update_kernel<CB><<<dim3((unsigned)gx, ngc), 256, smem, s>>>(A, k, d_h, cols, C, vs, alpha, beta);
+    if (CB == 2)
+        ts_update_kernel<2><<<dim3((unsigned)gx, ngc), 256, smem, s>>>(A, k, d_h, cols, C, vs, alpha, beta);
+    else
+        ts_update_kernel<4><<<dim3((unsigned)gx, ngc), 256, smem, s>>>(A, k, d_h, cols, C, vs, alpha, beta);
     note_launch();
     PC_CUDA_TRY(cudaGetLastError());
     return PC_OK;

@@ -282,7 +282,7 @@ int pc_eigs_batch(pc_batch_job* jobs, int njobs, const pc_options* opt, int work
 
 /* Autotuner of the stencil apply (no counterpart in the paper: an implementation choice).
  * Times every applicable kernel and launch shape (row-tile kernel with several persistent CTA
- * counts, TMA tile kernel, register-staged kernel; several k-chunkings) on scratch vectors for
+ * counts, TMA tile kernel, register-staged kernel, two-pass kernels; several k-chunkings) on scratch vectors for
  * batches of `nitems` (rounded up to a power of two, 1..64) vectors of precision `dtype` in the
  * parity-block layout (layout 0), the full-space layout (1) or both (2), and keeps the fastest
  * for every later apply, PCG and eigen-solve on grids of the same size, material kind and lattice
@@ -292,8 +292,9 @@ int pc_eigs_batch(pc_batch_job* jobs, int njobs, const pc_options* opt, int work
 int pc_autotune(pc_grid* g, int dtype, int layout, int nitems, void* stream);
 
 /* The launch configuration the library will use for a batch of `nitems` vectors of `dtype` in
- * layout 0 (blocks) or 1 (full): kind 0 = register-staged, 1 = TMA tile, 2 = row tile; tile
- * shape code; planes per CTA (tz; row kernel: least planes per CTA); CTAs of the launch. */
+ * layout 0 (blocks) or 1 (full): kind 0 = register-staged, 1 = TMA tile, 2 = row tile, 3 = two-pass
+ * (fluxes once per node, then gather; the default for complex128); tile shape code; planes per CTA
+ * (tz; row kernel: least planes per CTA); CTAs of the launch (two-pass: of its gather). */
 int pc_tuned_config(const pc_grid* g, int dtype, int layout, int nitems, int* kind, int* shape, int* tz, int* ctas);
 
 /* ---- differentiation --------------------------------------------------- */

@@ -368,7 +368,7 @@ def pc_autotune(g, dtype, layout, nitems, stream=None):
 
 
 def pc_tuned_config(g, dtype, layout, nitems):
-    """(kind, shape, tz, ctas) of the launch the library uses; kind 0 registers, 1 TMA tile, 2 row."""
+    """(kind, shape, tz, ctas) of the launch the library uses; kind 0 registers, 1 TMA tile, 2 row, 3 two-pass."""
     v = [ctypes.c_int() for _ in range(4)]
     _check(lib.pc_tuned_config(g, int(dtype), int(layout), int(nitems), *[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)

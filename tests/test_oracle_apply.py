@@ -186,3 +186,19 @@ def test_golden_materials_match_workloads(golden_dir):
     assert np.array_equal(Cq / 1e9, _voigt_from_dict(mat["quartz"]["C"]))
     assert np.array_equal(Cs / 1e9, _voigt_from_dict(mat["silicon"]["C"]))
     assert rq == mat["quartz"]["rho"] and rs == mat["silicon"]["rho"]
+
+
+def test_fcc_workload_geometry():
+    """The paper's FCC cell generator: primitive cell volume a0^3 / 4, the sphere inside the
+    cell, sub-pixel fractions in [0, 1] summing to the sphere's volume fraction."""
+    import math
+    from workloads import fcc_lattice, fcc_quartz_silicon_cell
+    from workloads.materials import FCC_A0
+    A = fcc_lattice()
+    assert abs(abs(np.linalg.det(A)) - FCC_A0 ** 3 / 4) <= 1e-15
+    cell = fcc_quartz_silicon_cell(32)
+    th = cell.theta.astype(np.float64)
+    assert th.min() >= 0.0 and th.max() <= 1.0
+    exact = (4.0 / 3.0) * math.pi * (0.25 * FCC_A0) ** 3 / (FCC_A0 ** 3 / 4)
+    assert abs(th.mean() - exact) <= 2e-4
+    assert 0 < np.count_nonzero((th > 0) & (th < 1)) < th.size // 4

@@ -12,6 +12,8 @@ from .materials import (  # noqa: F401
     two_phase_sphere,
     config_cell,
     quartz_silicon_constants,
+    fcc_lattice,
+    fcc_quartz_silicon_cell,
 )
-from .kpath import sc_path, sc_eight_points, sc_uniform_path  # noqa: F401
+from .kpath import FCC_POINTS, sc_path, sc_eight_points, sc_uniform_path  # noqa: F401
 from .vectors import complex_gaussian  # noqa: F401

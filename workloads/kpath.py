@@ -48,3 +48,15 @@ def sc_uniform_path(count: int) -> np.ndarray:
         f = (t - cum[i]) / seg[i]
         out.append(verts[i] + f * (verts[i + 1] - verts[i]))
     return np.array(out)
+
+
+# FCC high-symmetry points in reduced reciprocal coordinates (q . a_l = 2 pi kappa_l) of the
+# paper's FCC example (Sec. 7, Eq. fcc_high_symmetry_points).
+FCC_POINTS = {
+    "G": np.array([0.0, 0.0, 0.0]),
+    "X": np.array([0.0, 0.5, 0.5]),
+    "W": np.array([0.25, 0.5, 0.75]),
+    "K": np.array([0.375, 0.375, 0.75]),
+    "L": np.array([0.5, 0.5, 0.5]),
+    "U": np.array([0.25, 0.625, 0.625]),
+}

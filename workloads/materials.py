@@ -167,3 +167,49 @@ def quartz_silicon_constants():
     Cs[3, 3] = Cs[4, 4] = Cs[5, 5] = 79.6
     Cs = np.triu(Cs) + np.triu(Cs, 1).T
     return Cq * GPA, 2650.0, Cs * GPA, 2329.0
+
+
+FCC_A0 = 3.0e-2  # lattice constant of the paper's FCC example, m
+
+
+def fcc_lattice(a0: float = FCC_A0) -> np.ndarray:
+    """FCC primitive basis a1 = (0, a0/2, a0/2), a2 = (a0/2, 0, a0/2), a3 = (a0/2, a0/2, 0) as the
+    columns of A_lat (Sec. 7.1, Eq. num_lattice_vectors)."""
+    h = a0 / 2
+    return np.array([[0.0, h, h], [h, 0.0, h], [h, h, 0.0]]).T
+
+
+def fcc_quartz_silicon_cell(N: int, supersample: int = 8, radius: float = 0.25) -> TwoPhaseCell:
+    """The paper's FCC example (Sec. 7.1): low-quartz matrix, silicon sphere of radius
+    ``radius`` * a0 centred at reduced coordinate (1/2, 1/2, 1/2), sub-pixel inclusion fractions
+    (Eq. subpixel_material_average).
+
+    The cell of node r = (i, j, k) / N is read as the reduced cube of side 1/N centred on the
+    node, mapped to Cartesian space by A_lat; its silicon fraction theta is the share of
+    ``supersample``^3 equally spaced sub-samples inside the sphere.  Nodes farther from the
+    sphere surface than the cell's circumradius get 0 or 1 directly.
+    """
+    Cq, rq, Cs, rs = quartz_silicon_constants()
+    A = fcc_lattice()
+    n = N ** 3
+    idx = np.arange(n)
+    r = np.stack([idx % N, (idx // N) % N, idx // (N * N)], axis=1).astype(np.float64) / N
+    centre = A @ np.full(3, 0.5)
+    R = radius * FCC_A0
+    x = r @ A.T
+    d = np.linalg.norm(x - centre, axis=1)
+    # circumradius of a cell: half the longest diagonal of the parallelepiped spanned by A / N
+    diag = max(np.linalg.norm(A @ np.array(sgn)) for sgn in
+               [(1, 1, 1), (1, 1, -1), (1, -1, 1), (-1, 1, 1)]) / (2 * N)
+    theta = (d <= R).astype(np.float64)
+    cut = np.nonzero(np.abs(d - R) <= diag)[0]
+    off = (np.arange(supersample) + 0.5) / supersample - 0.5
+    sub = np.stack(np.meshgrid(off, off, off, indexing="ij"), axis=-1).reshape(-1, 3) / N  # reduced offsets
+    sub_x = sub @ A.T
+    for lo in range(0, cut.size, 4096):
+        c = cut[lo:lo + 4096]
+        pts = x[c][:, None, :] + sub_x[None, :, :]
+        inside = np.linalg.norm(pts - centre, axis=2) <= R
+        theta[c] = inside.mean(axis=1)
+    return TwoPhaseCell(N=N, C=np.stack([Cq, Cs]), rho=np.array([rq, rs]), phase=None,
+                        theta=theta.astype(np.float32), a_lat=A)

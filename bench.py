@@ -48,7 +48,8 @@ BYTES_PER_NODE = {"c64": 3 * 8 * 2 + 1, "c128": 3 * 16 * 2 + 1}
 FLOPS_PER_NODE = 294
 # DRAM bytes per node of the two-pass complex128 apply (the four kernels together), from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, cold cache, 8 block vectors of the
-# N=48 workload per launch); summary and command in profiles/split_flux_f64_n48.md.
+# N=48 workload per launch: ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum
+# --clock-control none --profile-from-start off -k regex:split_ -c 8 python bench.py --profile kpoint).
 SPLIT_F64_DRAM_BYTES_PER_NODE = (10634752 + 2304 + 16088320 + 3559168 + 18640640 + 14592 + 68762624 + 59136) / 221184
 
 

@@ -12,7 +12,8 @@ Contents:
 * ``sparse_ops``     -- the same operators as scipy.sparse matrices, transcribed
   equation by equation (Sec. 3 and 4).
 * ``oracle``         -- index maps, block restriction, dense pencils, Fourier
-  symbols and closed forms (Sec. 4, 5, App. B, C), eigen oracles, merging
+  symbols and closed forms (Sec. 4, 5, App. B, C), the weighted local SVD and the
+  reference-medium preconditioner built on it (Sec. 5.4), eigen oracles, merging
   (Sec. 6), Hellmann-Feynman gradients.
 
 Parity status of each function is stated in its docstring; "parity unpinned"

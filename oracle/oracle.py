@@ -15,7 +15,11 @@ Pins (tests under ``tests/test_oracle_*.py``, marker ``not gpu``):
 * block reduction: merged dense block spectra equal the dense full spectrum
   (Cor. 4.2), off-block couplings exactly zero;
 * block Fourier basis: dense T_sigma = T F_sigma (Eqs. f_sigma_unified,
-  Tsigma_unified) against the separable form, unitarity;
+  Tsigma_unified) against the separable forms (both directions), unitarity;
+* reference-medium preconditioner: for a homogeneous medium it is the exact
+  inverse of the shifted block operator evaluated by the C apply (independent of
+  the symbols and transforms); the weighted SVD satisfies
+  Eq. weighted_svd_local_unified for any Hermitian positive definite Psi;
 * eigen oracles: dense LAPACK, homogeneous closed form, ARPACK shift-invert.
 """
 
@@ -388,6 +392,108 @@ def block_fourier_separable(w_compact, dims, kappa, b: int) -> np.ndarray:
         plane = Ej @ w_compact[k] @ Ei.T  # (q, p)
         out += np.exp(-1j * k * ga)[:, None, None] * plane[None, :, :]
     return out * (2.0 / np.sqrt(n1 * n2 * n3))
+
+
+def block_fourier_separable_inverse(what, dims, kappa, b: int) -> np.ndarray:
+    """T_sigma what for mode coefficients on the representatives, by separable Bloch sums.
+
+    what: (n3, n2/2, n1/2) indexed (r, q, p); output (n3, n2/2, n1/2) in quarter-grid order
+    (k, j'', i').  Column m of T_sigma on the block is 2 n^-1/2 exp(i(i alpha_p + j beta_q +
+    k gamma_r)) (Eqs. psi_pqr_unified, Tsigma_unified), so
+    w(i', j'', k) = 2 n^-1/2 sum_{p,q,r} what(r,q,p) exp(i(i alpha_p + j beta_q + k gamma_r)).
+    """
+    n1, n2, n3 = dims
+    X, Y = n1 // 2, n2 // 2
+    p12, p13 = b >> 1, b & 1
+    al, be, ga = bloch_freqs(dims, kappa)
+    what = np.asarray(what, dtype=np.complex128).reshape(n3, Y, X)
+    ip = np.arange(X)
+    jp = np.arange(Y)
+    out = np.empty((n3, Y, X), dtype=np.complex128)
+    for k in range(n3):
+        i0 = (k + p13) % 2
+        j0 = (k + p12 + p13) % 2
+        S = np.tensordot(np.exp(1j * k * ga), what, axes=(0, 0))  # (q, p): sum over r
+        Ei = np.exp(1j * np.outer(al[:X], 2 * ip + i0))  # (p, i')
+        Ej = np.exp(1j * np.outer(be[:Y], 2 * jp + j0))  # (q, j'')
+        out[k] = Ej.T @ S @ Ei
+    return out * (2.0 / np.sqrt(n1 * n2 * n3))
+
+
+# --------------------------------------------------------------------------- reference-medium preconditioner (Sec. 5.4)
+def weighted_svd(Bh, Psi):
+    """Psi-weighted local SVD of a 3x6 symbol block (Eq. weighted_svd_unified).
+
+    SVD of B_hat Psi^-1/2 = P Sigma Q~^H; Q = Psi^-1/2 Q~ and Q^{H,Psi} = Q^H Psi, so that
+    B_hat = P Sigma Q^{H,Psi} and Q^{H,Psi} Q = I (Eq. weighted_svd_local_unified).
+    Returns (P (3x3), sigma (3,), Q (6x3), Q^{H,Psi} (3x6)).
+    """
+    Psi = np.asarray(Psi, dtype=np.complex128)
+    w, V = np.linalg.eigh(0.5 * (Psi + Psi.conj().T))
+    Psi_mhalf = (V * (1.0 / np.sqrt(w))) @ V.conj().T
+    P, sig, Qt_h = np.linalg.svd(np.asarray(Bh) @ Psi_mhalf, full_matrices=False)
+    Q = Psi_mhalf @ Qt_h.conj().T
+    return P, sig, Q, Q.conj().T @ Psi
+
+
+def reference_medium(pb: Problem):
+    """Constant reference material: the volume averages of the nodal stiffness and density
+    (for the two-phase rule C_i = (1 - theta_i) C0 + theta_i C1, the rule at the mean theta)."""
+    if pb.C_nodes is None and pb.rho_nodes is None:
+        t = float(np.mean(pb.theta))
+        return (1.0 - t) * pb.C[0] + t * pb.C[1], float((1.0 - t) * pb.rho[0] + t * pb.rho[1])
+    return pb.node_C().mean(axis=0), float(pb.node_rho().mean())
+
+
+def precond_mode_factor(pb: Problem, kappa, sigma: float, p, q, r, C_ref, rho_ref) -> np.ndarray:
+    """F(m) = (B_hat(m) C_ref B_hat(m)^H - sigma rho_ref I_3)^-1 at mode m = (p, q, r).
+
+    Formed from the weighted SVD with Psi = C_ref^-1 (Eq. weighted_svd_unified):
+    B_hat C_ref^(1/2) = P Sigma Q~^H gives B_hat C_ref B_hat^H = P Sigma^2 P^H, hence
+    F(m) = P (Sigma^2 - sigma rho_ref)^-1 P^H.
+    """
+    Psi = np.linalg.inv(np.asarray(C_ref, dtype=np.float64))
+    P, sig, _, _ = weighted_svd(symbol_block(pb.dims, kappa, pb.ainv, p, q, r), Psi)
+    return (P * (1.0 / (sig ** 2 - sigma * rho_ref))) @ P.conj().T
+
+
+def block_mode_vector(dims, kappa, b: int, p, q, r) -> np.ndarray:
+    """Column m = (p, q, r) of T_sigma at every node of block b (quarter-grid order):
+    2 n^-1/2 exp(i(i alpha_p + j beta_q + k gamma_r)) (Eqs. psi_pqr_unified, Tsigma_unified)."""
+    n1, n2, n3 = dims
+    al, be, ga = bloch_freqs(dims, kappa)
+    l = block_index(dims, b)
+    i, j, k = l % n1, (l // n1) % n2, l // (n1 * n2)
+    return np.exp(1j * (i * al[p] + j * be[q] + k * ga[r])) * (2.0 / np.sqrt(n1 * n2 * n3))
+
+
+def precond_block(pb: Problem, kappa, b: int, sigma: float, r, C_ref=None, rho_ref=None) -> np.ndarray:
+    """z = T_sigma diag_m F(m) T_sigma^H r on block b (Sec. 5.4 with a constant reference material),
+    F(m) of ``precond_mode_factor`` for every representative mode m.
+    r: block vector (3, n_b) in quarter-grid order; C_ref, rho_ref default to the volume averages.
+    """
+    n1, n2, n3 = pb.dims
+    X, Y = n1 // 2, n2 // 2
+    if C_ref is None or rho_ref is None:
+        C_ref, rho_ref = reference_medium(pb)
+    r = np.asarray(r, dtype=np.complex128).reshape(3, n3, Y, X)
+    what = np.stack([block_fourier_separable(r[a], pb.dims, kappa, b) for a in range(3)])  # (3, n3, Y, X)
+    what = what.reshape(3, -1)
+    zhat = np.empty_like(what)
+    for idx, (p, q, rr) in enumerate(representatives(pb.dims)):
+        zhat[:, idx] = precond_mode_factor(pb, kappa, sigma, p, q, rr, C_ref, rho_ref) @ what[:, idx]
+    zhat = zhat.reshape(3, n3, Y, X)
+    z = np.stack([block_fourier_separable_inverse(zhat[a], pb.dims, kappa, b) for a in range(3)])
+    return z.reshape(3, -1)
+
+
+def precond_full(pb: Problem, kappa, sigma: float, r) -> np.ndarray:
+    """Full-space preconditioner: the four block preconditioners on the block parts of r."""
+    r = np.asarray(r, dtype=np.complex128).reshape(3, pb.n)
+    z = np.zeros_like(r)
+    for b in range(4):
+        z += inject(pb, b, precond_block(pb, kappa, b, sigma, extract(pb, b, r)))
+    return z
 
 
 # --------------------------------------------------------------------------- eigen oracles (Sec. 6)

@@ -184,6 +184,24 @@ int pc_block_transfer(pc_grid* g, int block, int dtype, int direction, const voi
 int pc_block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* w, void* what,
                      void* stream);
 
+/* Reference-medium preconditioner of the inner solves (Sec. 5.4), applied once:
+ *   z = T_sigma diag_m (B_hat(m) C_ref B_hat(m)^H - sigma rho_ref I_3)^-1 T_sigma^H r
+ * over the block's representative modes m (Eqs. Bhat_xi_m_def, Tsigma_unified), with C_ref
+ * and rho_ref the volume averages of the stiffness and the density in hat units.  This is the
+ * Psi-weighted Fourier SVD of Eq. weighted_svd_unified with Psi = C_ref^-1: the SVD
+ * B_hat(m) C_ref^(1/2) = P Sigma Q^H gives B_hat C_ref B_hat^H = P Sigma^2 P^H, so each mode's
+ * factor is P (Sigma^2 - sigma rho_ref)^-1 P^H.  For a homogeneous medium z solves
+ * (A_hat - sigma M_hat) z = r exactly.
+ * block: 0..3 (r, z block vectors [3][N^3/4]) or -1 (full-space vectors [3][N^3], handled as
+ * its four blocks).  dtype PC_C64 or PC_C128.  fp32_transforms (PC_C128 only; ignored for
+ * PC_C64): run the transforms and the 3x3 solves in complex64 on r rounded once and widen z,
+ * as the FP64 solver does by default (pc_options.precond_fp32).  sigma: hat units, finite;
+ * below the lowest eigenvalue keeps the factor positive definite.  r and z are caller-owned
+ * device vectors and may be the same buffer.  Requires pc_set_k.  Stream-ordered; scratch
+ * comes from the stream-ordered allocator and is released on the same stream. */
+int pc_block_precond(pc_grid* g, int block, int dtype, int fp32_transforms, double sigma,
+                     const void* r, void* z, void* stream);
+
 /* ---- solvers ----------------------------------------------------------- */
 
 /* Solve (A_hat - sigma M_hat) x = rhs on block b by PCG with the block Fourier

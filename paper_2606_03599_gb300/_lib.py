@@ -25,7 +25,7 @@ PC_PREC_FP64, PC_PREC_MIXED = 0, 1
 EXPORTED = [
     "pc_grid_create", "pc_grid_destroy", "pc_grid_units", "pc_set_k", "pc_block_index",
     "pc_block_apply", "pc_block_apply_many", "pc_block_mass", "pc_block_transfer",
-    "pc_block_fourier", "pc_shift_invert_pcg", "pc_options_default", "pc_default_sigma",
+    "pc_block_fourier", "pc_block_precond", "pc_shift_invert_pcg", "pc_options_default", "pc_default_sigma",
     "pc_eigs", "pc_last_error", "pc_version", "pc_apply_batch", "pc_stats_timing", "pc_stats_reset",
     "pc_stats_get", "pc_block_apply_dot_noalloc", "pc_eig_grad", "pc_autotune", "pc_tuned_config",
     "pc_grid_clone", "pc_eigs_batch",
@@ -106,6 +106,7 @@ def _load():
         "pc_block_mass": ([vp, ci, ci, vp, vp, vp], ci),
         "pc_block_transfer": ([vp, ci, ci, ci, vp, vp, vp], ci),
         "pc_block_fourier": ([vp, ci, ci, ci, vp, vp, vp], ci),
+        "pc_block_precond": ([vp, ci, ci, ci, cd, vp, vp, vp], ci),
         "pc_shift_invert_pcg": ([vp, ci, ci, cd, vp, vp, cd, ci, ctypes.POINTER(c_pcg_info), vp], ci),
         "pc_options_default": ([ctypes.POINTER(c_options)], ci),
         "pc_default_sigma": ([vp], cd),
@@ -253,6 +254,12 @@ def pc_block_transfer(g, block, direction, src, dst, stream=None):
 def pc_block_fourier(g, block, inverse, w, what, stream=None):
     _check(lib.pc_block_fourier(g, int(block), _dtype_code(w), int(inverse), _ptr(w), _ptr(what),
                                 _stream(stream)))
+
+
+def pc_block_precond(g, block, sigma, r, z, fp32_transforms=False, stream=None):
+    """z = P_ref r (reference-medium preconditioner, Sec. 5.4); block -1 = full space."""
+    _check(lib.pc_block_precond(g, int(block), _dtype_code(r), int(bool(fp32_transforms)), float(sigma), _ptr(r),
+                                _ptr(z), _stream(stream)))
 
 
 def pc_shift_invert_pcg(g, block, sigma, rhs, x, tol=1e-10, maxit=400, stream=None, raise_on_fail=True):

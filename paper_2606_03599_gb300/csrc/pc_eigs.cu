@@ -908,6 +908,16 @@ int pc_block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* 
     return block_fourier(g, block, dtype, inverse ? 1 : 0, w, what, (cudaStream_t)stream);
 }
 
+int pc_block_precond(pc_grid* g, int block, int dtype, int fp32_transforms, double sigma, const void* r, void* z,
+                     void* stream) {
+    if (!g || !r || !z) return fail(PC_EINVAL, "pc_block_precond: null argument");
+    if (block < -1 || block > 3) return fail(PC_EINVAL, "pc_block_precond: block must be -1..3");
+    if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_block_precond: bad dtype");
+    if (!std::isfinite(sigma)) return fail(PC_EINVAL, "pc_block_precond: non-finite sigma");
+    if (!g->k.set) return fail(PC_ESTATE, "pc_block_precond: call pc_set_k first");
+    return precond_once(g, block, dtype, fp32_transforms != 0, sigma, r, z, (cudaStream_t)stream);
+}
+
 int pc_shift_invert_pcg(pc_grid* g, int block, int dtype, double sigma, const void* rhs, void* x, double tol, int maxit,
                         pc_pcg_info* info, void* stream) {
     if (!g || !rhs || !x) return fail(PC_EINVAL, "pc_shift_invert_pcg: null argument");

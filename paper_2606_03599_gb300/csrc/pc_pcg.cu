@@ -481,6 +481,58 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
     return PC_OK;
 }
 
+// One application of the reference-medium preconditioner outside a solve: block b (one system)
+// or the full space (block < 0: gathered into its four blocks, each preconditioned, scattered
+// back).  Scratch comes from the stream-ordered allocator and is released on the same stream.
+template <typename C>
+static int precond_once_t(pc_grid* g, int block, int dtype, bool fp32_inner, double sigma, const void* r, void* z,
+                          cudaStream_t s) {
+    struct Scratch {
+        cudaStream_t s;
+        void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Scratch() {
+            for (void* q : p)
+                if (q) cudaFreeAsync(q, s);
+        }
+    } sc{s};
+    const bool full = block < 0;
+    const int nsys = full ? 4 : 1;
+    const int64_t vs = 3 * g->nb;
+    const bool lower = fp32_inner && dtype == PC_C128;
+    int hb[4] = {0, 1, 2, 3};
+    if (!full) hb[0] = block;
+    PC_CUDA_TRY(cudaMallocAsync(&sc.p[0], sizeof(int) * 4, s));
+    PC_CUDA_TRY(cudaMemcpyAsync(sc.p[0], hb, sizeof(int) * 4, cudaMemcpyHostToDevice, s));
+    // the partial sums of Re<r, z> are not returned; they keep the unpack on the kernels a solve runs
+    PC_CUDA_TRY(cudaMallocAsync(&sc.p[1], sizeof(double) * nsys * unpack_ctas(vs), s));
+    double* d_part = static_cast<double*>(sc.p[1]);
+    const void* rin = r;
+    void* zout = z;
+    const int gb = (int)std::min<int64_t>((4 * g->nb + 255) / 256, 152 * 16);
+    if (full) {
+        PC_CUDA_TRY(cudaMallocAsync(&sc.p[2], sizeof(C) * 4 * vs, s));
+        PC_CUDA_TRY(cudaMallocAsync(&sc.p[3], sizeof(C) * 4 * vs, s));
+        full_to_blocks<C><<<gb, 256, 0, s>>>(static_cast<const C*>(r), static_cast<C*>(sc.p[2]), g->N, 1);
+        note_launch();
+        rin = sc.p[2];
+        zout = sc.p[3];
+    }
+    PC_TRY(precond_apply(g, dtype, nsys, rin, zout, static_cast<const int*>(sc.p[0]), nullptr, sigma, s, d_part,
+                         nullptr, lower));
+    if (full) {
+        blocks_to_full<C><<<gb, 256, 0, s>>>(static_cast<const C*>(sc.p[3]), static_cast<C*>(z), g->N, 1);
+        note_launch();
+    }
+    PC_CUDA_TRY(cudaGetLastError());
+    return PC_OK;
+}
+
+int precond_once(pc_grid* g, int block, int dtype, bool fp32_inner, double sigma, const void* r, void* z,
+                 cudaStream_t s) {
+    if (dtype == PC_C64) return precond_once_t<float2>(g, block, dtype, false, sigma, r, z, s);
+    return precond_once_t<double2>(g, block, dtype, fp32_inner, sigma, r, z, s);
+}
+
 int pcg_solve(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* B, void* X, double tol,
               int maxit, PcgResult* res, cudaStream_t s, bool pre32) {
     if (nsys <= 0) return PC_OK;

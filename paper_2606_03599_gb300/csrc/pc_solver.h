@@ -57,6 +57,11 @@ struct PcgWork {
 int pcg_solve(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* B, void* X,
               double tol, int maxit, PcgResult* res, cudaStream_t s, bool pre32 = false);
 
+// z = P_ref r once, outside a solve (block 0..3, or -1 for the full space through its four
+// blocks); fp32_inner as pre32 above.
+int precond_once(pc_grid* g, int block, int dtype, bool fp32_inner, double sigma, const void* r, void* z,
+                 cudaStream_t s);
+
 // Launch one batch of stencil applies on grid g (items share the layout kind).
 int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nitems, double* dot_partials,
                int dot_stride, cudaStream_t s, const ApplyConfig* cfg_in);

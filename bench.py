@@ -228,7 +228,9 @@ def run_reference(args):
 
 
 def apply_throughput(pc, torch, reps=20):
-    """Four-block apply at N = 160 (R = 0.3, seed 3), complex64 and complex128, one launch per rep."""
+    """Block apply at N = 160 (R = 0.3, seed 3), complex64 and complex128, one launch per rep:
+    all four blocks in one launch with the shift term (the headline figures), the same without
+    the shift term, and block 0 alone."""
     from workloads import config_cell
     cell = config_cell("precision")
     N = cell.N
@@ -240,11 +242,10 @@ def apply_throughput(pc, torch, reps=20):
         pc.pc_set_k(g, [0.3, 0.1, 0.2])
         nb = N ** 3 // 4
         flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
-        for name, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
-            xs = [torch.randn(3 * nb, dtype=dt, device="cuda") for _ in range(4)]
-            ys = [torch.empty_like(x) for x in xs]
+
+        def timed(name, nodes, launch):
             for _ in range(3):
-                pc.pc_apply_batch(g, [0, 1, 2, 3], xs, ys, [0.5] * 4)
+                launch()
             torch.cuda.synchronize()
             ts = []
             for r in range(reps):
@@ -252,18 +253,52 @@ def apply_throughput(pc, torch, reps=20):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record()
-                pc.pc_apply_batch(g, [0, 1, 2, 3], xs, ys, [0.5] * 4)
+                launch()
                 e1.record()
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1) / 1e3)
             t = sorted(ts)[len(ts) // 2]
-            nodes = 4 * nb
             gbs = nodes * BYTES_PER_NODE[name] / t / 1e9
-            out[name] = {"ms": t * 1e3, "gdof_s": 3 * nodes / t / 1e9, "alg_gbs": gbs, "hbm_frac": gbs / hbm,
-                         "fp_tflops": nodes * FLOPS_PER_NODE / t / 1e12}
+            return {"ms": t * 1e3, "gdof_s": 3 * nodes / t / 1e9, "alg_gbs": gbs, "hbm_frac": gbs / hbm,
+                    "fp_tflops": nodes * FLOPS_PER_NODE / t / 1e12}
+
+        for name, dt in (("c64", torch.complex64), ("c128", torch.complex128)):
+            xs = [torch.randn(3 * nb, dtype=dt, device="cuda") for _ in range(4)]
+            ys = [torch.empty_like(x) for x in xs]
+            res = timed(name, 4 * nb, lambda: pc.pc_apply_batch(g, [0, 1, 2, 3], xs, ys, [0.5] * 4))
+            res["no_shift"] = timed(name, 4 * nb, lambda: pc.pc_apply_batch(g, [0, 1, 2, 3], xs, ys, [0.0] * 4))
+            res["block0_alone"] = timed(name, nb, lambda: pc.pc_block_apply(g, 0, xs[0], ys[0], shift=0.5))
+            out[name] = res
             del xs, ys
     finally:
         pc.pc_grid_destroy(g)
+    return out
+
+
+def cpu_oracle_apply_rate():
+    """The FP64 CPU oracle's full-grid apply on the same N = 160 grid (the DoF of all four blocks),
+    with every host thread (best of 3 after a warm-up) and with one thread (one run)."""
+    from oracle import oracle as O
+    from workloads import complex_gaussian, config_cell
+    cell = config_cell("precision")
+    pb = O.problem_from_cell(cell, C0=1e9, rho0=1e3)
+    x = complex_gaussian((3, cell.N ** 3), 7)
+    kappa = [0.3, 0.1, 0.2]
+    dof = 3 * cell.N ** 3
+    threads = os.cpu_count() or 1
+    out = {"workload": "N=160 two-phase cell (R=0.3, seed 3), full-grid FP64 oracle apply, kappa=(0.3,0.1,0.2), "
+                       "shift on"}
+    O.apply_full(pb, kappa, x, 0.5, nthreads=threads)
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        O.apply_full(pb, kappa, x, 0.5, nthreads=threads)
+        ts.append(time.perf_counter() - t0)
+    out["threads_%d" % threads] = {"ms": min(ts) * 1e3, "gdof_s": dof / min(ts) / 1e9}
+    t0 = time.perf_counter()
+    O.apply_full(pb, kappa, x, 0.5, nthreads=1)
+    t1 = time.perf_counter() - t0
+    out["threads_1"] = {"ms": t1 * 1e3, "gdof_s": dof / t1 / 1e9}
     return out
 
 
@@ -636,6 +671,8 @@ def main():
     # block-apply equivalents per k-point (FP64 applies of the timed steps, counted in nodes)
     applies_per_k = int(round(st["apply_nodes"][1] / (cell.N ** 3 / 4) / args.steps))
     cpu = None if args.no_cpu else cpu_oracle_sample(applies_per_k)
+    if cpu is not None:
+        cpu["apply_n160"] = cpu_oracle_apply_rate()
     pcg_total = sum(i["pcg_iters"] for i in infos)
     line = {
         "metric": METRIC, "value": value, "unit": "s/k-point", "n_gpus": world, "steps": args.steps,

@@ -43,6 +43,13 @@
  *            device loops carry iteration caps and report through status codes.
  * Threads:   a pc_grid handle must not be used by two threads at once; any
  *            number of handles may coexist.
+ * Environment (read once per process; results do not depend on them):
+ *            PC_APPLY_KERNEL = legacy | tma | split forces one stencil-kernel
+ *            family for A/B comparisons (default: the row-tile kernel for
+ *            complex64, the two-pass kernels for complex128, or the autotuner's
+ *            choice); PC_PCG_GRAPHS = 0 turns off CUDA-graph replay of PCG
+ *            iterations; PC_TUNE_CACHE names the autotuner's cache file
+ *            (pc_autotune).
  */
 #ifndef PCBAND_H
 #define PCBAND_H
@@ -57,7 +64,7 @@ extern "C" {
 #define PC_OK 0
 #define PC_EINVAL (-1)      /* bad argument: odd/small N, block, dtype, null pointer */
 #define PC_ENOMEM (-2)      /* device or host allocation failed */
-#define PC_ECUDA (-3)       /* a CUDA / cuFFT / cuBLAS call failed */
+#define PC_ECUDA (-3)       /* a CUDA or cuFFT call failed */
 #define PC_ENOCONV (-4)     /* iteration cap reached; outputs hold the best iterate */
 #define PC_EBREAKDOWN (-5)  /* PCG found p^H (A - sigma M) p <= 0: shifted operator not SPD */
 #define PC_ENAN (-6)        /* NaN or Inf met in a reduction */
@@ -336,7 +343,7 @@ int pc_eig_grad(pc_grid* g, int block, int nvec, const void* X, const double* la
 
 /* ---- diagnostics ------------------------------------------------------- */
 
-/* Process-wide counters of the library's own kernel launches (cuFFT and cuBLAS
+/* Process-wide counters of the library's own kernel launches (cuFFT
  * kernels excluded) and, while timing is enabled, the device time of the
  * stencil-apply launches measured with CUDA events on their launch stream. */
 typedef struct {

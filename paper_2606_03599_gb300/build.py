@@ -2,7 +2,7 @@
 host-side kernel emulator used by the CPU tests.
 
 Each CUDA translation unit is compiled by its own nvcc process (in parallel),
-then linked with cuFFT and cuBLAS.  A rebuild happens only when a source or
+then linked with cuFFT.  A rebuild happens only when a source or
 header is newer than the library.
 """
 

@@ -84,7 +84,7 @@ ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool
         // tile height follows the shape code of launch_tma_shape: 16x16 / 16x8 or 8x8
         const int ty = (c.shape == 0 && dtype == PC_C64) ? 16 : 8;
         const int tiles = ((X + tx - 1) / tx) * ((Y + ty - 1) / ty);
-        const long target = 152L * 2;  // two resident CTAs per SM: one full wave
+        const long target = 2L * device_sm_count();  // two resident CTAs per SM: one full wave
         long nch = (target + (long)tiles * nitems - 1) / ((long)tiles * nitems);
         const long maxch = Z / 6 > 0 ? Z / 6 : 1;
         if (nch > maxch) nch = maxch;
@@ -105,7 +105,7 @@ ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool
     }
     const int tiles = ((X + tile_tx(c.shape) - 1) / tile_tx(c.shape)) *
                       ((Y + tile_ty(c.shape) - 1) / tile_ty(c.shape));
-    const long target = 152L * 4;  // about four resident CTAs per SM
+    const long target = 4L * device_sm_count();  // about four resident CTAs per SM
     long nch = (target + (long)tiles * nitems - 1) / ((long)tiles * nitems);
     const long maxch = Z / 4 > 0 ? Z / 4 : 1;
     if (nch > maxch) nch = maxch;

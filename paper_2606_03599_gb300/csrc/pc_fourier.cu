@@ -339,7 +339,8 @@ int unpack_ctas(int64_t vs) {
 
 static int nblocks_for(int64_t work) {
     int64_t g = (work + 255) / 256;
-    if (g > 152 * 8) g = 152 * 8;
+    const int64_t cap = 8LL * device_sm_count();
+    if (g > cap) g = cap;
     return (int)(g < 1 ? 1 : g);
 }
 

@@ -156,7 +156,7 @@ extern "C" int pc_eig_grad(pc_grid* g, int block, int nvec, const void* X, const
     PC_CUDA_TRY(cudaMemcpyAsync(dw, weights, sizeof(double) * nvec, cudaMemcpyHostToDevice, s));
     const int64_t m = (int64_t)P.X * P.Y * P.Z;
     int64_t gb = (m + 127) / 128;
-    if (gb > 152 * 16) gb = 152 * 16;
+    if (gb > 16LL * device_sm_count()) gb = 16LL * device_sm_count();
     eig_grad_kernel<<<(int)gb, 128, 0, s>>>(P, nvec, static_cast<const double2*>(X), dl, dw, dC, drho, g->n);
     note_launch();
     PC_CUDA_TRY(cudaGetLastError());

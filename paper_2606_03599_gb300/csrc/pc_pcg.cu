@@ -351,7 +351,7 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
     int nrz = 0;
     auto precondition = [&](const int* skip) -> int {
         if (!full) return precond_apply(g, dtype, nsys, R, Z, w->blocks, skip, sigma, s, part_c, &nrz, flex);
-        const int gb = (int)std::min<int64_t>((nsys * vs + 255) / 256, 152 * 16);
+        const int gb = (int)std::min<int64_t>((nsys * vs + 255) / 256, 16LL * device_sm_count());
         full_to_blocks<C><<<gb, 256, 0, s>>>(R, static_cast<C*>(Rb), g->N, nsys);
         note_launch();
         int np = 0;
@@ -508,7 +508,7 @@ static int precond_once_t(pc_grid* g, int block, int dtype, bool fp32_inner, dou
     double* d_part = static_cast<double*>(sc.p[1]);
     const void* rin = r;
     void* zout = z;
-    const int gb = (int)std::min<int64_t>((4 * g->nb + 255) / 256, 152 * 16);
+    const int gb = (int)std::min<int64_t>((4 * g->nb + 255) / 256, 16LL * device_sm_count());
     if (full) {
         PC_CUDA_TRY(cudaMallocAsync(&sc.p[2], sizeof(C) * 4 * vs, s));
         PC_CUDA_TRY(cudaMallocAsync(&sc.p[3], sizeof(C) * 4 * vs, s));

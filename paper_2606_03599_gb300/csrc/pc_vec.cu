@@ -42,7 +42,7 @@ __global__ void transfer_kernel(const C* __restrict__ src, C* __restrict__ dst, 
 
 static int grid_for(int64_t m) {
     int64_t g = (m + 255) / 256;
-    if (g > 152 * 16) g = 152 * 16;
+    if (g > 16LL * device_sm_count()) g = 16LL * device_sm_count();
     if (g < 1) g = 1;
     return (int)g;
 }

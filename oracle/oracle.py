@@ -337,6 +337,36 @@ def homogeneous_spectrum(dims, kappa, ainv, C, rho) -> np.ndarray:
     return np.sort(np.concatenate(out))
 
 
+def homogeneous_spectrum_planes(dims, kappa, ainv, C, rho) -> np.ndarray:
+    """``homogeneous_spectrum`` evaluated one r-plane of modes at a time with array operations,
+    for grids where a loop over every mode is too slow.  The symbol is the one of
+    ``symbol_block`` (Eqs. Sd_phase_maintext, delta1-3_xi_unified, Bhat_xi_m_def) on arrays:
+    s_l = exp(i(alpha +- beta +- gamma)), d_l = (s_l - 1)/h_d,
+    delta_s = h_d/(4 h_s) sum_l c_{s l} d_l, eta_m = sum_s (A_lat^-1)_{s m} (-i delta_s)."""
+    n1, n2, n3 = dims
+    h = np.array([1.0 / m for m in dims])
+    hd = np.sqrt(np.sum(h ** 2))
+    al, be, ga = bloch_freqs(dims, kappa)
+    a, bb = al[None, :], be[:, None]  # (q, p) plane of modes
+    C = np.asarray(C, dtype=np.float64)
+    out = []
+    for r in range(n3):
+        g = ga[r]
+        s = np.stack([np.exp(1j * (a + bb + g)), np.exp(1j * (a + bb - g)),
+                      np.exp(1j * (a - bb + g)), np.exp(1j * (a - bb - g))])
+        d = (s - 1.0) / hd
+        delta = np.stack([hd / (4.0 * h[t]) * np.tensordot(so.C_SIGNS[t], d, axes=(0, 0)) for t in range(3)])
+        eta = np.tensordot(np.asarray(ainv).T, -1j * delta, axes=(1, 0))  # eta[m] = sum_s ainv[s, m] (-i delta[s])
+        e1, e2, e3 = eta
+        Bh = np.zeros((n2, n1, 3, 6), dtype=np.complex128)
+        Bh[..., 0, 0], Bh[..., 0, 4], Bh[..., 0, 5] = e1, e3, e2
+        Bh[..., 1, 1], Bh[..., 1, 3], Bh[..., 1, 5] = e2, e3, e1
+        Bh[..., 2, 2], Bh[..., 2, 3], Bh[..., 2, 4] = e3, e2, e1
+        S = Bh @ C @ np.conj(np.swapaxes(Bh, -1, -2))
+        out.append(np.linalg.eigvalsh(0.5 * (S + np.conj(np.swapaxes(S, -1, -2)))).reshape(-1) / rho)
+    return np.sort(np.concatenate(out))
+
+
 # --------------------------------------------------------------------------- block Fourier basis (Sec. 5.2)
 def representatives(dims):
     """Representative set R = {p < n1/2, q < n2/2, all r} of the half-period orbits (Eq. orbit_unified)."""

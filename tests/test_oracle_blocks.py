@@ -51,6 +51,19 @@ def test_off_block_couplings_vanish(kappa):
     assert np.all(Acoo.data[off] == 0)
 
 
+@pytest.mark.parametrize("N", [4, 6, 8])
+def test_plane_by_plane_closed_form_equals_per_mode_loop(N):
+    """The array form used at large N equals the per-mode closed form (skew lattice, two kappas)."""
+    rng = np.random.default_rng(9)
+    G = rng.standard_normal((6, 6))
+    C = G @ G.T + 3 * np.eye(6)
+    ainv = np.linalg.inv(np.array([[1.0, 0.2, 0.0], [0.1, 1.1, 0.3], [0.0, -0.2, 0.9]]))
+    for kappa in ([0.3, -0.1, 0.2], [0.0, 0.0, 0.0]):
+        ref = O.homogeneous_spectrum((N,) * 3, kappa, ainv, C, 1.7)
+        got = O.homogeneous_spectrum_planes((N,) * 3, kappa, ainv, C, 1.7)
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 @pytest.mark.parametrize("N", [4, 8])
 @pytest.mark.parametrize("kappa", [np.array([0.3, 0.1, 0.2]), np.zeros(3), np.array([0.5, 0.5, 0.5])])
 def test_merged_block_spectra_equal_full(N, kappa):

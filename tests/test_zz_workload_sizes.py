@@ -1,0 +1,92 @@
+"""Eigen-solver parity at the workloads' full grid sizes (N = 48: the FP64 band workload;
+N = 160: the precision workload), where the oracle's dense and ARPACK solves are out of reach.
+
+* A homogeneous medium has a closed-form spectrum at any size: the union over all modes of
+  eig(B_hat(m) C B_hat(m)^H) / rho (Sec. 5.3, App. B), evaluated by the oracle plane by plane.
+  The solver's lowest 20 eigenvalues must equal it to 1e-10 relative, in FP64 and in mixed
+  precision with FP64 refinement.
+* On the heterogeneous N = 48 workload cell, every returned eigenpair is checked with the
+  oracle's matrix-free C apply: true residual ||A x - lambda M x|| <= 1e-8 |lambda| ||M x||
+  (which bounds the eigenvalue's distance to the spectrum), M-orthonormality to 1e-9.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from workloads import two_phase_sphere
+from workloads.materials import TwoPhaseCell
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pc():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2606_03599_gb300 as pc
+    return pc
+
+
+class Grid:
+    def __init__(self, pc, cell):
+        self.pc = pc
+        self.h = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=cell.phase, theta=cell.theta,
+                                   a_lat=cell.a_lat)
+        self.C0, self.rho0, self.L = pc.pc_grid_units(self.h)
+        self.pb = O.problem_from_cell(cell, C0=self.C0, rho0=self.rho0, L=self.L)
+        self.to_si = self.C0 / (self.rho0 * self.L ** 2)
+
+    def close(self):
+        self.pc.pc_grid_destroy(self.h)
+
+
+def _homogeneous_cell(N):
+    rng = np.random.default_rng(4)
+    G = rng.standard_normal((6, 6))
+    C = (G @ G.T + 6 * np.eye(6)) * 1e10
+    return TwoPhaseCell(N=N, C=np.stack([C, C]), rho=np.array([2000.0, 2000.0]), phase=None, theta=None,
+                        a_lat=np.eye(3))
+
+
+@pytest.mark.parametrize("kappa", [[0.3, 0.1, 0.2], [0.0, 0.0, 0.0]])
+def test_n48_workload_eigenpairs_pass_the_oracle_residual(pc, kappa):
+    import torch
+    N, nev = 48, 20
+    g = Grid(pc, two_phase_sphere(N, 0.35, 2))
+    try:
+        evecs = torch.empty(nev * 3 * N ** 3, dtype=torch.complex128, device="cuda")
+        ev, blocks, info = pc.pc_eigs(g.h, kappa, nev, evecs=evecs)
+        assert np.all(np.diff(ev) >= 0) and np.all(ev > 0)
+        V = evecs.cpu().numpy().reshape(nev, 3, -1)
+        rho = g.pb.node_rho()
+        for i in range(nev):
+            lam = ev[i] / g.to_si
+            Mv = rho[None, :] * V[i]
+            r = O.apply_full(g.pb, kappa, V[i]) - lam * Mv
+            assert np.linalg.norm(r) <= 1e-8 * abs(lam) * np.linalg.norm(Mv), i
+        W = V.reshape(nev, -1)
+        gram = (W.conj() * np.tile(rho, 3)[None, :]) @ W.T
+        assert np.abs(gram - np.eye(nev)).max() <= 1e-9
+    finally:
+        g.close()
+
+
+_CLOSED_FORM = {}
+
+
+@pytest.mark.parametrize("N,precision", [(48, "fp64"), (160, "fp64"), (160, "mixed")])
+def test_homogeneous_closed_form_at_workload_sizes(pc, N, precision):
+    kappa = [0.21, 0.13, 0.05]
+    g = Grid(pc, _homogeneous_cell(N))
+    try:
+        prec = pc.PC_PREC_MIXED if precision == "mixed" else pc.PC_PREC_FP64
+        ev, blocks, info = pc.pc_eigs(g.h, kappa, 20, opt=pc.pc_options_default(precision=prec))
+        key = (N, tuple(kappa))
+        if key not in _CLOSED_FORM:
+            _CLOSED_FORM[key] = O.homogeneous_spectrum_planes(g.pb.dims, kappa, g.pb.ainv, g.pb.C[0], g.pb.rho[0])
+        cf = _CLOSED_FORM[key][:20] * g.to_si
+        assert np.abs(ev - cf).max() / cf.max() <= 1e-10
+        assert info["max_rel_resid"] <= 1e-8
+    finally:
+        g.close()

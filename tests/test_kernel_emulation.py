@@ -74,6 +74,9 @@ CASES = [
     (4, 0, 2, 30, 0), (4, 3, 2, 30, 0), (4, -1, 2, 30, 0), (8, 1, 2, 30, 0), (8, 2, 2, 30, 0),
     (8, -1, 2, 30, 0), (12, 3, 2, 30, 0), (16, 0, 2, 30, 0),
     (8, 1, 1, 30, 0), (12, -1, 1, 30, 0), (16, 2, 1, 30, 0),
+    # odd quarter-grid widths (X = N/2 = 3, 5, 7): two-pass and register-staged kernels
+    (6, 3, 2, 30, 0), (10, 1, 2, 30, 0), (10, -1, 2, 30, 0), (14, 2, 1, 30, 0),
+    (6, 0, 2, 3, 2), (10, 2, 1, 3, 3), (14, -1, 2, 2, 5), (10, 3, 2, 1, 4),
 ]
 
 

@@ -175,10 +175,9 @@ def test_apply_argument_errors(pc):
 
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 def test_block_apply_sampled_n160(pc, dtype):
-    """Full-size grid of the apply benchmark (N = 160, R = 0.3, seed 3), in the
-    launch configuration the bench times (all four blocks through
-    pc_block_apply_many per block), checked on sampled outputs the oracle
-    computes node by node."""
+    """Full-size grid of the apply benchmark (N = 160, R = 0.3, seed 3), one launch
+    per block (pc_block_apply_many), checked on sampled outputs the oracle computes
+    node by node."""
     import torch
     N = 160
     cell = two_phase_sphere(N, 0.3, 3)

@@ -1,5 +1,8 @@
-"""Eigen-solver parity at the workloads' full grid sizes (N = 48: the FP64 band workload;
-N = 160: the precision workload), where the oracle's dense and ARPACK solves are out of reach.
+"""Parity at the workloads' full grid sizes (N = 48: the FP64 band workload; N = 160: the
+apply and precision workloads), where the oracle's dense and ARPACK solves are out of reach.
+
+* The block apply exactly as the bench times it (all four blocks in one launch, N = 160) on
+  sampled outputs the oracle computes node by node.
 
 * A homogeneous medium has a closed-form spectrum at any size: the union over all modes of
   eig(B_hat(m) C B_hat(m)^H) / rho (Sec. 5.3, App. B), evaluated by the oracle plane by plane.
@@ -14,7 +17,7 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from workloads import two_phase_sphere
+from workloads import complex_gaussian, two_phase_sphere
 from workloads.materials import TwoPhaseCell
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +50,42 @@ def _homogeneous_cell(N):
     C = (G @ G.T + 6 * np.eye(6)) * 1e10
     return TwoPhaseCell(N=N, C=np.stack([C, C]), rho=np.array([2000.0, 2000.0]), phase=None, theta=None,
                         a_lat=np.eye(3))
+
+
+TOL = {"c128": 1e-12, "c64": 2e-6}
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_four_block_batch_apply_n160_as_benchmarked(pc, dtype):
+    """N = 160 (R = 0.3, seed 3), all four parity blocks in one pc_apply_batch launch with
+    shift 0.5 at kappa = (0.3, 0.1, 0.2), as the bench times it; per block, random nodes plus
+    the quarter grid's faces (the Bloch-wrap paths) against the oracle."""
+    import torch
+    N = 160
+    g = Grid(pc, two_phase_sphere(N, 0.3, 3))
+    try:
+        kappa = [0.3, 0.1, 0.2]
+        pc.pc_set_k(g.h, kappa)
+        nb, X = N ** 3 // 4, N // 2
+        td = torch.complex64 if dtype == "c64" else torch.complex128
+        xs_host = [complex_gaussian((3, nb), 20 + b) for b in range(4)]
+        xs = [torch.from_numpy(x.reshape(-1)).to(td).cuda() for x in xs_host]
+        ys = [torch.empty_like(x) for x in xs]
+        pc.pc_apply_batch(g.h, [0, 1, 2, 3], xs, ys, [0.5] * 4)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(12)
+        for b in range(4):
+            y = ys[b].cpu().numpy().astype(np.complex128).reshape(3, -1)
+            t = rng.integers(0, nb, 1000)
+            a, bb, k = rng.integers(0, X, 200), rng.integers(0, X, 200), rng.integers(0, N, 200)
+            faces = np.concatenate([0 + X * (bb + X * k), (X - 1) + X * (bb + X * k),
+                                    a + X * (0 + X * k), a + X * ((X - 1) + X * k),
+                                    a + X * (bb + X * 0), a + X * (bb + X * (N - 1))])
+            ts = np.unique(np.concatenate([t, faces]))
+            ref = O.apply_block_at(g.pb, kappa, b, xs_host[b], ts, 0.5)
+            assert np.abs(y[:, ts].T - ref).max() <= TOL[dtype] * np.abs(ref).max(), b
+    finally:
+        g.close()
 
 
 @pytest.mark.parametrize("kappa", [[0.3, 0.1, 0.2], [0.0, 0.0, 0.0]])

@@ -299,7 +299,7 @@ struct Eigs {
     }
 };
 
-static const cuDoubleComplex kOne = {1.0, 0.0}, kZero = {0.0, 0.0}, kMinusOne = {-1.0, 0.0};
+static const cuDoubleComplex kOne = {1.0, 0.0}, kZero = {0.0, 0.0};
 
 // dh (device, rows x cols) = A^H M B in the mass inner product of space S.
 static int gram_m(Eigs& E, const Space& S, const double2* A, int rows, const double2* B, int cols, cd* dh) {

@@ -11,6 +11,8 @@ apply and precision workloads), where the oracle's dense and ARPACK solves are o
 * On the heterogeneous N = 48 workload cell, every returned eigenpair is checked with the
   oracle's matrix-free C apply: true residual ||A x - lambda M x|| <= 1e-8 |lambda| ||M x||
   (which bounds the eigenvalue's distance to the spectrum), M-orthonormality to 1e-9.
+* On the same grid, a right-hand side holding a NaN ends the inner solve with PC_ENAN and
+  leaves x at its zero start (the status path of the reductions, no device fault).
 """
 
 import numpy as np
@@ -127,5 +129,23 @@ def test_homogeneous_closed_form_at_workload_sizes(pc, N, precision):
         cf = _CLOSED_FORM[key][:20] * g.to_si
         assert np.abs(ev - cf).max() / cf.max() <= 1e-10
         assert info["max_rel_resid"] <= 1e-8
+    finally:
+        g.close()
+
+
+def test_n48_pcg_with_nan_right_hand_side_reports_enan(pc):
+    import torch
+    N = 48
+    g = Grid(pc, two_phase_sphere(N, 0.35, 2))
+    try:
+        pc.pc_set_k(g.h, [0.3, 0.1, 0.2])
+        rhs = torch.from_numpy(complex_gaussian(3 * N ** 3 // 4, 31)).cuda()
+        rhs[1234] = complex(float("nan"), 0.0)
+        x = torch.empty_like(rhs)
+        r = pc.pc_shift_invert_pcg(g.h, 0, pc.pc_default_sigma(g.h), rhs, x, tol=1e-10, maxit=50,
+                                   raise_on_fail=False)
+        torch.cuda.synchronize()
+        assert r["rc"] == pc.PC_ENAN and r["status"] == pc.PC_ENAN
+        assert torch.count_nonzero(x).item() == 0
     finally:
         g.close()

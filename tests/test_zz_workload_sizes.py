@@ -13,6 +13,8 @@ apply and precision workloads), where the oracle's dense and ARPACK solves are o
   (which bounds the eigenvalue's distance to the spectrum), M-orthonormality to 1e-9.
 * On the same grid, a right-hand side holding a NaN ends the inner solve with PC_ENAN and
   leaves x at its zero start (the status path of the reductions, no device fault).
+* Guard bands: outputs written into views of larger buffers leave a sentinel on both sides
+  untouched (no write outside the caller's vector), for the benchmarked launches.
 """
 
 import numpy as np
@@ -147,5 +149,54 @@ def test_n48_pcg_with_nan_right_hand_side_reports_enan(pc):
         torch.cuda.synchronize()
         assert r["rc"] == pc.PC_ENAN and r["status"] == pc.PC_ENAN
         assert torch.count_nonzero(x).item() == 0
+    finally:
+        g.close()
+
+
+GUARD = 1024  # elements on each side of a guarded vector (keeps 16-byte and larger alignments)
+SENTINEL = complex(12345.0, -678.0)
+
+
+def _guarded(torch, n, dtype):
+    buf = torch.full((GUARD + n + GUARD,), SENTINEL, dtype=dtype, device="cuda")
+    return buf, buf[GUARD:GUARD + n]
+
+
+def _guards_intact(buf, n):
+    head, tail = buf[:GUARD], buf[GUARD + n:]
+    return bool(((head == SENTINEL).all() & (tail == SENTINEL).all()).item())
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_outputs_stay_inside_the_callers_vectors(pc, dtype):
+    import torch
+    td = torch.complex64 if dtype == "c64" else torch.complex128
+    # N = 160: all four blocks in one launch, as the bench times it
+    N = 160
+    nb = N ** 3 // 4
+    g = Grid(pc, two_phase_sphere(N, 0.3, 3))
+    try:
+        pc.pc_set_k(g.h, [0.3, 0.1, 0.2])
+        xs = [torch.from_numpy(complex_gaussian(3 * nb, 40 + b)).to(td).cuda() for b in range(4)]
+        guarded = [_guarded(torch, 3 * nb, td) for _ in range(4)]
+        pc.pc_apply_batch(g.h, [0, 1, 2, 3], xs, [v for _, v in guarded], [0.5] * 4)
+        torch.cuda.synchronize()
+        for buf, v in guarded:
+            assert _guards_intact(buf, 3 * nb)
+            assert bool(torch.isfinite(torch.view_as_real(v)).all().item())
+    finally:
+        g.close()
+    # N = 48: eight vectors of one block in one launch (the solver's batched apply)
+    N, count = 48, 8
+    nb = N ** 3 // 4
+    g = Grid(pc, two_phase_sphere(N, 0.35, 2))
+    try:
+        pc.pc_set_k(g.h, [0.3, 0.1, 0.2])
+        x = torch.from_numpy(complex_gaussian(count * 3 * nb, 50)).to(td).cuda()
+        buf, y = _guarded(torch, count * 3 * nb, td)
+        pc.pc_block_apply_many(g.h, 2, count, x, y, 0.5)
+        torch.cuda.synchronize()
+        assert _guards_intact(buf, count * 3 * nb)
+        assert bool(torch.isfinite(torch.view_as_real(y)).all().item())
     finally:
         g.close()

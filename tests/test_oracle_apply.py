@@ -202,3 +202,24 @@ def test_fcc_workload_geometry():
     exact = (4.0 / 3.0) * math.pi * (0.25 * FCC_A0) ** 3 / (FCC_A0 ** 3 / 4)
     assert abs(th.mean() - exact) <= 2e-4
     assert 0 < np.count_nonzero((th > 0) & (th < 1)) < th.size // 4
+
+
+def test_fcc_path_and_bloch_vector_conversion():
+    """The paper's 91-point FCC path (9 segments of 10 intervals, vertices in route order), and
+    the conversion of its Cartesian points (units 2 pi / a0) to reduced kappa with
+    q . a_l = 2 pi kappa_l; kappa is defined modulo integers, so Gamma maps to 0 and L, which
+    both readings share, to (1/2, 1/2, 1/2)."""
+    from workloads import FCC_POINTS, fcc_kappa, fcc_lattice, fcc_path
+    from workloads.kpath import FCC_ROUTE
+    from workloads.materials import FCC_A0
+    path = fcc_path(10)
+    assert path.shape == (91, 3)
+    for s, name in enumerate(FCC_ROUTE):
+        assert np.array_equal(path[10 * s], FCC_POINTS[name])
+    A = fcc_lattice()
+    for name, k in FCC_POINTS.items():
+        kap = fcc_kappa(k, A, FCC_A0)
+        q = 2 * np.pi * np.asarray(k) / FCC_A0
+        assert np.allclose([q @ A[:, l] for l in range(3)], 2 * np.pi * kap, rtol=0, atol=1e-12)
+    assert np.allclose(fcc_kappa(FCC_POINTS["G"], A, FCC_A0), 0.0)
+    assert np.allclose(fcc_kappa(FCC_POINTS["L"], A, FCC_A0), 0.5)

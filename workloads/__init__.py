@@ -15,5 +15,5 @@ from .materials import (  # noqa: F401
     fcc_lattice,
     fcc_quartz_silicon_cell,
 )
-from .kpath import FCC_POINTS, sc_path, sc_eight_points, sc_uniform_path  # noqa: F401
+from .kpath import FCC_POINTS, fcc_kappa, fcc_path, sc_path, sc_eight_points, sc_uniform_path  # noqa: F401
 from .vectors import complex_gaussian  # noqa: F401

@@ -60,3 +60,22 @@ FCC_POINTS = {
     "L": np.array([0.5, 0.5, 0.5]),
     "U": np.array([0.25, 0.625, 0.625]),
 }
+FCC_ROUTE = ["G", "X", "W", "K", "G", "L", "U", "W", "L", "K"]
+
+
+def fcc_path(intervals_per_segment: int = 10) -> np.ndarray:
+    """The paper's FCC path Gamma-X-W-K-Gamma-L-U-W-L-K (Sec. 7) with equal intervals per
+    segment, vertices included: 9 * 10 + 1 = 91 points, in the coordinates of ``FCC_POINTS``."""
+    pts = [FCC_POINTS["G"]]
+    for a, b in zip(FCC_ROUTE[:-1], FCC_ROUTE[1:]):
+        pa, pb = FCC_POINTS[a], FCC_POINTS[b]
+        for s in range(1, intervals_per_segment + 1):
+            pts.append(pa + (pb - pa) * (s / intervals_per_segment))
+    return np.array(pts)
+
+
+def fcc_kappa(k_cartesian, a_lat, a0) -> np.ndarray:
+    """Reduced Bloch vector kappa_l = a_l . k / a0 of a wave vector k given in Cartesian units of
+    2 pi / a0 (the reading under which the paper's listed FCC points reproduce its printed
+    results), so that q . a_l = 2 pi kappa_l with q = 2 pi k / a0."""
+    return np.asarray(a_lat, dtype=np.float64).T @ np.asarray(k_cartesian, dtype=np.float64) / a0

@@ -147,3 +147,32 @@ def test_planted_transposed_mode_factor_fails_the_exactness_pin(monkeypatch):
     z = O.precond_block(hp, kappa, 1, sigma, r)
     back = O.apply_block(hp, kappa, 1, z, shift=sigma)
     assert np.abs(back - r).max() > 1e-3 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("mistake", ["shift_sign", "conjugate_forward"])
+def test_planted_shift_sign_or_conjugated_transform_fails_the_exactness_pin(monkeypatch, mistake):
+    """Planted mistakes: the shift term added with the wrong sign, or the forward transform
+    taken with the conjugate phase (the inverse left as is); each must break the pin."""
+    N = 4
+    C = _spd6(5)
+    hp = O.homogeneous_problem(N, C, 2.5)
+    sigma = -0.3 * np.abs(C).max() / 2.5
+    kappa = [0.23, -0.41, 0.17]
+    if mistake == "shift_sign":
+        real = O.precond_mode_factor
+
+        def wrong(pb, kap, sig, p, q, r, C_ref, rho_ref):
+            return real(pb, kap, -sig, p, q, r, C_ref, rho_ref)
+
+        monkeypatch.setattr(O, "precond_mode_factor", wrong)
+    else:
+        real = O.block_fourier_separable
+
+        def wrong(w, dims, kap, b):
+            return np.conj(real(np.conj(w), dims, kap, b))
+
+        monkeypatch.setattr(O, "block_fourier_separable", wrong)
+    r = complex_gaussian((3, N ** 3 // 4), 62)
+    z = O.precond_block(hp, kappa, 2, sigma, r)
+    back = O.apply_block(hp, kappa, 2, z, shift=sigma)
+    assert np.abs(back - r).max() > 1e-3 * np.abs(r).max()

@@ -161,7 +161,7 @@ def kpoint_index(step, world, rank, nk):
     return (step * world + rank) % nk
 
 
-def cpu_oracle_sample(apply_count_per_kpoint, seconds_budget=15.0):
+def cpu_oracle_sample(apply_count_per_kpoint, seconds=15.0):
     """Time the FP64 CPU oracle apply (OpenMP) on block applies of the N = 48 workload,
     and scale by the number of block applies one k-point solve performs."""
     import numpy as np
@@ -179,7 +179,7 @@ def cpu_oracle_sample(apply_count_per_kpoint, seconds_budget=15.0):
         O.apply_block(pb, kappa, n % 4, x, 0.1, nthreads=threads)
         n += 1
         el = time.perf_counter() - t0
-        if el >= seconds_budget or n >= 2000:
+        if el >= seconds or n >= 2000:
             break
     per_apply = el / n
     return {"value": per_apply * apply_count_per_kpoint, "unit": "s/k-point", "cores": threads, "kind": "oracle",

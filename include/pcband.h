@@ -44,12 +44,21 @@
  * Threads:   a pc_grid handle must not be used by two threads at once; any
  *            number of handles may coexist.
  * Environment (read once per process; results do not depend on them):
- *            PC_APPLY_KERNEL = legacy | tma | split forces one stencil-kernel
- *            family for A/B comparisons (default: the row-tile kernel for
- *            complex64, the two-pass kernels for complex128, or the autotuner's
- *            choice); PC_PCG_GRAPHS = 0 turns off CUDA-graph replay of PCG
+ *            PC_APPLY_KERNEL = legacy | tma | split | row forces one stencil-
+ *            kernel family for A/B comparisons (default: the plane-pipelined
+ *            kernel for complex64 parity blocks, the two-pass kernels for
+ *            complex128, or the autotuner's choice); PC_PCG_GRAPHS = 0 turns off CUDA-graph replay of PCG
  *            iterations; PC_TUNE_CACHE names the autotuner's cache file
- *            (pc_autotune).
+ *            (pc_autotune); PC_WAIT_LIMIT = n sets how many polls a kernel's
+ *            wait on its own shared-memory copies makes before it gives up
+ *            (default 2^26; see pc_device_status).
+ * Device waits: kernels that stage data through bulk or tensor copies wait
+ *            on them with a bounded number of polls.  When a wait runs out the
+ *            kernel lets its copies in flight land, records the event in the
+ *            grid's device error word and returns, leaving its part of the
+ *            output unwritten (inner products: NaN).  pc_shift_invert_pcg and
+ *            pc_eigs read and clear that word before they return and then fail
+ *            with PC_ECUDA; pc_device_status does the same for applies.
  */
 #ifndef PCBAND_H
 #define PCBAND_H
@@ -75,7 +84,9 @@ extern "C" {
 #define PC_C128 2  /* complex128: FP64 storage and FP64 arithmetic */
 
 /* ---- precision of pc_eigs ---------------------------------------------- */
-#define PC_PREC_FP64 0   /* every step in FP64 (plain method) */
+#define PC_PREC_FP64 0   /* FP64 operator, inner PCG iterates, Krylov recurrences and residuals; the
+                            Fourier preconditioner of the inner PCG runs in complex64 unless
+                            pc_options.precond_fp32 = 0 (then every step is FP64) */
 #define PC_PREC_MIXED 1  /* complex64 inner PCG, FP64 outer Krylov + residual refinement */
 
 typedef struct pc_grid pc_grid; /* opaque, owned by the library */
@@ -157,7 +168,9 @@ int pc_set_k(pc_grid* g, const double kappa[3]);
 
 /* Host-only index map (no GPU needed): full_node_of_t[t] = full index l of
  * position t of block b, for t < N^3/4 (ascending l; Sec. 4, Eq. V_sigma_main).
- * full_node_of_t is caller-owned host memory of N^3/4 entries. */
+ * full_node_of_t is caller-owned host memory of N^3/4 entries.  Takes the grid
+ * size N rather than a grid handle: the map depends on N only, and taking N
+ * lets it run without a device. */
 int pc_block_index(int N, int block, int64_t* full_node_of_t);
 
 /* ---- operator ---------------------------------------------------------- */
@@ -174,6 +187,12 @@ int pc_block_apply(pc_grid* g, int block, int dtype, const void* x, void* y, dou
  * x and y hold `count` consecutive vectors of 3*m elements each. */
 int pc_block_apply_many(pc_grid* g, int block, int dtype, int count, const void* x, void* y,
                         double shift, void* stream);
+
+/* Status of the device work enqueued on `stream` for grid g: synchronises the
+ * stream, then reads and clears the grid's device error word.  PC_OK, or
+ * PC_ECUDA when a kernel's bounded wait on its own copies expired since the
+ * last check (the outputs of the launches since then are incomplete). */
+int pc_device_status(pc_grid* g, void* stream);
 
 /* Apply M_hat (nodewise density, Eq. discrete_GEP) to a block vector. */
 int pc_block_mass(pc_grid* g, int block, int dtype, const void* x, void* y, void* stream);
@@ -259,12 +278,15 @@ int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const vo
  * (16 KiB) that every device loading the library holds until the process
  * exits; no call allocates or frees.  Limits: at most 2^24 nodes per call
  * (N <= 406 for a block, N <= 256 for the full space), else PC_EINVAL with the
- * reason.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls on a device share the array: calls whose
- * kernels overlap on the GPU race and may return a wrong *dot, so order them
- * on one stream.  Each call rewrites every slot it reads, so no state carries
- * over between calls.  Enqueued on `stream`. */
+ * reason; within that limit every grid size is accepted (the call picks a
+ * launch of at most 2048 CTAs).  x and y must not overlap.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls on a device share the array: calls whose kernels overlap on the GPU
+ * race and may return a wrong *dot, so order them on one stream.  Each call
+ * rewrites every slot it reads (a CTA whose bounded copy wait expired writes
+ * NaN into its slot), so no state carries over between calls; an expired wait
+ * during the call also makes *dot NaN.  Enqueued on `stream`. */
 int pc_block_apply_dot_noalloc(pc_grid* g, int block, int dtype, const void* x, void* y, double shift,
                                double* dot, void* stream);
 
@@ -318,8 +340,10 @@ int pc_autotune(pc_grid* g, int dtype, int layout, int nitems, void* stream);
 
 /* The launch configuration the library will use for a batch of `nitems` vectors of `dtype` in
  * layout 0 (blocks) or 1 (full): kind 0 = register-staged, 1 = TMA tile, 2 = row tile, 3 = two-pass
- * (fluxes once per node, then gather; the default for complex128); tile shape code; planes per CTA
- * (tz; row kernel: least planes per CTA); CTAs of the launch (two-pass: of its gather). */
+ * (fluxes once per node, then gather; the default for complex128), 4 = plane-pipelined (producer
+ * warp + consumer warps; the default for complex64 parity blocks); tile shape code; planes per CTA
+ * (tz; row and plane-pipelined kernels: least planes per CTA); CTAs of the launch (two-pass: of
+ * its gather). */
 int pc_tuned_config(const pc_grid* g, int dtype, int layout, int nitems, int* kind, int* shape, int* tz, int* ctas);
 
 /* ---- differentiation --------------------------------------------------- */
@@ -370,6 +394,14 @@ const char* pc_last_error(void);
 
 /* Library version string. */
 const char* pc_version(void);
+
+/* FP64 FMA throughput of the current device (no counterpart in the paper: the denominator of
+ * the FP64 roofline of the complex128 kernels).  Runs a kernel of independent FP64 FMA chains
+ * on every SM, growing its length until one launch takes about seconds/4, and returns the best
+ * rate of the later launches: *tflops = 2 x FMA/s / 1e12, *fma_per_s (may be NULL) the FP64
+ * FMA instruction rate summed over all threads.  Allocates and frees 8 bytes; synchronises
+ * the device's legacy default stream.  seconds in (0, 60]. */
+int pc_fp64_peak(double seconds, double* tflops, double* fma_per_s);
 
 #ifdef __cplusplus
 }

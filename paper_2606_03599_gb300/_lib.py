@@ -28,7 +28,7 @@ EXPORTED = [
     "pc_block_fourier", "pc_block_precond", "pc_shift_invert_pcg", "pc_options_default", "pc_default_sigma",
     "pc_eigs", "pc_last_error", "pc_version", "pc_apply_batch", "pc_stats_timing", "pc_stats_reset",
     "pc_stats_get", "pc_block_apply_dot_noalloc", "pc_eig_grad", "pc_autotune", "pc_tuned_config",
-    "pc_grid_clone", "pc_eigs_batch",
+    "pc_grid_clone", "pc_eigs_batch", "pc_device_status", "pc_fp64_peak",
 ]
 
 
@@ -123,6 +123,8 @@ def _load():
         "pc_stats_timing": ([ci], ci),
         "pc_stats_reset": ([], ci),
         "pc_stats_get": ([ctypes.POINTER(c_stats)], ci),
+        "pc_device_status": ([vp, vp], ci),
+        "pc_fp64_peak": ([cd, dp, dp], ci),
         "pc_last_error": ([], ctypes.c_char_p),
         "pc_version": ([], ctypes.c_char_p),
     }
@@ -316,8 +318,25 @@ def pc_block_apply_dot_noalloc(g, block, x, y, dot, shift=0.0, stream=None):
 
     ``dot`` is a caller-owned device tensor holding one float64.
     """
+    import torch
+    if not (isinstance(dot, torch.Tensor) and dot.is_cuda and dot.dtype == torch.float64 and dot.numel() >= 1):
+        raise ValueError("dot must be a float64 CUDA tensor with at least one element")
+    if x.dtype != y.dtype or x.numel() != y.numel():
+        raise ValueError("x and y must have the same dtype and size")
     _check(lib.pc_block_apply_dot_noalloc(g, int(block), _dtype_code(x), _ptr(x), _ptr(y), float(shift),
                                           _ptr(dot), _stream(stream)))
+
+
+def pc_fp64_peak(seconds=0.5):
+    """Measured FP64 FMA throughput of the current device: (TFLOP/s, FMA instructions/s)."""
+    t, f = ctypes.c_double(), ctypes.c_double()
+    _check(lib.pc_fp64_peak(float(seconds), ctypes.byref(t), ctypes.byref(f)))
+    return t.value, f.value
+
+
+def pc_device_status(g, stream=None):
+    """Synchronise the stream and raise PcError (PC_ECUDA) if a kernel's bounded copy wait expired."""
+    _check(lib.pc_device_status(g, _stream(stream)))
 
 
 def pc_eig_grad(g, block, X, lambdas, weights, dC, drho, stream=None):

@@ -11,6 +11,7 @@
 #include "../pc_apply_tile.cuh"
 #include "../pc_apply_tma.cuh"
 #include "../pc_apply_row.cuh"
+#include "../pc_apply_pipe.cuh"
 #include "../pc_apply_split.cuh"
 
 using namespace pc;
@@ -196,6 +197,137 @@ static void emu_row_x(const StencilParams<float>& P, int block, const void* x, v
     emu_run_row<CUBIC, MATK, 0>(P, block, x, y, mat, shift, ctas);
 }
 
+// Same segment, plane and step sequence as apply_pipe_kernel (complex64 parity blocks) with
+// `ctas` persistent CTAs.  The producer is modelled as issuing each plane copy as early as the
+// kernel's ring allows (right after the consumers release the slot's previous plane), so a
+// premature reuse of a slot shows up as a wrong output; the copies are immediate.
+template <bool CUBIC, int MATK, int XC, int TC>
+static void emu_run_pipe(const StencilParams<float>& P, int block, const void* x, void* y, const void* mat,
+                         double shift, int ctas, int Tr) {
+    using T = PipeTile<CUBIC, MATK, XC, TC>;
+    const PipeGeom G = make_pipe_geom(P.X, P.Y, P.Z, MATK, XC > 0 ? TC : Tr);
+    if ((XC > 0 && (G.X != XC || G.Y != XC)) || !pipe_geom_fits(G) || (G.X & 1)) {
+        std::fprintf(stderr, "pipe geometry not supported\n");
+        std::abort();
+    }
+    const size_t NS = (size_t)G.ns;
+    std::vector<unsigned char> matp((size_t)G.Xp * G.Y * G.Z * G.matsz, 0);
+    for (int64_t row = 0; row < (int64_t)G.Y * G.Z; ++row)
+        std::memcpy(&matp[(size_t)row * G.Xp * G.matsz],
+                    static_cast<const unsigned char*>(mat) + (size_t)row * G.X * G.matsz, (size_t)G.X * G.matsz);
+    std::vector<unsigned char> smem(G.total);
+    typename T::Sh sh{smem.data(), &G};
+    std::vector<typename T::Regs> regs(G.NC);
+    const int64_t W = (int64_t)G.nt * G.Z;  // one item
+    for (int cta = 0; cta < ctas; ++cta) {
+        std::memset(smem.data(), 0xFF, smem.size());  // poison: reads of unwritten cells show up as NaN
+        for (int t = 0; t < G.NC; ++t) T::load_tables(P, sh, t, G.NC);
+        for (int t = 0; t < G.NC; ++t) T::init(G, t, regs[t]);
+        const int64_t u0 = (int64_t)cta * W / ctas, u1 = (int64_t)(cta + 1) * W / ctas;
+        // the CTA's segments and, in order, every plane the producer copies
+        std::vector<PipeSeg> segs;
+        std::vector<std::pair<int, int>> seq;  // (segment, plane)
+        for (int64_t u = u0; u < u1;) {
+            int item, tile, ks, ke;
+            pipe_seg_at(G, u, u1, item, tile, ks, ke);
+            u += ke - ks;
+            PC_IDX(item, 1);
+            PipeSeg S;
+            S.b0 = pipe_tile_lo(G, tile);
+            S.Vt = pipe_tile_lo(G, tile + 1) - S.b0;
+            if (S.Vt < 1 || S.Vt > G.V) {
+                std::fprintf(stderr, "bad tile height %d\n", S.Vt);
+                std::abort();
+            }
+            S.top = S.b0 == 0;
+            S.bot = S.b0 + S.Vt == G.Y;
+            S.ks = ks;
+            S.ke = ke;
+            S.p12 = block >> 1;
+            S.p13 = block & 1;
+            S.x = static_cast<const float2*>(x);
+            S.y = static_cast<float2*>(y);
+            S.mat = matp.data();
+            S.shift = (float)shift;
+            for (int kp = ks - 2; kp <= ke + 1; ++kp) seq.emplace_back((int)segs.size(), kp);
+            segs.push_back(S);
+        }
+        size_t issued = 0;
+        std::vector<char> released(seq.size(), 0);
+        auto pump = [&]() {
+            while (issued < seq.size() && (issued < NS || released[issued - NS])) {
+                T::host_copy_plane(G, segs[seq[issued].first], sh, (int)(issued % NS), seq[issued].second);
+                ++issued;
+            }
+        };
+        auto need = [&](size_t qq) {
+            pump();
+            if (qq >= issued) {
+                std::fprintf(stderr, "plane %zu needed before it can be issued (ring deadlock)\n", qq);
+                std::abort();
+            }
+        };
+        auto release = [&](size_t qq) {
+            PC_IDX(qq, seq.size());
+            if (released[qq]) {
+                std::fprintf(stderr, "plane %zu released twice\n", qq);
+                std::abort();
+            }
+            released[qq] = 1;
+            pump();
+        };
+        // launches with an odd CTA count model the launch without the inner product (its slots are
+        // released before the flux step instead of after the gather)
+        const bool want_dot = (ctas & 1) == 0;
+        size_t q = 0;
+        for (const PipeSeg& S : segs) {
+            for (int t = 0; t < G.NC; ++t) T::seg_begin(regs[t]);
+            const size_t q0 = q;
+            auto slot_of = [&](int kp) { return (int)((q0 + (size_t)(kp - S.ks + 2)) % NS); };
+            need(q0);
+            need(q0 + 1);
+            for (int t = 0; t < G.NC; ++t) T::prologue(P, G, S, sh, regs[t], slot_of(S.ks - 2), slot_of(S.ks - 1));
+            const int nsteps = S.ke - S.ks + 2;
+            for (int j = 0; j < nsteps; ++j) {
+                const int kf = S.ks - 1 + j;
+                if (!want_dot) release(q0 + (size_t)j);
+                need(q0 + (size_t)j + 2);
+                const int buf = j & 1;
+                for (int t = 0; t < G.NC; ++t) {
+                    if (j & 1) T::template flux_step<1>(P, G, S, sh, regs[t], kf, slot_of(kf), slot_of(kf + 1), buf);
+                    else T::template flux_step<0>(P, G, S, sh, regs[t], kf, slot_of(kf), slot_of(kf + 1), buf);
+                }
+                for (int t = 0; t < G.NC; ++t) {
+                    if (j & 1) T::template gather_step<1>(P, G, S, sh, regs[t], kf, slot_of(kf - 1), buf, want_dot);
+                    else T::template gather_step<0>(P, G, S, sh, regs[t], kf, slot_of(kf - 1), buf, want_dot);
+                }
+                if (want_dot) release(q0 + (size_t)j);
+            }
+            release(q0 + (size_t)nsteps);
+            release(q0 + (size_t)nsteps + 1);
+            q = q0 + (size_t)nsteps + 2;
+        }
+        if (q != seq.size()) {
+            std::fprintf(stderr, "plane sequence mismatch\n");
+            std::abort();
+        }
+    }
+}
+
+template <bool CUBIC, int MATK>
+static void emu_pipe_x(const StencilParams<float>& P, int block, const void* x, void* y, const void* mat,
+                       double shift, int ctas, bool ct, int Tr) {
+    if (ct && MATK == 0 && P.X == P.Y) {
+        switch (P.X) {
+            case 16: return emu_run_pipe<CUBIC, MATK, 16, pipe_rows_for(16)>(P, block, x, y, mat, shift, ctas, 0);
+            case 24: return emu_run_pipe<CUBIC, MATK, 24, pipe_rows_for(24)>(P, block, x, y, mat, shift, ctas, 0);
+            case 32: return emu_run_pipe<CUBIC, MATK, 32, pipe_rows_for(32)>(P, block, x, y, mat, shift, ctas, 0);
+            default: break;
+        }
+    }
+    emu_run_pipe<CUBIC, MATK, 0, 0>(P, block, x, y, mat, shift, ctas, Tr);
+}
+
 // Same four passes as the two-pass complex128 kernels, scratch poisoned with NaN first so that
 // a read of a cell no pass wrote shows up in the output.
 template <typename R, bool FULL, bool CUBIC, int MATK>
@@ -270,6 +402,21 @@ extern "C" int pc_emu_apply(int N, int block, int dtype, int shape, int tz, cons
             } else {
                 if (matkind) emu_row_x<false, 1>(P, block, x, y, mat, shift, tz, ct);
                 else emu_row_x<false, 0>(P, block, x, y, mat, shift, tz, ct);
+            }
+            return 0;
+        }
+        if (shape == 40 || shape == 41 || (shape > 50 && shape <= 58)) {
+            // plane-pipelined kernel (41: compile-time width; 5T: runtime geometry with T thread rows),
+            // tz = persistent CTAs
+            if (full) return -1;
+            const bool ct = shape == 41;
+            const int Tr = shape > 50 ? shape - 50 : 0;
+            if (cubic) {
+                if (matkind) emu_pipe_x<true, 1>(P, block, x, y, mat, shift, tz, ct, Tr);
+                else emu_pipe_x<true, 0>(P, block, x, y, mat, shift, tz, ct, Tr);
+            } else {
+                if (matkind) emu_pipe_x<false, 1>(P, block, x, y, mat, shift, tz, ct, Tr);
+                else emu_pipe_x<false, 0>(P, block, x, y, mat, shift, tz, ct, Tr);
             }
             return 0;
         }

@@ -31,15 +31,42 @@ int tile_ty(int shape) { return shape <= 2 ? 8 : 4; }
 
 static int apply_kernel_mode() {
     // PC_APPLY_KERNEL=legacy selects the register-staged kernel everywhere, =tma the TMA tile
-    // kernel in place of the row kernel, =split the two-pass kernels for both precisions (A/B
-    // comparisons)
+    // kernel in place of the plane-pipelined kernel, =split the two-pass kernels for both
+    // precisions, =row the row-tile kernel (A/B comparisons)
     static int mode = -1;
     if (mode < 0) {
         const char* v = std::getenv("PC_APPLY_KERNEL");
         const std::string m = v ? v : "";
-        mode = m == "legacy" ? 1 : (m == "tma" ? 2 : (m == "split" ? 3 : 0));
+        mode = m == "legacy" ? 1 : (m == "tma" ? 2 : (m == "split" ? 3 : (m == "row" ? 4 : 0)));
     }
     return mode;
+}
+
+uint32_t wait_limit() {
+    static uint32_t lim = 0;
+    static bool read = false;
+    if (!read) {
+        lim = 1u << 26;
+        if (const char* v = std::getenv("PC_WAIT_LIMIT")) {
+            char* end = nullptr;
+            const unsigned long long n = std::strtoull(v, &end, 10);
+            if (end != v && *end == 0 && n <= 0xffffffffull) lim = (uint32_t)n;
+        }
+        read = true;
+    }
+    return lim;
+}
+
+int grid_device_status(pc_grid* g, cudaStream_t s) {
+    if (!g->d_err) return PC_OK;
+    int h = 0;
+    PC_CUDA_TRY(cudaMemcpyAsync(&h, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h == 0) return PC_OK;
+    PC_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), s));
+    PC_CUDA_TRY(cudaStreamSynchronize(s));
+    return fail(PC_ECUDA, "a bounded device wait expired: the outputs of the launches since the last status "
+                          "check are incomplete");
 }
 
 int device_sm_count() {
@@ -65,7 +92,16 @@ ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool
         c.ctas = split_apply_ctas((int64_t)X * Y * Z);
         return c;
     }
-    if (apply_kernel_mode() == 0 && blocks && dtype == PC_C64 && X % 2 == 0 && row_geom_fits(X, Y, Z, matkind)) {
+    if (apply_kernel_mode() == 0 && blocks && dtype == PC_C64 && pipe_geom_ok(X, Y, Z, matkind)) {
+        // plane-pipelined kernel: persistent, whole rows per tile, producer warp + consumer warps
+        c.pipe = true;
+        c.shape = 0;
+        c.tz = 12;  // planes per CTA at least
+        c.ctas = pipe_apply_ctas(X, Y, Z, matkind, nitems, c.tz);
+        return c;
+    }
+    if ((apply_kernel_mode() == 0 || apply_kernel_mode() == 4) && blocks && dtype == PC_C64 && X % 2 == 0 &&
+        row_geom_fits(X, Y, Z, matkind)) {
         // row-tile kernel: persistent, whole rows per tile
         c.row = true;
         c.tma = false;
@@ -351,6 +387,15 @@ int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nit
             rc = launch_apply_split_f64(full, g->cubic, g->matkind, P, items, nitems, g->d_split, g->split_bytes,
                                         dot_partials, dot_stride, s);
         }
+    } else if (dtype == PC_C64 && cfg.pipe) {
+        StencilParams<float> P = g->P32;
+        P.X = X;
+        P.Y = Y;
+        P.Z = Z;
+        std::vector<const void*> mats(nitems);
+        for (int i = 0; i < nitems; ++i) mats[i] = items[i].block >= 0 ? g->d_mat_row[items[i].block] : nullptr;
+        rc = launch_apply_pipe_f32(g->cubic, g->matkind, P, items, mats.data(), nitems, cfg.ctas, dot_partials,
+                                   dot_stride, g->d_err, s);
     } else if (dtype == PC_C64 && cfg.row) {
         StencilParams<float> P = g->P32;
         P.X = X;
@@ -441,6 +486,11 @@ int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const vo
         items[i].skip = nullptr;
     }
     return grid_apply(g, dtype, full, items.data(), count, nullptr, 0, (cudaStream_t)stream, nullptr);
+}
+
+int pc_device_status(pc_grid* g, void* stream) {
+    if (!g) return fail(PC_EINVAL, "pc_device_status: null grid");
+    return grid_device_status(g, (cudaStream_t)stream);
 }
 
 int pc_block_apply(pc_grid* g, int block, int dtype, const void* x, void* y, double shift, void* stream) {

@@ -1,0 +1,581 @@
+// Fused stencil apply, plane-pipelined variant (complex64, parity blocks).
+//
+// Same operator as pc_apply_tile.cuh (see there for the algebra: backward
+// differences along the four body diagonals, reconstruction, Voigt strain,
+// nodewise stiffness, fluxes F_l and the forward gather; Sec. 3, Eqs. Sd_def,
+// Dd_def, Dtilde_recon_main, B_discrete_main).  The design is organised
+// around the two facts that bound this kernel on GB300: the data movement is
+// a plain stream (x read once, y written once), and the per-node arithmetic
+// and shared-memory traffic must stay small enough to run under that stream.
+//
+// Tiling.  A tile is V_t <= V consecutive rows b of the quarter grid, all X
+// columns a (so the a-direction wraps inside the tile), marched through the
+// planes k.  For the body diagonals d = (1, s2, s3) of a parity block the
+// neighbours of plane k sit in planes k -+ 1, shifted in the plane by
+// (i0(k), j0(k)) with i0(k) = (k + p13) mod 2, j0(k) = (k + p12 + p13) mod 2.
+// Consequences used below (derived from the step rule of pc_apply_tile.cuh):
+//   * the x rows any step reads are always [b0 - 1, b0 + V_t]: a plane slot
+//     holds V_t + 2 rows ("slot row" s <-> row b0 - 1 + s);
+//   * the fluxes of plane kf are needed on V_t + 1 rows, flux row
+//     f <-> row b0 - j0(kf) + f, f = 0..V_t;
+//   * flux row f reads its s2 = +1 neighbours on slot row f and its s2 = -1
+//     neighbours on slot row f + 1, in column a + i0(kf) - 1 of planes
+//     kf -+ 1, and its own value on slot row f + 1 - j0(kf);
+//   * output row o (row b0 + o) of plane p reads F_0, F_1 on flux row o + 1
+//     and F_2, F_3 on flux row o, in column a + i0(p), of planes p +- 1, and
+//     its local term sum_l F_l on flux row o + j0(p) of plane p.
+//
+// Threads.  Consumer thread (a, t) computes flux rows 2t and 2t + 1 of column
+// a.  Their s2 = +-1 neighbours in one plane are the three slot rows 2t, 2t+1,
+// 2t+2 of column a + i0 - 1.  Steps kf and kf + 2 have the same parity, so the
+// neighbours that step kf loads from plane kf + 1 (its s3 = -1 side) are
+// exactly those that step kf + 2 needs from the same plane (its s3 = +1 side):
+// each thread keeps two such sets of 9 complex values in registers and loads
+// one new set per step.  The same thread owns output rows 2t - j0(p) and
+// 2t + 1 - j0(p) of plane p, whose local terms are its own fluxes, so the
+// local term goes straight into the accumulator; only the F_l of the two
+// neighbouring flux rows pass through shared memory (double-buffered by plane
+// parity, one named barrier among the consumer warps per plane).
+//
+// Data movement.  One producer warp (one elected lane) fills a ring of NS
+// plane slots with bulk copies (cp.async.bulk, completion counted by a "full"
+// mbarrier per slot): per plane three copies of V_t + 2 contiguous rows of x
+// and one of the row-padded material; wrapped halo rows and planes outside
+// [0, Z) come from the other end of the grid.  Consumers release a slot
+// through an "empty" mbarrier (one arrival per consumer warp) once the plane
+// is no longer read: by the flux step q (own values; its neighbour values live
+// on in registers), or, when the launch forms <x, y>, by the gather of step
+// q + 1, which re-reads x for the inner product.
+// Bloch phases of wrapped values (exp(-+i phi) of the axis crossed) are
+// applied in registers as values are loaded, so shared memory holds the plain
+// copies.
+//
+// Every mbarrier wait is bounded (B.wait_limit polls).  A consumer whose wait
+// runs out sets a shared abort flag and the device error word; after the next
+// named barrier every consumer writes NaN into its inner-product slots and
+// returns, and the producer, which checks the flag while it waits, lets its
+// copies in flight land (bounded again) before the CTA exits.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include <cstring>
+
+#include "pc_apply_tma.cuh"
+
+namespace pc {
+
+constexpr int kPipeMaxItems = 64;
+constexpr int kPipeMaxThreads = 416;  // consumer warps + the producer warp, one CTA per SM
+
+struct PipeGeom {
+    int X, Y, Z;
+    int T;      // consumer thread rows (two flux rows each)
+    int V;      // most output rows per tile = 2T - 1
+    int nt;     // tiles per plane (balanced: rows [t Y / nt, (t+1) Y / nt))
+    int NC;     // consumer threads (X * T rounded up to whole warps)
+    int SR;     // rows per plane slot = V + 2
+    int Xp;     // material row pitch in elements (16-byte rows)
+    int matsz;  // 1 = uint8 phase id, 4 = float theta
+    int ns;     // plane slots in the ring
+    // dynamic shared memory layout, byte offsets from a 128-byte aligned base
+    int slot_bytes, off_mat, off_flux, fbuf_bytes, off_cp, off_rho, off_full, off_empty, off_flag, off_red, total;
+};
+
+PC_HD int pipe_tile_lo(const PipeGeom& G, int t) { return (int)(((int64_t)t * G.Y) / G.nt); }
+
+// Thread rows per width: the most that keeps X * T near 320 consumer threads (two flux rows each
+// need about 160 registers), at least 1.
+constexpr int pipe_rows_for(int X) { return X >= 320 ? 1 : (320 / X > 8 ? 8 : 320 / X); }
+
+inline PipeGeom make_pipe_geom(int X, int Y, int Z, int matkind, int T = 0) {
+    PipeGeom G;
+    G.X = X;
+    G.Y = Y;
+    G.Z = Z;
+    G.T = T > 0 ? T : pipe_rows_for(X);
+    G.V = 2 * G.T - 1;
+    G.nt = (Y + G.V - 1) / G.V;
+    G.NC = (X * G.T + 31) / 32 * 32;
+    G.SR = G.V + 2;
+    G.matsz = matkind ? 4 : 1;
+    const int q = 16 / G.matsz;
+    G.Xp = (X + q - 1) / q * q;
+    auto al = [](int v) { return (v + 127) / 128 * 128; };
+    G.off_mat = 3 * G.SR * X * 8;  // inside a slot: x [3][SR][X] float2, then material [SR][Xp]
+    G.slot_bytes = al(G.off_mat + G.SR * G.Xp * G.matsz);
+    // fluxes of one plane: components 0 and 1 as [4 l][2T flux rows][X] float4, then component 2 as
+    // [4 l][2T][X] float2 (one 16-byte and one 8-byte access per flux instead of three 8-byte ones)
+    G.fbuf_bytes = 4 * 2 * G.T * X * (16 + 8);
+    const int fixed = al(2 * G.fbuf_bytes) + al(2 * 36 * 8 + 2 * 4) + al(2 * 8 * 8 + 16) + al(32 * 8);
+    G.ns = 6;
+    while (G.ns > 3 && G.ns * G.slot_bytes + fixed + 128 + 1024 > 227 * 1024) --G.ns;
+    G.off_flux = G.ns * G.slot_bytes;
+    G.off_cp = al(G.off_flux + 2 * G.fbuf_bytes);  // stiffness pairs [2][36] float2
+    G.off_rho = G.off_cp + 2 * 36 * 8;
+    G.off_full = al(G.off_rho + 2 * 4);
+    G.off_empty = G.off_full + 8 * 8;
+    G.off_flag = G.off_empty + 8 * 8;
+    G.off_red = al(G.off_flag + 16);
+    G.total = al(G.off_red + 32 * 8);
+    return G;
+}
+
+inline bool pipe_geom_fits(const PipeGeom& G) {
+    return G.ns >= 3 && G.total + 128 + 1024 <= 227 * 1024 && G.NC + 32 <= 1024 && G.V >= 1;
+}
+
+struct PipeBatch {
+    ApplyItem it[kPipeMaxItems];
+    const void* mat_row[kPipeMaxItems];  // row-padded material of each item's block
+    int n;
+    int* err;             // device error word (1 when a bounded wait expired)
+    uint32_t wait_limit;  // mbarrier polls before a wait gives up
+};
+
+// One (item, tile) piece of a CTA's plane range.
+struct PipeSeg {
+    int b0, Vt;    // tile rows [b0, b0 + Vt)
+    bool top, bot; // slot row 0 is the wrapped row Y - 1 (b0 = 0); slot row Vt + 1 is the wrapped row 0
+    int ks, ke;    // output planes [ks, ke)
+    int p12, p13;
+    const float2* x;
+    float2* y;
+    const void* mat;
+    float shift;
+};
+
+// Split of the linear work index u = (item * nt + tile) * Z + k.
+PC_HD void pipe_seg_at(const PipeGeom& G, int64_t u, int64_t uend, int& item, int& tile, int& ks, int& ke) {
+    const int64_t it_tile = u / G.Z;
+    item = (int)(it_tile / G.nt);
+    tile = (int)(it_tile % G.nt);
+    ks = (int)(u % G.Z);
+    const int64_t lim = (it_tile + 1) * (int64_t)G.Z;
+    ke = (int)((uend < lim ? uend : lim) - it_tile * (int64_t)G.Z);
+}
+
+// XC > 0: compile-time width X (= Y) with TC thread rows, so that shared-memory strides are
+// immediates; XC = 0: runtime geometry.  PK: complex arithmetic in the packed FP32x2 instructions
+// of sm_100-class SMs (one instruction per complex add or real-times-complex FMA) or in scalar FP32
+// instructions (two per operation, but constants as immediate operands); both round identically.
+template <bool CUBIC, int MATK, int XC = 0, int TC = 0, bool PK = true>
+struct PipeTile {
+    using C = float2;
+
+    static PC_HD C cadd(C a, C b) { return PK ? ::pc::cadd(a, b) : make_float2(a.x + b.x, a.y + b.y); }
+    static PC_HD C csub(C a, C b) { return PK ? ::pc::csub(a, b) : make_float2(a.x - b.x, a.y - b.y); }
+    static PC_HD C cscale(float r, C a) { return PK ? ::pc::cscale(r, a) : make_float2(r * a.x, r * a.y); }
+    static PC_HD C cfma(float r, C a, C acc) {
+        return PK ? ::pc::cfma(r, a, acc) : make_float2(fmaf(r, a.x, acc.x), fmaf(r, a.y, acc.y));
+    }
+    static PC_HD C cmul(C a, C b) {
+        return PK ? ::pc::cmul(a, b) : make_float2(fmaf(-a.y, b.y, a.x * b.x), fmaf(a.y, b.x, a.x * b.y));
+    }
+
+    static PC_HD int Xw(const PipeGeom& G) { return XC > 0 ? XC : G.X; }
+    static PC_HD int Tw(const PipeGeom& G) { return XC > 0 ? TC : G.T; }
+    static PC_HD int SRw(const PipeGeom& G) { return XC > 0 ? 2 * TC + 1 : G.SR; }
+    static PC_HD int FRw(const PipeGeom& G) { return 2 * Tw(G); }
+    // with a compile-time width the grid is the quarter grid of a cubic N^3 grid: Y = X, Z = N = 2X
+    static PC_HD int Yw(const PipeGeom& G) { return XC > 0 ? XC : G.Y; }
+    static PC_HD int Zw(const PipeGeom& G) { return XC > 0 ? 2 * XC : G.Z; }
+
+    struct Regs {
+        int a, t;
+        C S[2][3][3];    // neighbour sets [step parity][slot row 2t + r][component]
+        C acc[2][2][3];  // outputs in progress [output-plane parity][node][component]
+        float dot;
+    };
+
+    struct Sh {  // views into dynamic shared memory
+        unsigned char* base;
+        const PipeGeom* G;
+        PC_HD const C* xslot(int slot) const {
+            return reinterpret_cast<const C*>(base + (size_t)slot * G->slot_bytes);
+        }
+        PC_HD C* xslot_w(int slot) const { return reinterpret_cast<C*>(base + (size_t)slot * G->slot_bytes); }
+        PC_HD const unsigned char* mslot(int slot) const {
+            return base + (size_t)slot * G->slot_bytes + G->off_mat;
+        }
+        PC_HD unsigned char* mslot_w(int slot) const { return base + (size_t)slot * G->slot_bytes + G->off_mat; }
+        PC_HD float4* fA(int buf) const {
+            return reinterpret_cast<float4*>(base + G->off_flux + (size_t)buf * G->fbuf_bytes);
+        }
+        PC_HD float2* fB(int buf) const {
+            return reinterpret_cast<float2*>(base + G->off_flux + (size_t)buf * G->fbuf_bytes +
+                                             (size_t)4 * 2 * G->T * G->X * 16);
+        }
+        PC_HD float2* cp() const { return reinterpret_cast<float2*>(base + G->off_cp); }
+        PC_HD float* rho() const { return reinterpret_cast<float*>(base + G->off_rho); }
+        PC_HD uint64_t* full() const { return reinterpret_cast<uint64_t*>(base + G->off_full); }
+        PC_HD uint64_t* empty() const { return reinterpret_cast<uint64_t*>(base + G->off_empty); }
+        PC_HD int* flag() const { return reinterpret_cast<int*>(base + G->off_flag); }
+        PC_HD double* red() const { return reinterpret_cast<double*>(base + G->off_red); }
+    };
+
+    // exp(i w phi_axis), w in {-1, 0, 1}
+    static PC_HD C phase_of(const StencilParams<float>& P, int axis, int w) {
+        if (w == 0) return cmk(1.f, 0.f);
+        return cmk(P.ph[axis][0], w < 0 ? -P.ph[axis][1] : P.ph[axis][1]);
+    }
+    static PC_HD int plane_wrap(const PipeGeom& G, int kp) { return kp < 0 ? -1 : (kp >= G.Z ? 1 : 0); }
+    // Bloch phase of slot row s of a plane with plane wrap wk (rows -1 and Y of the grid are wrapped)
+    static PC_HD bool row_phase(const StencilParams<float>& P, const PipeGeom& G, const PipeSeg& S, int s, int wk,
+                                C& ph) {
+        const int wr = (s == 0 && S.top) ? -1 : ((s == S.Vt + 1 && S.bot) ? 1 : 0);
+        if (wr == 0 && wk == 0) return false;
+        ph = cmul(phase_of(P, 1, wr), phase_of(P, 2, wk));
+        return true;
+    }
+
+    static PC_HD float mat_at(const Sh& sh, const PipeGeom& G, int slot, int s, int a) {
+        const unsigned char* m = sh.mslot(slot);
+        const int idx = s * G.Xp + a;
+        PC_IDX(idx, G.SR * G.Xp);
+        if (MATK == 0) return (float)m[idx];
+        return reinterpret_cast<const float*>(m)[idx];
+    }
+
+    static PC_HD void load_tables(const StencilParams<float>& P, const Sh& sh, int tid, int nthreads) {
+        for (int i = tid; i < 72; i += nthreads) sh.cp()[i] = make_float2(P.C[i / 36][i % 36], P.C[i / 36][i % 36]);
+        if (tid < 2) sh.rho()[tid] = P.rho[tid];
+    }
+
+    static PC_HD void init(const PipeGeom& G, int tid, Regs& r) {
+        r.a = tid % Xw(G);
+        r.t = tid / Xw(G);
+        r.dot = 0.f;
+    }
+
+    static PC_HD void seg_begin(Regs& r) {
+        for (int q = 0; q < 2; ++q)
+            for (int n = 0; n < 2; ++n)
+                for (int c = 0; c < 3; ++c) r.acc[q][n][c] = czero(0.f);
+    }
+
+    // The neighbour set of thread row t in the plane held by `slot` (plane index kp): slot rows
+    // 2t .. 2t+2 of column a + i0 - 1, i0 = i0(kf) of the step kf = kp - 1 that first uses it.
+    static PC_HD void load_set(const StencilParams<float>& P, const PipeGeom& G, const PipeSeg& S, const Sh& sh,
+                               int a, int t, int slot, int kp, int i0, C out[3][3]) {
+        const int X = Xw(G), SR = SRw(G);
+        int na = a + i0 - 1;
+        const bool wa = na < 0;
+        if (wa) na += X;
+        const int wk = plane_wrap(G, kp);
+        const C* xs = sh.xslot(slot);
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr) {
+            const int s = 2 * t + rr;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int idx = (c * SR + s) * X + na;
+                PC_IDX(idx, 3 * G.SR * G.X);
+                out[rr][c] = xs[idx];
+            }
+        }
+        // rows 2t .. 2t+2 hold a wrapped grid row only at the tile's wrapped ends
+        const bool rowwrap = (S.top && t == 0) || (S.bot && 2 * t + 2 >= S.Vt + 1);
+        if (!(wa || wk != 0 || rowwrap)) return;
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr) {
+            const int s = 2 * t + rr;
+            C ph;
+            bool need = row_phase(P, G, S, s, wk, ph);
+            if (wa) {
+                ph = need ? cmul(ph, phase_of(P, 0, -1)) : phase_of(P, 0, -1);
+                need = true;
+            }
+            if (need) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[rr][c] = cmul(out[rr][c], ph);
+            }
+        }
+    }
+
+    // t = C_PH e for phase PH: the normal 3x3 block and the shear diagonal only when the phase is
+    // orthotropic in the lattice axes (a grid-uniform flag), else all 36 entries.
+    template <int PH>
+    static PC_HD void stiff_phase(const StencilParams<float>& P, const C e[6], C t[6]) {
+        if (P.ortho[PH]) {
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                float re = 0.f, im = 0.f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    re = fmaf(P.C[PH][p * 6 + q], e[q].x, re);
+                    im = fmaf(P.C[PH][p * 6 + q], e[q].y, im);
+                }
+                t[p] = make_float2(re, im);
+            }
+#pragma unroll
+            for (int p = 3; p < 6; ++p) t[p] = make_float2(P.C[PH][p * 7] * e[p].x, P.C[PH][p * 7] * e[p].y);
+        } else {
+#pragma unroll
+            for (int p = 0; p < 6; ++p) {
+                float re = 0.f, im = 0.f;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    re = fmaf(P.C[PH][p * 6 + q], e[q].x, re);
+                    im = fmaf(P.C[PH][p * 6 + q], e[q].y, im);
+                }
+                t[p] = make_float2(re, im);
+            }
+        }
+    }
+
+    // Fluxes of one node from its four neighbours n[l][c] (l = 0..3: (s2, s3) = (+,+), (+,-), (-,+),
+    // (-,-)), its own value xo and material m; F[l][c] and the local term loc = sum_l F_l = 4 P_0.
+    static PC_HD void flux_node(const StencilParams<float>& P, float m, const C n0[3], const C n1[3],
+                                const C n2[3], const C n3[3], const C xo[3], C F[4][3], C loc[3]) {
+        C H[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const C u = cadd(n0[a], n1[a]), v = cadd(n2[a], n3[a]);
+            const C w = csub(n0[a], n1[a]), z = csub(n2[a], n3[a]);
+            H[0][a] = cfma(-4.f, xo[a], cadd(u, v));  // sum_l (n_l - xo)
+            H[1][a] = csub(u, v);
+            H[2][a] = cadd(w, z);
+        }
+        C Gm[3][3];
+        if (CUBIC) {
+#pragma unroll
+            for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) Gm[mm][a] = H[mm][a];
+        } else {
+#pragma unroll
+            for (int mm = 0; mm < 3; ++mm)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    C acc = cscale(P.Mmix[0 * 3 + mm], H[0][a]);
+                    acc = cfma(P.Mmix[1 * 3 + mm], H[1][a], acc);
+                    Gm[mm][a] = cfma(P.Mmix[2 * 3 + mm], H[2][a], acc);
+                }
+        }
+        C e[6];
+        e[0] = Gm[0][0];
+        e[1] = Gm[1][1];
+        e[2] = Gm[2][2];
+        e[3] = cadd(Gm[2][1], Gm[1][2]);
+        e[4] = cadd(Gm[2][0], Gm[0][2]);
+        e[5] = cadd(Gm[1][0], Gm[0][1]);
+        C t[6];
+        if (MATK == 0) {
+            // phase-id material: the stiffness entries of each phase are kernel-parameter constants
+            // (constant-bank operands of scalar FMAs); a warp whose nodes span both phases runs both
+            // branches
+            if (m != 0.f) stiff_phase<1>(P, e, t);
+            else stiff_phase<0>(P, e, t);
+        } else {
+#pragma unroll
+            for (int p = 0; p < 6; ++p) {
+                C acc = czero(0.f);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const float c0 = P.C[0][p * 6 + q], c1 = P.C[1][p * 6 + q];
+                    acc = cfma(c0 + m * (c1 - c0), e[q], acc);
+                }
+                t[p] = acc;
+            }
+        }
+        // stress tensor S[a][m] (symmetric) and P[s][a] = sum_m Mmix[s][m] S[a][m]
+        const C Sx[3][3] = {{t[0], t[5], t[4]}, {t[5], t[1], t[3]}, {t[4], t[3], t[2]}};
+        C Pm[3][3];
+        if (CUBIC) {
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) Pm[s][a] = Sx[a][s];
+        } else {
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    C acc = cscale(P.Mmix[s * 3 + 0], Sx[a][0]);
+                    acc = cfma(P.Mmix[s * 3 + 1], Sx[a][1], acc);
+                    Pm[s][a] = cfma(P.Mmix[s * 3 + 2], Sx[a][2], acc);
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const C u = cadd(Pm[0][a], Pm[1][a]), v = csub(Pm[0][a], Pm[1][a]);
+            F[0][a] = cadd(u, Pm[2][a]);
+            F[1][a] = csub(u, Pm[2][a]);
+            F[2][a] = cadd(v, Pm[2][a]);
+            F[3][a] = csub(v, Pm[2][a]);
+            loc[a] = cscale(4.f, Pm[0][a]);
+        }
+    }
+
+    // Step kf, first half: fluxes of flux rows 2t, 2t+1 of plane kf into flux buffer `buf`, the local
+    // terms into the accumulators of plane kf's outputs, and the new neighbour set (plane kf + 1)
+    // into S[JP].  JP = parity of the step within the segment (step j <-> kf = ks - 1 + j): S[JP]
+    // holds plane kf - 1 on entry, acc[JP] the outputs of plane kf.  Lanes past the last thread row
+    // compute on the last row's data and store nothing.
+    template <int JP>
+    static PC_HD void flux_step(const StencilParams<float>& P, const PipeGeom& G, const PipeSeg& S, const Sh& sh,
+                                Regs& r, int kf, int slot_0, int slot_p, int buf) {
+        const int X = Xw(G), SR = SRw(G), FR = FRw(G);
+        const bool active = r.t < Tw(G);
+        const int t = active ? r.t : Tw(G) - 1;
+        const int i0 = (kf + S.p13) & 1, j0 = (kf + S.p12 + S.p13) & 1;
+        C Pn[3][3];
+        load_set(P, G, S, sh, r.a, t, slot_p, kf + 1, i0, Pn);
+        // own values: flux rows f = 2t + n sit on slot rows f + 1 - j0 of plane kf
+        const int wk = plane_wrap(G, kf);
+        const C* x0 = sh.xslot(slot_0);
+        C xo[2][3];
+        float mo[2];
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+            const int s = 2 * t + n + 1 - j0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int idx = (c * SR + s) * X + r.a;
+                PC_IDX(idx, 3 * G.SR * G.X);
+                xo[n][c] = x0[idx];
+            }
+            C ph;
+            if ((wk != 0 || S.top || S.bot) && row_phase(P, G, S, s, wk, ph)) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) xo[n][c] = cmul(xo[n][c], ph);
+            }
+            mo[n] = mat_at(sh, G, slot_0, s, r.a);
+        }
+        C F[2][4][3], loc[2][3];
+        const C(&M)[3][3] = r.S[JP];
+        flux_node(P, mo[0], M[0], Pn[0], M[1], Pn[1], xo[0], F[0], loc[0]);
+        flux_node(P, mo[1], M[1], Pn[1], M[2], Pn[2], xo[1], F[1], loc[1]);
+        if (!active) return;
+        float4* fa4 = sh.fA(buf);
+        float2* fb2 = sh.fB(buf);
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+            const int f = 2 * t + n;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const int idx = (l * FR + f) * X + r.a;
+                PC_IDX(idx, 4 * 2 * G.T * G.X);
+                fa4[idx] = make_float4(F[n][l][0].x, F[n][l][0].y, F[n][l][1].x, F[n][l][1].y);
+                fb2[idx] = F[n][l][2];
+            }
+        }
+        // outputs of plane kf owned by this thread: rows o = 2t + n - j0, whose local terms are F[n]
+        // and whose x and material are the flux nodes' own (never a wrapped value: o < Vt, kf in [0, Z))
+        if (kf >= S.ks && kf < S.ke) {
+#pragma unroll
+            for (int n = 0; n < 2; ++n) {
+                const int o = 2 * t + n - j0;
+                if (o >= 0 && o < S.Vt) {
+                    const float rho = (MATK == 0) ? (mo[n] != 0.f ? P.rho[1] : P.rho[0])
+                                                  : P.rho[0] + mo[n] * (P.rho[1] - P.rho[0]);
+                    const float sr = -S.shift * rho;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        r.acc[JP][n][c] = cfma(sr, xo[n][c], csub(r.acc[JP][n][c], loc[n][c]));
+                }
+            }
+        }
+#pragma unroll
+        for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r.S[JP][rr][c] = Pn[rr][c];
+    }
+
+    // Prologue of a segment: the neighbour sets of planes ks - 2 (for step ks - 1) and ks - 1 (for
+    // step ks), into S[0] and S[1].
+    static PC_HD void prologue(const StencilParams<float>& P, const PipeGeom& G, const PipeSeg& S, const Sh& sh,
+                               Regs& r, int slot_a, int slot_b) {
+        const int t = r.t < Tw(G) ? r.t : Tw(G) - 1;
+        load_set(P, G, S, sh, r.a, t, slot_a, S.ks - 2, (S.ks - 1 + S.p13) & 1, r.S[0]);
+        load_set(P, G, S, sh, r.a, t, slot_b, S.ks - 1, (S.ks + S.p13) & 1, r.S[1]);
+    }
+
+    // Step kf, second half (after the barrier): finish the outputs of plane kf - 1 with the s3 = +1
+    // fluxes of plane kf (their local and shift terms are in already; for the inner product x is
+    // re-read from plane kf - 1's slot), and start those of plane kf + 1 with the s3 = -1 fluxes of
+    // plane kf.
+    template <int JP>
+    static PC_HD void gather_step(const StencilParams<float>& P, const PipeGeom& G, const PipeSeg& S, const Sh& sh,
+                                  Regs& r, int kf, int slot_m, int buf, bool want_dot) {
+        if (r.t >= Tw(G)) return;
+        const int X = Xw(G), SR = SRw(G), FR = FRw(G);
+        const int p = kf - 1;  // planes kf - 1 and kf + 1 have the same parity
+        const int i0 = (p + S.p13) & 1, j0 = (p + S.p12 + S.p13) & 1;
+        int ca = r.a + i0;
+        const bool wa = ca >= X;
+        if (wa) ca -= X;
+        const C pha = phase_of(P, 0, 1);
+        const float4* fa4 = sh.fA(buf);
+        const float2* fb2 = sh.fB(buf);
+        const bool fin = p >= S.ks && p < S.ke, start = kf + 1 >= S.ks && kf + 1 < S.ke;
+        const int64_t plane = (int64_t)X * Yw(G), vstr = plane * Zw(G);
+        constexpr int pq = JP ^ 1;  // outputs of planes kf -+ 1
+        // sum of flux l1 on flux row f1 and flux l2 on flux row f2 (column ca), Bloch-phased on a wrap
+        auto pair = [&](int l1, int f1, int l2, int f2, C out[3]) {
+            const int i1 = (l1 * FR + f1) * X + ca, i2 = (l2 * FR + f2) * X + ca;
+            PC_IDX(i1, 4 * 2 * G.T * G.X);
+            PC_IDX(i2, 4 * 2 * G.T * G.X);
+            const float4 u = fa4[i1], v = fa4[i2];
+            out[0] = cadd(make_float2(u.x, u.y), make_float2(v.x, v.y));
+            out[1] = cadd(make_float2(u.z, u.w), make_float2(v.z, v.w));
+            out[2] = cadd(fb2[i1], fb2[i2]);
+            if (wa) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) out[c] = cmul(out[c], pha);
+            }
+        };
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+            const int o = 2 * r.t + n - j0;
+            const bool valid = o >= 0 && o < S.Vt;
+            const int fa = o + 1, fb = o;  // flux rows of the F_0/F_1 and F_2/F_3 neighbours
+            if (valid && fin) {
+                C f[3];
+                pair(0, fa, 2, fb, f);
+                const C* xm = sh.xslot(slot_m);
+                float2* yo = S.y + (int64_t)p * plane + (int64_t)(S.b0 + o) * X + r.a;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const C v = cadd(r.acc[pq][n][c], f[c]);
+                    PC_IDX((yo - S.y) + c * vstr, 3 * (int64_t)G.X * G.Y * G.Z);
+                    yo[c * vstr] = v;
+                    if (want_dot) {  // x of the output node: slot row o + 1 of plane p, never wrapped
+                        const int ix = (c * SR + o + 1) * X + r.a;
+                        PC_IDX(ix, 3 * G.SR * G.X);
+                        r.dot = cdotre(xm[ix], v, r.dot);
+                    }
+                }
+            }
+            if (valid && start) {
+                pair(1, fa, 3, fb, r.acc[pq][n]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) r.acc[pq][n][c] = czero(0.f);
+            }
+        }
+    }
+
+    // Host model of the copies of plane kp into `slot` (same source rows and wraps as the kernel's
+    // bulk copies): slot row s holds grid row b0 - 1 + s (wrapped), of plane kp mod Z.
+    static void host_copy_plane(const PipeGeom& G, const PipeSeg& S, const Sh& sh, int slot, int kp) {
+        const int kw = ((kp % G.Z) + G.Z) % G.Z;
+        C* xs = sh.xslot_w(slot);
+        unsigned char* ms = sh.mslot_w(slot);
+        for (int s = 0; s < S.Vt + 2; ++s) {
+            const int b = ((S.b0 - 1 + s) % G.Y + G.Y) % G.Y;
+            for (int c = 0; c < 3; ++c)
+                for (int a = 0; a < G.X; ++a) {
+                    PC_IDX((c * G.SR + s) * G.X + a, 3 * G.SR * G.X);
+                    xs[(c * G.SR + s) * G.X + a] = S.x[(int64_t)c * G.X * G.Y * G.Z + ((int64_t)kw * G.Y + b) * G.X + a];
+                }
+            std::memcpy(ms + (size_t)s * G.Xp * G.matsz,
+                        static_cast<const unsigned char*>(S.mat) + ((size_t)kw * G.Y + b) * G.Xp * G.matsz,
+                        (size_t)G.Xp * G.matsz);
+        }
+    }
+};
+
+}  // namespace pc

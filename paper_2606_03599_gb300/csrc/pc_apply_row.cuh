@@ -104,7 +104,8 @@ struct RowBatch {
     ApplyItem it[kRowMaxItems];
     const void* mat_row[kRowMaxItems];  // row-padded material of each item's block
     int n;
-    int* err;
+    int* err;             // device error word (set to 1 when a bounded wait expires)
+    uint32_t wait_limit;  // mbarrier polls before a CTA gives up
 };
 
 // One (item, tile) piece of a CTA's plane range.

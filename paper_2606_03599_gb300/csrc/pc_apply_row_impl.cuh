@@ -28,7 +28,6 @@ __global__ void __launch_bounds__(kRowMaxThreads, 1)
     typename T::Sh sh{base, &G};
     const int tid = threadIdx.x;
     const uint32_t NS = (uint32_t)G.ns;
-    constexpr uint32_t kWaitLimit = 1u << 26;
     uint64_t* bars = sh.bar();
     if (tid == 0) {
         for (uint32_t s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
@@ -124,14 +123,15 @@ __global__ void __launch_bounds__(kRowMaxThreads, 1)
                 bulk_load(ms + (int64_t)sb * mrow, mat + (int64_t)kw * G.Y * mrow, mrow, bar);
             }
         };
-        auto wait = [&](int kp) -> bool {
+        auto wait_n = [&](int kp, uint32_t limit) -> bool {
             const uint32_t q = gseq + (uint32_t)(kp - kfirst);
             uint64_t* bar = &bars[q & (NS - 1)];
             const uint32_t parity = (q >> G.ns_log2) & 1u;
-            for (uint32_t n = 0; n < kWaitLimit; ++n)
+            for (uint32_t n = 0; n < limit; ++n)
                 if (mbar_try_wait(bar, parity)) return true;
             return false;
         };
+        auto wait = [&](int kp) -> bool { return wait_n(kp, B.wait_limit); };
         auto slot_of = [&](int kp) { return (int)((gseq + (uint32_t)(kp - kfirst)) & (NS - 1)); };
 
         if (tid == 0) {
@@ -161,8 +161,14 @@ __global__ void __launch_bounds__(kRowMaxThreads, 1)
             if (*sh.abort_flag()) {
                 if (tid == 0) {
                     atomicExch(B.err, 1);
+                    // the inner products of this launch are void: NaN in every partial slot of this CTA
+                    if (dot_partials != nullptr)
+                        for (int i = 0; i < B.n; ++i)
+                            if (B.it[i].dot_slot >= 0)
+                                dot_partials[(int64_t)B.it[i].dot_slot * dot_stride + blockIdx.x] = __longlong_as_double(
+                                    0x7ff8000000000000LL);
                     // let the copies still in flight land before the CTA's shared memory is released
-                    for (int kp = max(kfirst, kf - 1); kp <= last_issued; ++kp) wait(kp);
+                    for (int kp = max(kfirst, kf - 1); kp <= last_issued; ++kp) wait_n(kp, kDrainLimit);
                 }
                 return;
             }
@@ -204,6 +210,7 @@ static int launch_row_t(const StencilParams<float>& P, const ApplyItem* items, c
         RowBatch B;
         B.n = nitems - base < kRowMaxItems ? nitems - base : kRowMaxItems;
         B.err = err;
+        B.wait_limit = wait_limit();
         for (int i = 0; i < B.n; ++i) {
             B.it[i] = items[base + i];
             B.mat_row[i] = mats[base + i];

@@ -38,7 +38,8 @@ struct TmaBatch {
     CUtensorMap map[kTmaMaxItems];  // one tensor map per item's x vector
     ApplyItem it[kTmaMaxItems];
     int n;
-    int* err;  // device error word (nonzero after a timed-out wait)
+    int* err;             // device error word (nonzero after a timed-out wait)
+    uint32_t wait_limit;  // mbarrier polls before a CTA gives up
 };
 
 // Stiffness entries as packed-FMA operands: (c, c) pairs for complex64, plain doubles for complex128.
@@ -103,7 +104,6 @@ struct TmaTile {
     static constexpr int SLOT_ELEMS = 3 * XR;
     static constexpr int SLOT_BYTES = ((SLOT_ELEMS * (int)sizeof(C) + 127) / 128) * 128;
     static constexpr int NFIX = (3 * XR + NT - 1) / NT;  // box cells per thread (wrap fix-ups)
-    static constexpr uint32_t kWaitLimit = 1u << 26;     // try_wait polls before a CTA gives up
 
     struct Shared {
         alignas(128) unsigned char xs[NSLOT][SLOT_BYTES];

@@ -53,14 +53,15 @@ __global__ void __launch_bounds__(TmaTile<R, FULL, CUBIC, MATK, TX, TY>::NT, 2)
         mbar_expect_tx(bar, kBytes);
         tma_load_4d(sh.xs[j % T::NSLOT], map, bar, (c.a0 - 2) * kUnits, c.b0 - 2, kw, 0);
     };
-    auto wait = [&](int kp) -> bool {
+    auto wait_n = [&](int kp, uint32_t limit) -> bool {
         const int j = kp - kfirst;
         uint64_t* bar = &sh.mbar[j % T::NSLOT];
         const uint32_t parity = (uint32_t)((j / T::NSLOT) & 1);
-        for (uint32_t n = 0; n < T::kWaitLimit; ++n)
+        for (uint32_t n = 0; n < limit; ++n)
             if (mbar_try_wait(bar, parity)) return true;
         return false;
     };
+    auto wait = [&](int kp) -> bool { return wait_n(kp, B.wait_limit); };
 
     typename T::Regs r;
     if (tid == 0) {
@@ -101,8 +102,12 @@ __global__ void __launch_bounds__(TmaTile<R, FULL, CUBIC, MATK, TX, TY>::NT, 2)
         if (sh.abort) {
             if (tid == 0) {
                 atomicExch(B.err, 1);
+                // this CTA's inner-product partial is void
+                if (dot_partials != nullptr && it.dot_slot >= 0)
+                    dot_partials[(int64_t)it.dot_slot * dot_stride + blockIdx.x + gridDim.x * blockIdx.y] =
+                        __longlong_as_double(0x7ff8000000000000LL);
                 // let the copies still in flight land before the CTA's shared memory is released
-                for (int kp = p; kp <= last_issued; ++kp) wait(kp);
+                for (int kp = p; kp <= last_issued; ++kp) wait_n(kp, kDrainLimit);
             }
             return;
         }
@@ -209,6 +214,7 @@ static int launch_tma_tile(const StencilParams<R>& P, const ApplyItem* items, in
         TmaBatch B;
         B.n = nitems - base < kTmaMaxItems ? nitems - base : kTmaMaxItems;
         B.err = err;
+        B.wait_limit = wait_limit();
         for (int i = 0; i < B.n; ++i) {
             B.it[i] = items[base + i];
             PC_TRY(tma_map(&B.map[i], items[base + i].x, P.X, P.Y, P.Z, (int)sizeof(typename CT<R>::T), T::XW,

@@ -928,6 +928,7 @@ int pc_shift_invert_pcg(pc_grid* g, int block, int dtype, double sigma, const vo
     PcgResult r;
     int rc = pcg_solve(g, dtype, 1, &block, sigma, rhs, x, tol, maxit, &r, (cudaStream_t)stream);
     if (rc != PC_OK) return rc;
+    PC_TRY(grid_device_status(g, (cudaStream_t)stream));
     if (info) {
         info->iters = r.iters;
         info->status = r.status;
@@ -952,7 +953,9 @@ int pc_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_o
     if (!std::isnan(sigma) && !std::isfinite(sigma)) return fail(PC_EINVAL, "pc_eigs: bad sigma");
     const int64_t dim = o->full_space ? 3 * g->n : 3 * g->nb;
     if (nev > dim / 8) return fail(PC_EINVAL, "pc_eigs: nev too large for this grid");
-    return run_eigs(g, kappa, nev, sigma, o, evals, evecs, block_of, info);
+    const int rc = run_eigs(g, kappa, nev, sigma, o, evals, evecs, block_of, info);
+    const int st = grid_device_status(g, (cudaStream_t)o->stream);
+    return st != PC_OK ? st : rc;
 }
 
 }  // extern "C"

@@ -70,6 +70,12 @@ int launch_apply_tma_f32(bool full, bool cubic, int matkind, int shape, const St
 int launch_apply_row_f32(bool cubic, int matkind, const StencilParams<float>& P, const ApplyItem* items,
                          const void* const* mats, int nitems, int ctas, double* dp, int ds, int* err, cudaStream_t s);
 int row_apply_ctas(int X, int Y, int Z, int matkind, int nitems, int minseg = 12);
+// Plane-pipelined kernel (complex64 parity blocks, even X): producer warp + consumer warps.
+int launch_apply_pipe_f32(bool cubic, int matkind, const StencilParams<float>& P, const ApplyItem* items,
+                          const void* const* mats, int nitems, int ctas, double* dp, int ds, int* err,
+                          cudaStream_t s);
+int pipe_apply_ctas(int X, int Y, int Z, int matkind, int nitems, int minseg = 12);
+bool pipe_geom_ok(int X, int Y, int Z, int matkind);
 bool row_geom_fits(int X, int Y, int Z, int matkind);
 int device_sm_count();
 int launch_apply_tma_f64(bool full, bool cubic, int matkind, int shape, const StencilParams<double>& P,
@@ -89,7 +95,12 @@ struct ApplyConfig {
     bool tma = false;  // TMA-staged kernel (quarter grids of even width >= 8)
     bool row = false;  // row-tile kernel (complex64 parity blocks, X even)
     bool split = false;  // two-pass complex128 kernels (flux, then gather)
+    bool pipe = false;   // plane-pipelined kernel (complex64 parity blocks, even X)
 };
+// Kind code of a configuration as pc_tuned_config reports it.
+inline int config_kind(const ApplyConfig& c) {
+    return c.pipe ? 4 : (c.split ? 3 : (c.row ? 2 : (c.tma ? 1 : 0)));
+}
 // scratch_ok = false: only kernels that need no scratch memory of their own (no two-pass apply).
 ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool blocks = false, int matkind = 0,
                                 bool scratch_ok = true);
@@ -131,6 +142,16 @@ inline void make_stencil_params(StencilParams<R>& P, const double Chat[2][36], c
     P.Y = Y;
     P.Z = Z;
 }
+
+// Bounded device waits.  Every spin-wait of a kernel (an mbarrier poll on its own copies) gives
+// up after wait_limit() polls, records 1 in the grid's device error word and returns; the copies
+// it still has in flight are then awaited with kDrainLimit polls so that no copy lands in shared
+// memory the CTA has released.  PC_WAIT_LIMIT (read once) overrides the default 2^26 polls.
+constexpr uint32_t kDrainLimit = 1u << 26;
+uint32_t wait_limit();
+// Reads and clears the grid's device error word after the work queued on s (synchronises s):
+// PC_OK, or PC_ECUDA with a message when a bounded device wait expired.
+int grid_device_status(pc_grid* g, cudaStream_t s);
 
 // Launch accounting (pc_stats): every kernel launch of the library calls note_launch.
 void note_launch(int n = 1);

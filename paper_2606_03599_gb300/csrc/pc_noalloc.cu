@@ -29,8 +29,9 @@ constexpr int64_t kNoAllocMaxNodes = int64_t(1) << 24;
 
 static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
 
-// Fixed-order sum of the partials (one CTA) into *out.
-__global__ void noalloc_reduce(int n, double* __restrict__ out) {
+// Fixed-order sum of the partials (one CTA) into *out; NaN when a bounded copy wait of the
+// apply expired (the grid's error word is set), so that the caller sees the failure in *dot.
+__global__ void noalloc_reduce(int n, const int* __restrict__ err, double* __restrict__ out) {
     __shared__ double red[32];
     double v = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) v += g_noalloc_partials[i];
@@ -40,7 +41,7 @@ __global__ void noalloc_reduce(int n, double* __restrict__ out) {
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        *out = s;
+        *out = (err != nullptr && *err != 0) ? __longlong_as_double(0x7ff8000000000000LL) : s;
     }
 }
 
@@ -79,8 +80,25 @@ extern "C" int pc_block_apply_dot_noalloc(pc_grid* g, int block, int dtype, cons
     if (nodes > kNoAllocMaxNodes)
         return fail(PC_EINVAL, "pc_block_apply_dot_noalloc: " + std::to_string(nodes) +
                                    " nodes exceed the static-scratch limit of " + std::to_string(kNoAllocMaxNodes));
-    const ApplyConfig cfg = choose_apply_config(full ? g->N : g->X, full ? g->N : g->Y, g->Z, 1, dtype, false, 0,
-                                                false /* no kernel that needs scratch of its own */);
+    {
+        const size_t vbytes = (size_t)3 * nodes * (dtype == PC_C64 ? 8 : 16);
+        const char* xb = static_cast<const char*>(x);
+        const char* yb = static_cast<const char*>(y);
+        if (xb < yb + vbytes && yb < xb + vbytes)
+            return fail(PC_EINVAL, "pc_block_apply_dot_noalloc: x and y overlap");
+    }
+    const int X = full ? g->N : g->X, Y = full ? g->N : g->Y;
+    ApplyConfig cfg = choose_apply_config(X, Y, g->Z, 1, dtype, false, 0,
+                                          false /* no kernel that needs scratch of its own */);
+    if (cfg.ctas > kNoAllocPartials) {
+        // widest register-staged tiles with every plane of a column in one CTA: at most
+        // ceil(X/32) ceil(Y/8) (complex64) or ceil(X/16) ceil(Y/8) (complex128) CTAs, which for
+        // 2^24 nodes stays far below the partial-sum capacity
+        cfg = ApplyConfig();
+        cfg.shape = dtype == PC_C128 ? 1 : 0;
+        cfg.tz = g->Z;
+        cfg.ctas = ((X + tile_tx(cfg.shape) - 1) / tile_tx(cfg.shape)) * ((Y + tile_ty(cfg.shape) - 1) / tile_ty(cfg.shape));
+    }
     if (cfg.ctas > kNoAllocPartials)
         return fail(PC_EINVAL, "pc_block_apply_dot_noalloc: launch needs " + std::to_string(cfg.ctas) +
                                    " partial sums, static scratch holds " + std::to_string(kNoAllocPartials));
@@ -96,7 +114,7 @@ extern "C" int pc_block_apply_dot_noalloc(pc_grid* g, int block, int dtype, cons
     it.skip = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
     PC_TRY(grid_apply(g, dtype, full, &it, 1, scratch, cfg.ctas, s, &cfg));
-    noalloc_reduce<<<1, 256, 0, s>>>(cfg.ctas, dot);
+    noalloc_reduce<<<1, 256, 0, s>>>(cfg.ctas, g->d_err, dot);
     note_launch();
     PC_CUDA_TRY(cudaGetLastError());
     return PC_OK;

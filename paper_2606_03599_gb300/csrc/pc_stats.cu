@@ -132,11 +132,71 @@ static void drain() {
     g_pending.clear();
 }
 
+// FP64 FMA throughput: every thread runs 8 independent chains a = fma(a, m, c) (m just below 1, so
+// the values stay bounded); the 8-way ILP and 32 warps per SM keep the FP64 pipe saturated.  The
+// sum is stored only under a condition that never holds, which keeps every chain live.
+__global__ void fp64_fma_rate_kernel(int iters, double seed, double* sink) {
+    double a[8];
+    const double m = 1.0 - 1e-9 * (double)(1 + (threadIdx.x & 7));
+    const double c = 1e-12 * seed;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = seed + (double)j + 1e-3 * (double)threadIdx.x;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fma(a[j], m, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t += a[j];
+    if (t == -1.0) *sink = t;
+}
+
 }  // namespace pc
 
 using namespace pc;
 
 extern "C" {
+
+int pc_fp64_peak(double seconds, double* tflops, double* fma_per_s) {
+    if (!tflops || !(seconds > 0) || seconds > 60) return fail(PC_EINVAL, "pc_fp64_peak: bad argument");
+    const int sms = device_sm_count();
+    const int threads = 512, blocks = 2 * sms;
+    double* sink = nullptr;
+    PC_CUDA_TRY(cudaMalloc(&sink, sizeof(double)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int iters = 256;
+    double best = 0.0;
+    int rc = PC_OK;
+    for (int round = 0; round < 12 && rc == PC_OK; ++round) {
+        cudaEventRecord(e0, 0);
+        fp64_fma_rate_kernel<<<blocks, threads, 0, 0>>>(iters, 1.0 + round, sink);
+        note_launch();
+        cudaEventRecord(e1, 0);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "fp64_fma_rate_kernel");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double fmas = (double)blocks * threads * 8.0 * iters;
+        if (ms > 0.f && round >= 2) best = std::fmax(best, fmas / (ms * 1e-3));
+        // grow the launch until it runs for about `seconds` / 4 (the last rounds are the measurement)
+        if (ms > 0.f && ms * 1e-3 < seconds / 4) {
+            const double f = std::fmin(16.0, (seconds / 4) / (ms * 1e-3));
+            iters = (int)std::fmin(1e9, iters * f);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (rc != PC_OK) return rc;
+    *tflops = 2.0 * best / 1e12;
+    if (fma_per_s) *fma_per_s = best;
+    return PC_OK;
+}
 
 int pc_stats_timing(int enable) {
     g_timing.store(enable ? 1 : 0);

@@ -2,7 +2,8 @@
 // or full space, material kind, lattice) and one batch size, time every applicable kernel and
 // launch shape on the GPU and keep the fastest.
 //
-// Candidates: the row-tile kernel (complex64 blocks) with several persistent CTA counts, the
+// Candidates: the plane-pipelined and row-tile kernels (complex64 blocks) with several persistent
+// CTA counts, the
 // TMA tile kernel (16-wide and 8-wide tiles) and the register-staged kernel (four tile shapes),
 // each with k-chunkings that target one, two or four resident CTAs per SM.  Results live in a
 // process-wide table keyed by (X, Y, Z, dtype, layout, material kind, lattice, batch-size
@@ -66,7 +67,7 @@ void load_locked() {
         if (std::sscanf(line.c_str() + q1 + 1, " : {\"kind\": %d, \"shape\": %d, \"tz\": %d, \"ctas\": %d", &kind, &shape,
                         &tz, &ctas) != 4)
             continue;
-        if (kind < 0 || kind > 3 || ctas < 1) continue;
+        if (kind < 0 || kind > 4 || ctas < 1) continue;
         ApplyConfig c;
         c.shape = shape;
         c.tz = tz;
@@ -74,6 +75,7 @@ void load_locked() {
         c.tma = kind == 1;
         c.row = kind == 2;
         c.split = kind == 3;
+        c.pipe = kind == 4;
         g_tuned[key] = c;
     }
 }
@@ -83,7 +85,7 @@ void append_locked(const std::string& key, const ApplyConfig& c, double us) {
     if (!path) return;
     std::ofstream f(path, std::ios::app);
     if (!f) return;
-    f << "\"" << key << "\": {\"kind\": " << (c.split ? 3 : (c.row ? 2 : (c.tma ? 1 : 0))) << ", \"shape\": " << c.shape
+    f << "\"" << key << "\": {\"kind\": " << config_kind(c) << ", \"shape\": " << c.shape
       << ", \"tz\": " << c.tz << ", \"ctas\": " << c.ctas << ", \"us\": " << us << "}\n";
 }
 
@@ -98,6 +100,8 @@ bool tuned_config(int X, int Y, int Z, int dtype, bool full, int matkind, bool c
     // a tuned chunking for a bucket is reused for every batch size in it: recount the CTAs
     if (out->split) {
         out->ctas = split_apply_ctas((int64_t)X * Y * Z);
+    } else if (out->pipe) {
+        out->ctas = pipe_apply_ctas(X, Y, Z, matkind, nitems, out->tz);
     } else if (out->row) {
         out->ctas = row_apply_ctas(X, Y, Z, matkind, nitems, out->tz);
     } else {
@@ -159,9 +163,21 @@ static std::vector<ApplyConfig> candidates(int X, int Y, int Z, int dtype, bool 
         base.tz = (int)((Z + nch - 1) / nch);
         base.ctas = tiles * ((Z + base.tz - 1) / base.tz);
         for (auto& o : out)
-            if (o.row == base.row && o.tma == base.tma && o.shape == base.shape && o.tz == base.tz) return;
+            if (!o.pipe && o.row == base.row && o.tma == base.tma && o.shape == base.shape && o.tz == base.tz) return;
         out.push_back(base);
     };
+    if (!full && dtype == PC_C64 && pipe_geom_ok(X, Y, Z, matkind)) {
+        for (int minseg : {4, 8, 12, 24, 48}) {
+            ApplyConfig c;
+            c.pipe = true;
+            c.shape = 0;
+            c.tz = minseg;
+            c.ctas = pipe_apply_ctas(X, Y, Z, matkind, nitems, minseg);
+            bool dup = false;
+            for (auto& o : out) dup = dup || (o.pipe && o.ctas == c.ctas);
+            if (!dup) out.push_back(c);
+        }
+    }
     if (!full && dtype == PC_C64 && X % 2 == 0 && row_geom_fits(X, Y, Z, matkind)) {
         for (int minseg : {4, 8, 12, 24, 48}) {
             ApplyConfig c;
@@ -239,7 +255,8 @@ int autotune_layout(pc_grid* g, int dtype, bool full, int nitems, cudaStream_t s
         if (rc != PC_OK) break;
         if (verbose)
             std::fprintf(stderr, "[pcband tune] %s kind=%s shape=%d tz=%d ctas=%d: %.1f us\n", key.c_str(),
-                         c.split ? "split" : (c.row ? "row" : (c.tma ? "tma" : "regs")), c.shape, c.tz, c.ctas, us);
+                         c.pipe ? "pipe" : (c.split ? "split" : (c.row ? "row" : (c.tma ? "tma" : "regs"))), c.shape,
+                         c.tz, c.ctas, us);
         if (us < best_us) {
             best_us = us;
             best = c;
@@ -281,7 +298,7 @@ extern "C" int pc_tuned_config(const pc_grid* g, int dtype, int layout, int nite
     if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_tuned_config: bad dtype");
     if (layout != 0 && layout != 1) return fail(PC_EINVAL, "pc_tuned_config: layout must be 0 or 1");
     const ApplyConfig c = apply_config_for(g, layout == 1, nitems < 1 ? 1 : nitems, dtype);
-    *kind = c.split ? 3 : (c.row ? 2 : (c.tma ? 1 : 0));
+    *kind = config_kind(c);
     *shape = c.shape;
     *tz = c.tz;
     *ctas = c.ctas;

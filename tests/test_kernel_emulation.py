@@ -70,6 +70,14 @@ CASES = [
     (16, 0, 1, 20, 2), (20, 2, 1, 20, 9), (48, 1, 1, 20, 13), (56, 3, 1, 20, 40), (68, 0, 1, 20, 17),
     # row-tile kernel with compile-time widths (code 21): X = 16, 24, 32 (N = 32, 48, 64)
     (32, 2, 1, 21, 5), (48, 0, 1, 21, 152), (64, 3, 1, 21, 31),
+    # plane-pipelined kernel (code 40, complex64 blocks; tz = persistent CTAs): one tile with both
+    # row wraps, several tiles, ragged tile heights, CTA ranges that split tiles, more CTAs than
+    # planes; code 41: compile-time widths X = 16, 24, 32; codes 51-53: 1, 2, 3 thread rows (tiles
+    # of 1, 3, 5 rows, so that most tiles touch a wrap or a neighbour tile)
+    (4, 0, 1, 40, 1), (4, 3, 1, 40, 5), (8, 1, 1, 40, 3), (8, 2, 1, 40, 64), (12, 3, 1, 40, 7),
+    (16, 0, 1, 40, 2), (20, 2, 1, 40, 9), (48, 1, 1, 40, 13), (56, 3, 1, 40, 40), (68, 0, 1, 40, 17),
+    (32, 2, 1, 41, 5), (48, 0, 1, 41, 152), (64, 3, 1, 41, 31),
+    (4, 1, 1, 51, 3), (12, 2, 1, 51, 5), (20, 2, 1, 52, 9), (24, 1, 1, 51, 11), (28, 3, 1, 53, 6),
     # two-pass complex128 kernels (code 30): every block, the full grid, the smallest grids
     (4, 0, 2, 30, 0), (4, 3, 2, 30, 0), (4, -1, 2, 30, 0), (8, 1, 2, 30, 0), (8, 2, 2, 30, 0),
     (8, -1, 2, 30, 0), (12, 3, 2, 30, 0), (16, 0, 2, 30, 0),
@@ -107,8 +115,9 @@ def test_emulated_kernel_general_lattice_and_fractions(emu, block):
     x = complex_gaussian((3, m), 9)
     ref = (O.apply_block(pb, kappa, block, x, shift=0.5) if block >= 0
            else O.apply_full(pb, kappa, x, shift=0.5))
-    for dtype, shape, tz in ((2, 2, 3), (1, 3, 4), (2, 11, 5), (1, 10, 3), (1, 20, 3), (2, 30, 0)):
-        if shape == 20 and block < 0:
+    for dtype, shape, tz in ((2, 2, 3), (1, 3, 4), (2, 11, 5), (1, 10, 3), (1, 20, 3), (1, 40, 3), (1, 52, 5),
+                             (2, 30, 0)):
+        if shape in (20, 40, 52) and block < 0:
             continue
         y = run_emu(emu, pb, block, dtype, shape, tz, kappa, x, 0.5, 1)
         err = np.linalg.norm(y - ref) / np.linalg.norm(ref)

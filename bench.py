@@ -38,6 +38,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "block B C B^H apply GDoF/s & HBM frac; sec per k-point for 20 bands @1e-8 resid"
+# block applies per k-point of the FP64 band workload, as the GPU arm measures them on GB300
+# (solver.block_applies_per_kpoint); the reference arm scales its per-apply time by it
+APPLIES_PER_KPOINT_MEASURED = 5151
 WORKLOAD = "two-phase SC cell N=48 (R=0.35, seed 2), 31-point Gamma-X-M-Gamma-R-X path, 20 bands, resid 1e-8, FP64"
 NEV = 20
 TOL = 1e-8
@@ -63,9 +66,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
-# FP64 peak of GB300: 1.25 TFLOP/s dense (recipe's nominal figure), used for the
-# ALU roofline of the complex128 apply.
-FP64_PEAK_TFLOPS = 1.25
+# FP64 peak of GB300: measured in the run by the library's FP64 FMA throughput kernel
+# (pc_fp64_peak); this nominal figure is used only when that measurement fails.
+FP64_NOMINAL_TFLOPS = 1.25
+PRECISION_FP64 = ("FP64 operator, inner PCG iterates and inner products, Krylov recurrences and true "
+                  "residuals; complex64 Fourier preconditioner inside the FP64 PCG")
 
 
 class ClockSampler:
@@ -202,10 +207,10 @@ def run_reference(args):
     pb = O.problem_from_cell(cell, C0=1e9, rho0=1e3)
     threads = os.cpu_count() or 1
     x = complex_gaussian((3, cell.N ** 3 // 4), 7)
-    # block applies one k-point solve of the GPU arm performs (its apply statistics on GB300:
-    # 173.5 inner solves x ~27 PCG iterations plus residual checks = 5151); the same count
-    # scales the GPU arm's own cpu_baseline
-    applies = int(os.environ.get("PC_APPLIES_PER_KPOINT", "5151"))
+    # block applies one k-point solve of the GPU arm performs, as that arm measures it
+    # (solver.block_applies_per_kpoint of its JSON line on GB300: 5151 = 173.5 inner solves x ~27
+    # PCG iterations plus residual checks); the same count scales the GPU arm's own cpu_baseline
+    applies = int(os.environ.get("PC_APPLIES_PER_KPOINT", str(APPLIES_PER_KPOINT_MEASURED)))
     reps = 16
     for _ in range(args.warmup):
         O.apply_block(pb, [0.25, 0, 0], 0, x, 0.1, nthreads=threads)
@@ -223,6 +228,11 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": "s/k-point", "cores": threads, "kind": "oracle",
                              "sample": "%d FP64 oracle block applies per step at N=48, scaled by %d block applies "
                                        "per k-point solve" % (reps, applies)},
+            "extrapolation": {"measured": "time of one FP64 oracle block apply at N=48 (OpenMP, all host cores)",
+                              "applies_per_kpoint": applies,
+                              "source": "the GPU arm's measured block-apply count per k-point "
+                                        "(solver.block_applies_per_kpoint); the oracle's own exact eigen-solve "
+                                        "(ARPACK + sparse LU) takes ~35 min per block and is not run"},
             "e2e": {"value": v, "unit": "s/k-point", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -333,7 +343,7 @@ def profile_run(what):
     pc.pc_grid_destroy(g)
 
 
-def batching_run(args):
+def batching_run(args, emit=True, full_space_sample=2):
     """Ragged batch: N in {32, 48, 64, 96, 128} (own seeds, R ~ U[0.2, 0.4]), `--batch-k` Bloch vectors
     each along the SC path, four parity blocks, 16 bands at 1e-8, complex64 apply and inner PCG with
     the FP64 outer loop, autotuned launches, CUDA-graph PCG chunks, pc_eigs_batch worker pool.
@@ -360,7 +370,7 @@ def batching_run(args):
     total_k = nk * len(sizes)
     # plain FP64 full space, one Bloch vector at a time, on a sample of the same Bloch vectors
     fopt = pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_FP64, full_space=1)
-    sample = [ks[len(ks) // 3], ks[(2 * len(ks)) // 3]]
+    sample = [ks[len(ks) // 3], ks[(2 * len(ks)) // 3]][:max(1, full_space_sample)]
     per_grid_full, max_diff = [], 0.0
     for g, ev in zip(grids, evs):
         pc.pc_eigs(g, sample[0], nev, opt=fopt)  # warm-up of the full-space state
@@ -386,10 +396,12 @@ def batching_run(args):
             "max_rel_diff_vs_fp64_full_space_sampled": max_diff,
             "max_true_rel_resid": info["max_rel_resid"], "failed": info["failed"],
             "pcg_iters": info["pcg_iters"]}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def precision_run(args):
+def precision_run(args, emit=True, nk_max=8):
     """N = 160 two-phase cell (R = 0.3, seed 3), Gamma/X/M/R and four midpoints, 20 bands at 1e-8:
     mixed precision s/k-point, and per-band relative error against the FP64 path on the first k-point."""
     import numpy as np
@@ -405,7 +417,7 @@ def precision_run(args):
     pc.pc_set_k(g, kpts[0])  # launch shapes tuned before the timed solves
     for dt in (pc.PC_C64, pc.PC_C128):
         pc.pc_autotune(g, dt, 0, 4 * om.block_size, stream.cuda_stream)
-    nk = max(1, min(args.steps, len(kpts)))
+    nk = max(1, min(args.steps, len(kpts), nk_max))
     res = []
     for i in range(nk):
         e0 = torch.cuda.Event(enable_timing=True)
@@ -435,7 +447,9 @@ def precision_run(args):
             "max_true_rel_resid_mixed": max(r[2]["max_rel_resid"] for r in res),
             "pcg_iters_per_kpoint_mixed": float(np.mean([r[2]["pcg_iters"] for r in res])),
             "pcg_iters_fp64_first_k": info64["pcg_iters"]}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def paper_run(args):
@@ -493,72 +507,79 @@ def paper_run(args):
     print(json.dumps(line), flush=True)
 
 
-def differentiation_run(args):
-    """N = 64 two-phase cell (R = 0.35, seed 4): gradients of the lowest 12 eigenvalues at 10
-    Bloch vectors of the SC path and of the width of the gap between bands 6 and 7 over them,
-    with respect to the nodewise stiffness (21 entries) and density, by the adjoint kernel.
-    Reported: seconds per Bloch vector for solve + eigenvectors + adjoint, the gap gradient's
-    time, and central differences (step 2^-10 in the inclusion fraction) along seeded random
-    directions against the chain-ruled adjoint gradient."""
+def differentiation_run(args, emit=True, nk=10):
+    """N = 64 two-phase cell (R = 0.35, seed 4) entered as a nodewise material (the (N^3, 21)
+    stiffness and (N^3,) density tensors): gradients of the lowest 12 eigenvalues at `nk` Bloch
+    vectors of the SC path and of the width of the gap between bands 6 and 7 over them, through the
+    torch.autograd functions whose inputs are those tensors (forward: the GPU solve of the nodewise
+    grid; backward: the adjoint kernel).  Reported: seconds per Bloch vector for solve +
+    eigenvectors + adjoint, the gap gradient's time, and central differences with a relative step of
+    1e-6 along `--fd-dirs` seeded random directions in (C, rho) against the autograd gradient of
+    sum(lambda) at one Bloch vector."""
     import numpy as np
     import torch
-    import paper_2606_03599_gb300 as pc
     from paper_2606_03599_gb300 import autodiff as ad
     from workloads import config_cell
     from workloads.kpath import sc_uniform_path
+    import paper_2606_03599_gb300 as pc
     cell = config_cell("diff")
-    N, n = cell.N, cell.N ** 3
+    N = cell.N
     nev = 12
-    ks = sc_uniform_path(10)
-    # nearly binary fractions theta in [h, 1 - h], so that central differences stay in [0, 1]
-    h = 2.0 ** -10
-    theta0 = (h + (1 - 2 * h) * cell.phase.astype(np.float64)).astype(np.float32)
-    g = pc.pc_grid_create(N, cell.C, cell.rho, theta=theta0, a_lat=cell.a_lat)
+    ks = sc_uniform_path(nk)
+    C21, rho = ad.two_phase_nodewise(cell)
     opt = pc.pc_options_default(tol=TOL, autotune=1)
-    try:
-        ad.nodewise_gradients(g, N, ks[1], nev, opt=opt)  # untimed: tuning, workspaces
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        grads = []
-        for k in ks:
-            grads.append(ad.nodewise_gradients(g, N, k, nev, opt=opt))
-        torch.cuda.synchronize()
-        t_grad = (time.perf_counter() - t0) / len(ks)
-        t0 = time.perf_counter()
-        gap, dCg, drg = ad.band_gap(g, N, ks, 5, opt=opt)
-        torch.cuda.synchronize()
-        t_gap = time.perf_counter() - t0
-        # directional derivatives of sum(lambda) at one Bloch vector along random theta directions
-        dC = np.asarray(cell.C[1] - cell.C[0])[ad.IU]
-        drho = float(cell.rho[1] - cell.rho[0])
-        ev0, gC, gr = grads[3]
-        dtheta_grad = gC @ dC + gr * drho
-        rng = np.random.default_rng(2024)
-        errs = []
-        for _ in range(max(1, args.fd_dirs)):
-            d = rng.choice([-1.0, 1.0], size=n)
-            vals = []
-            for sgn in (1.0, -1.0):
-                th = (theta0.astype(np.float64) + sgn * h * d).astype(np.float32)
-                g2 = pc.pc_grid_create(N, cell.C, cell.rho, theta=th, a_lat=cell.a_lat)
-                try:
-                    ev, _, _ = pc.pc_eigs(g2, ks[3], nev, opt=opt)
-                finally:
-                    pc.pc_grid_destroy(g2)
-                vals.append(float(np.sum(ev)))
-            fd = (vals[0] - vals[1]) / (2 * h)
-            an = float(dtheta_grad @ d)
-            errs.append(abs(fd - an) / abs(fd))
-    finally:
-        pc.pc_grid_destroy(g)
+    Ct = torch.tensor(C21, dtype=torch.float64, requires_grad=True)
+    rt = torch.tensor(rho, dtype=torch.float64, requires_grad=True)
+    ad.band_eigenvalues_nodewise(Ct, rt, N, ks[0], nev, opt=opt).sum().backward()  # untimed: tuning
+    Ct.grad = None
+    rt.grad = None
+    torch.cuda.synchronize()
+    kfd = min(3, len(ks) - 1)
+    t0 = time.perf_counter()
+    grad_fd_k = None
+    for i, k in enumerate(ks):
+        lam = ad.band_eigenvalues_nodewise(Ct, rt, N, k, nev, opt=opt)
+        lam.sum().backward()
+        if i == kfd:
+            grad_fd_k = (Ct.grad.numpy().copy(), rt.grad.numpy().copy(), lam.detach().numpy())
+        Ct.grad = None
+        rt.grad = None
+    torch.cuda.synchronize()
+    t_grad = (time.perf_counter() - t0) / len(ks)
+    Cg = torch.tensor(C21, dtype=torch.float64, requires_grad=True)
+    rg = torch.tensor(rho, dtype=torch.float64, requires_grad=True)
+    t0 = time.perf_counter()
+    gap = ad.band_gap_nodewise(Cg, rg, N, ks, 5, opt=opt)
+    gap.backward()
+    torch.cuda.synchronize()
+    t_gap = time.perf_counter() - t0
+    gc, gr, lam0 = grad_fd_k
+    h = 1e-6
+    sC, sr = float(np.abs(C21[:, [0, 6, 11]]).mean()), float(rho.mean())
+    rng = np.random.default_rng(2024)
+    errs = []
+    for _ in range(max(1, args.fd_dirs)):
+        dCd = sC * rng.standard_normal(C21.shape)
+        drd = sr * rng.standard_normal(rho.shape)
+        vals = []
+        for sgn in (1.0, -1.0):
+            ev, _ = ad._solve_nodewise(C21 + sgn * h * dCd, rho + sgn * h * drd, N, ks[kfd], nev, None, opt)
+            vals.append(float(np.sum(ev)))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        an = float(np.sum(gc * dCd) + np.sum(gr * drd))
+        errs.append(abs(fd - an) / abs(fd))
     line = {"metric": METRIC, "mode": "differentiation", "unit": "s/k-point", "dtype": "f64",
-            "config": {"workload": "two-phase SC cell N=64 (R=0.35, seed 4, theta in [2^-10, 1-2^-10]), 10 Bloch "
-                                   "vectors on the SC path, 12 bands, gap between bands 6 and 7, resid 1e-8",
-                       "fd_directions": max(1, args.fd_dirs), "fd_step_theta": h},
-            "grad_s_per_kpoint": t_grad, "gap_hz": gap, "gap_grad_s": t_gap,
-            "gap_grad_norm": float(np.sqrt(np.sum(dCg ** 2) + np.sum(drg ** 2))),
+            "config": {"workload": "two-phase SC cell N=64 (R=0.35, seed 4) as a nodewise material "
+                                   "((N^3, 21) stiffness, (N^3,) density), %d Bloch vectors on the SC path, "
+                                   "12 bands, gap between bands 6 and 7, resid 1e-8" % len(ks),
+                       "k_points": len(ks), "fd_directions": max(1, args.fd_dirs), "fd_relative_step": h,
+                       "fd_direction_scale": {"C": sC, "rho": sr}},
+            "grad_s_per_kpoint": t_grad, "gap_hz": float(gap.detach()), "gap_grad_s": t_gap,
+            "gap_grad_norm": float(np.sqrt(float((Cg.grad ** 2).sum()) + float((rg.grad ** 2).sum()))),
             "fd_rel_err_sum_lambda": errs, "fd_rel_err_max": max(errs)}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -568,6 +589,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the reduced precision / batching / differentiation sub-results of the default line")
     ap.add_argument("--precision", action="store_true",
                     help="run the N=160 precision workload (8 k-points, 20 bands, mixed precision) instead")
     ap.add_argument("--batching", action="store_true",
@@ -575,7 +598,7 @@ def main():
     ap.add_argument("--batch-k", type=int, default=64, help="Bloch vectors per grid of --batching")
     ap.add_argument("--differentiation", action="store_true",
                     help="run the N=64 gradient workload (10 Bloch vectors, 12 bands, gap 6-7) instead")
-    ap.add_argument("--fd-dirs", type=int, default=4, help="finite-difference directions of --differentiation")
+    ap.add_argument("--fd-dirs", type=int, default=50, help="finite-difference directions of --differentiation")
     ap.add_argument("--workers", type=int, default=4, help="host worker threads of --batching")
     ap.add_argument("--paper", action="store_true",
                     help="run the paper's own FCC quartz/silicon workload (40 bands) instead")
@@ -662,7 +685,14 @@ def main():
     kpts_total = sum_over_ranks(world, float(args.steps))
     value = t_max / kpts_total
 
-    # dominant kernel: FP64 stencil apply, device time from events on its launch stream
+    # dominant kernel: FP64 stencil apply, device time from events on its launch stream; its
+    # roofline denominator is the FP64 FMA rate measured here (outside the timed region)
+    try:
+        fp64_peak, fma_rate = pc.pc_fp64_peak(0.5)
+        peak_src = "measured: pc_fp64_peak FP64 FMA throughput kernel on this GPU (2 flops per FMA)"
+    except Exception:
+        fp64_peak, fma_rate = FP64_NOMINAL_TFLOPS, None
+        peak_src = "nominal FP64 dense rate of GB300 (measurement failed)"
     n_app = st["apply_timed"][1]
     app_ms = st["apply_ms"][1] / max(1, n_app)
     nodes_per_launch = st["apply_nodes"][1] / max(1, n_app)
@@ -672,12 +702,13 @@ def main():
              3: "split_fill_x + split_flux + split_fill_f + split_gather (two-pass FP64)"}[kind]
     traffic = SPLIT_F64_DRAM_BYTES_PER_NODE * nodes_per_launch if kind == 3 else None
     roofline = {"kernel": kname + " (block stencil, FP64, autotuned launch)", "bound": "alu",
-                "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / fp64_peak, "traffic": traffic,
                 "traffic_note": "bytes per launch, ncu cold-cache capture scaled by nodes per launch"
                 if traffic is not None else None,
                 "launches": n_app, "avg_launch_us": app_ms * 1e3, "nodes_per_launch": nodes_per_launch,
-                "flops_per_node": FLOPS_PER_NODE, "peak_source": "nominal FP64 dense rate of GB300"}
+                "flops_per_node": FLOPS_PER_NODE, "peak_source": peak_src,
+                "fp64_fma_per_s": fma_rate, "peak_nominal_tflops": FP64_NOMINAL_TFLOPS}
 
     # end-to-end through the C ABI from host buffers: material upload, solve, eigenvalues back
     e2e = None
@@ -699,14 +730,16 @@ def main():
         e2e = {"value": float(np.mean(e2e_ms)) / 1e3, "unit": "s/k-point", "h2d_bytes_per_step": 2 * n,
                "d2h_bytes_per_step": NEV * 8, "steps": len(e2e_ms)}
 
-    # same k-points: mixed precision (complex64 inner PCG + FP64 refinement) and the full-space
-    # FP64 solve, for the blocked-vs-full and FP64-vs-mixed comparisons on this GPU
+    # the same Bloch vectors as the timed steps: mixed precision (complex64 inner PCG + FP64
+    # refinement), the full-space solve (same precision as the main leg) and the main leg with its
+    # preconditioner in FP64 too, for the blocked-vs-full and precision comparisons on this GPU
     compare = None
     if rank == 0:
         compare = {}
-        nk = min(args.steps, 3)
+        nk = args.steps
         for name, o2 in (("mixed", pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED, autotune=1)),
-                         ("full_space_fp64", pc.pc_options_default(tol=TOL, full_space=1, autotune=1))):
+                         ("full_space_fp64", pc.pc_options_default(tol=TOL, full_space=1, autotune=1)),
+                         ("fp64_preconditioner", pc.pc_options_default(tol=TOL, precond_fp32=0, autotune=1))):
             o2.stream = stream.cuda_stream
             pc.pc_eigs(g, kpoint(0), NEV, opt=o2)  # untimed: tunes this leg's launches, builds its state
             ms, err = [], 0.0
@@ -720,10 +753,36 @@ def main():
                 ms.append(e0.elapsed_time(e1))
                 err = max(err, float(np.max(np.abs(ev2 - evals[s]) / evals[s])))
             compare[name] = {"s_per_kpoint": float(np.mean(ms)) / 1e3, "k_points": nk,
-                             "max_rel_diff_vs_blocked_fp64": err}
+                             "same_k_points_as_main_leg": True, "max_rel_diff_vs_blocked_fp64": err}
+        compare["main_leg_s_per_kpoint"] = value
+        compare["blocked_speedup_vs_full_space"] = compare["full_space_fp64"]["s_per_kpoint"] / value
+        compare["mixed_speedup_vs_fp64_full_space"] = (compare["full_space_fp64"]["s_per_kpoint"] /
+                                                        compare["mixed"]["s_per_kpoint"])
 
     apply = apply_throughput(pc, torch) if rank == 0 else None
     pc.pc_grid_destroy(g)
+
+    # reduced runs of the precision, batching and differentiation workloads (counts in each config)
+    forms = None
+    if rank == 0 and not args.no_forms:
+        import copy
+        forms = {}
+        try:
+            forms["precision"] = precision_run(args, emit=False, nk_max=2)
+        except Exception as e:  # reported, never fatal for the headline
+            forms["precision"] = {"error": str(e)}
+        try:
+            a2 = copy.copy(args)
+            a2.batch_k = 4
+            forms["batching"] = batching_run(a2, emit=False, full_space_sample=1)
+        except Exception as e:
+            forms["batching"] = {"error": str(e)}
+        try:
+            a3 = copy.copy(args)
+            a3.fd_dirs = 4
+            forms["differentiation"] = differentiation_run(a3, emit=False, nk=2)
+        except Exception as e:
+            forms["differentiation"] = {"error": str(e)}
 
     if rank != 0:
         if world > 1:
@@ -741,11 +800,12 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": cell.N, "bands": NEV, "tol": TOL, "blocks": 4,
-                   "k_points_per_rank": args.steps, "precision": "plain FP64",
+                   "k_points_per_rank": args.steps, "precision": PRECISION_FP64,
                    "l2": "512 MB buffer written between timed steps (L2 = 129 MB)"},
         "roofline": roofline,
         "apply": apply,
         "compare_same_gpu": compare,
+        "forms": forms,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": st["launches"],

@@ -151,6 +151,19 @@ typedef struct {
  * handle.  Allocates device memory with cudaMalloc on the current device. */
 int pc_grid_create(int N, const pc_material* m, pc_grid** out);
 
+/* Create a grid with a nodewise material: every node l (full order) has its own stiffness and
+ * density, the general pencil of Eq. discrete_GEP (C_h and M_h nodewise, Sec. 2-3) of which the
+ * two-phase rule of pc_grid_create (Eq. subpixel_material_average) is the special case.
+ * C21: host [N^3][21], the independent entries C_l[p][r], p <= r, of each node's symmetric 6x6
+ * Voigt stiffness in row order ([11,22,33,23,13,12], engineering shear, Pa); rho: host [N^3],
+ * kg/m^3, positive; a_lat as in pc_material.  Both arrays are copied (caller keeps ownership).
+ * The device holds 22 FP64 values per node in each layout (about 0.35 KB per node in all).
+ * Supported paths: complex128 applies (two-pass kernels), PC_PREC_FP64 eigen-solves, PCG,
+ * mass, gradients (pc_eig_grad); complex64 applies and PC_PREC_MIXED return PC_EINVAL.  The
+ * preconditioner's reference medium and the default shift use the nodes' volume averages and
+ * largest entries.  PC_EINVAL for a non-finite entry or a non-positive density. */
+int pc_grid_create_nodewise(int N, const double* C21, const double* rho, const double a_lat[9], pc_grid** out);
+
 /* Release every device and host resource of the grid.  NULL is accepted. */
 int pc_grid_destroy(pc_grid* g);
 

@@ -28,7 +28,7 @@ EXPORTED = [
     "pc_block_fourier", "pc_block_precond", "pc_shift_invert_pcg", "pc_options_default", "pc_default_sigma",
     "pc_eigs", "pc_last_error", "pc_version", "pc_apply_batch", "pc_stats_timing", "pc_stats_reset",
     "pc_stats_get", "pc_block_apply_dot_noalloc", "pc_eig_grad", "pc_autotune", "pc_tuned_config",
-    "pc_grid_clone", "pc_eigs_batch", "pc_device_status", "pc_fp64_peak",
+    "pc_grid_clone", "pc_eigs_batch", "pc_device_status", "pc_fp64_peak", "pc_grid_create_nodewise",
 ]
 
 
@@ -124,6 +124,7 @@ def _load():
         "pc_stats_reset": ([], ci),
         "pc_stats_get": ([ctypes.POINTER(c_stats)], ci),
         "pc_device_status": ([vp, vp], ci),
+        "pc_grid_create_nodewise": ([ci, dp, dp, dp, ctypes.POINTER(vp)], ci),
         "pc_fp64_peak": ([cd, dp, dp], ci),
         "pc_last_error": ([], ctypes.c_char_p),
         "pc_version": ([], ctypes.c_char_p),
@@ -210,6 +211,23 @@ def pc_grid_create(N, C, rho, phase=None, theta=None, a_lat=None):
     h = ctypes.c_void_p()
     _check(lib.pc_grid_create(int(N), ctypes.byref(m), ctypes.byref(h)))
     del keep
+    return h.value
+
+
+def pc_grid_create_nodewise(N, C21, rho, a_lat=None):
+    """Grid with a nodewise material: C21 (N^3, 21) upper-triangular Voigt entries per node (Pa, row
+    order p <= r), rho (N^3,) kg/m^3, both in full-grid node order; host arrays (numpy or CPU tensors)."""
+    C21 = np.ascontiguousarray(np.asarray(C21, dtype=np.float64))
+    rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float64))
+    n = int(N) ** 3
+    if C21.shape != (n, 21) or rho.shape != (n,):
+        raise ValueError("C21 must be (N^3, 21) and rho (N^3,)")
+    A = np.eye(3) if a_lat is None else np.asarray(a_lat, dtype=np.float64)
+    a = np.ascontiguousarray(A.T.reshape(9))  # column-major
+    dp = ctypes.POINTER(ctypes.c_double)
+    h = ctypes.c_void_p()
+    _check(lib.pc_grid_create_nodewise(int(N), C21.ctypes.data_as(dp), rho.ctypes.data_as(dp), a.ctypes.data_as(dp),
+                                       ctypes.byref(h)))
     return h.value
 
 

@@ -8,9 +8,13 @@ Degenerate clusters are treated as subspaces: eigenvalues closer than a
 relative ``cluster_tol`` share the mean of their incoming gradients, which is
 the gradient of any symmetric function of the cluster (basis independent).
 
-``BandEigenvalues`` differentiates with respect to the sub-pixel inclusion
-fraction theta of every node (C_i = (1-theta_i) C0 + theta_i C1, rho likewise),
-by the chain rule through the nodewise gradients.
+``NodewiseBandEigenvalues`` and ``NodewiseBandGap`` take the nodewise material itself as
+their inputs: a (N^3, 21) tensor of the independent Voigt stiffness entries of every node
+and a (N^3,) density tensor (the general pencil of Eq. discrete_GEP_main, solved on a grid
+made by ``pc_grid_create_nodewise``); their gradients are the (N^3, 21) and (N^3,)
+Hellmann-Feynman gradients.  ``BandEigenvalues`` differentiates with respect to the
+sub-pixel inclusion fraction theta of every node (C_i = (1-theta_i) C0 + theta_i C1, rho
+likewise), by the chain rule through the nodewise gradients.
 """
 
 from __future__ import annotations
@@ -104,6 +108,118 @@ class BandEigenvalues(torch.autograd.Function):
 def band_eigenvalues(theta, N, C, rho, kappa, nev, a_lat=None, opt=None):
     """Differentiable lowest ``nev`` eigenvalues (SI) at ``kappa`` as a function of theta."""
     return BandEigenvalues.apply(theta, N, C, rho, kappa, nev, a_lat, opt)
+
+
+def _solve_nodewise(C21, rho, N, kappa, nev, a_lat, opt):
+    """Eigenvalues (numpy, SI) and M-normalised full-space eigenvectors (device complex128) of the
+    nodewise material at kappa; the grid lives only for the solve."""
+    g = pc.pc_grid_create_nodewise(N, C21, rho, a_lat=a_lat)
+    try:
+        evecs = torch.empty(nev * 3 * N ** 3, dtype=torch.complex128, device="cuda")
+        ev, _, _ = pc.pc_eigs(g, kappa, nev, opt=opt, evecs=evecs)
+    finally:
+        pc.pc_grid_destroy(g)
+    return ev, evecs
+
+
+def _adjoint(N, a_lat, kappa, evecs, ev, w):
+    """sum_v w_v d lambda_v / d(C_l, rho_l) for full-space eigenvectors: (dC [N^3, 21], drho [N^3])
+    device tensors.  The adjoint kernel reads the grid's geometry, units and Bloch vector only, so a
+    grid of any material with the same N and lattice serves."""
+    n = N ** 3
+    C = np.stack([np.eye(6), np.eye(6)]) * 1e9
+    g = pc.pc_grid_create(N, C, np.array([1e3, 1e3]), a_lat=a_lat)
+    try:
+        dC = torch.zeros(21 * n, dtype=torch.float64, device="cuda")
+        drho = torch.zeros(n, dtype=torch.float64, device="cuda")
+        pc.pc_set_k(g, kappa)
+        pc.pc_eig_grad(g, -1, evecs, ev, w, dC, drho)
+    finally:
+        pc.pc_grid_destroy(g)
+    return dC.view(21, n).T, drho
+
+
+class NodewiseBandEigenvalues(torch.autograd.Function):
+    """lambda(C, rho): lowest ``nev`` non-zero eigenvalues (SI, ascending) at ``kappa`` as a function
+    of the nodewise stiffness C21 (float64 (N^3, 21): entries C_l[p][r], p <= r, row order, Pa) and
+    density rho (float64 (N^3,), kg/m^3), full-grid node order.  Backward: d lambda / d C21 (an
+    off-diagonal entry stands for both C[p][r] and C[r][p]) and d lambda / d rho, with numerically
+    degenerate eigenvalues treated as subspaces."""
+
+    @staticmethod
+    def forward(ctx, C21, rho, N, kappa, nev, a_lat=None, opt=None, cluster_tol=1e-9):
+        ev, evecs = _solve_nodewise(C21.detach().cpu().numpy(), rho.detach().cpu().numpy(), N, kappa, nev, a_lat,
+                                    opt)
+        ctx.N, ctx.a_lat, ctx.kappa, ctx.ev, ctx.evecs, ctx.cluster_tol = N, a_lat, kappa, ev, evecs, cluster_tol
+        return torch.as_tensor(ev, dtype=torch.float64, device=C21.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        w = subspace_weights(ctx.ev, grad_out.detach().cpu().numpy(), ctx.cluster_tol)
+        dC, drho = _adjoint(ctx.N, ctx.a_lat, ctx.kappa, ctx.evecs, ctx.ev, w)
+        ctx.evecs = None
+        dev = grad_out.device
+        return (dC.to(dev), drho.to(dev)) + (None,) * 6
+
+
+def band_eigenvalues_nodewise(C21, rho, N, kappa, nev, a_lat=None, opt=None):
+    """Differentiable lowest ``nev`` eigenvalues (SI) at ``kappa`` of the nodewise material (C21, rho)."""
+    return NodewiseBandEigenvalues.apply(C21, rho, N, kappa, nev, a_lat, opt)
+
+
+class NodewiseBandGap(torch.autograd.Function):
+    """Width (Hz) of the gap above band ``lo`` (0-based) over a set of Bloch vectors,
+    min_k f_{lo+1}(k) - max_k f_lo(k) with f = sqrt(lambda) / (2 pi), as a function of the nodewise
+    material (C21, rho) (as ``NodewiseBandEigenvalues``).  Backward: through the two active Bloch
+    vectors (the minimiser and the maximiser) with d f / d lambda = 1 / (8 pi^2 f); a band that is
+    degenerate there is treated as a subspace (one more band is solved to see its cluster)."""
+
+    @staticmethod
+    def forward(ctx, C21, rho, N, kappas, lo, a_lat=None, opt=None, cluster_tol=1e-9):
+        hi, nev = lo + 1, lo + 3
+        Cn, rn = C21.detach().cpu().numpy(), rho.detach().cpu().numpy()
+        top = bot = None
+        for k in kappas:
+            ev, evecs = _solve_nodewise(Cn, rn, N, k, nev, a_lat, opt)
+            f = np.sqrt(ev) / (2 * np.pi)
+            if top is None or f[hi] < top[0]:
+                top = (f[hi], k, ev, evecs)
+            if bot is None or f[lo] > bot[0]:
+                bot = (f[lo], k, ev, evecs)
+        ctx.N, ctx.a_lat, ctx.lo, ctx.top, ctx.bot, ctx.cluster_tol = N, a_lat, lo, top, bot, cluster_tol
+        return torch.as_tensor(top[0] - bot[0], dtype=torch.float64, device=C21.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = float(grad_out.detach().cpu())
+        n = ctx.N ** 3
+        dC = torch.zeros((n, 21), dtype=torch.float64, device="cuda")
+        drho = torch.zeros(n, dtype=torch.float64, device="cuda")
+        for sign, band, (fval, k, ev, evecs) in ((1.0, ctx.lo + 1, ctx.top), (-1.0, ctx.lo, ctx.bot)):
+            w = np.zeros(len(ev))
+            w[band] = g * sign / (8 * np.pi ** 2 * fval)
+            w = subspace_weights(ev, w, ctx.cluster_tol)
+            dc, dr = _adjoint(ctx.N, ctx.a_lat, k, evecs, ev, w)
+            dC += dc
+            drho += dr
+        ctx.top = ctx.bot = None
+        dev = grad_out.device
+        return (dC.to(dev), drho.to(dev)) + (None,) * 6
+
+
+def band_gap_nodewise(C21, rho, N, kappas, lo, a_lat=None, opt=None):
+    """Differentiable width (Hz) of the gap above band ``lo`` over ``kappas`` of the nodewise material."""
+    return NodewiseBandGap.apply(C21, rho, N, kappas, lo, a_lat, opt)
+
+
+def two_phase_nodewise(cell):
+    """(C21 (N^3, 21), rho (N^3,)) numpy arrays of a two-phase cell's nodewise material (phase ids or
+    inclusion fractions, Eq. subpixel_material_average)."""
+    th = cell.theta_f64()
+    C = np.asarray(cell.C, dtype=np.float64)
+    C21 = (1.0 - th)[:, None] * C[0][IU][None, :] + th[:, None] * C[1][IU][None, :]
+    rho = (1.0 - th) * float(cell.rho[0]) + th * float(cell.rho[1])
+    return C21, rho
 
 
 def band_gap(g, N, kappas, lo, opt=None):

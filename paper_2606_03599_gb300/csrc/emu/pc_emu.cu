@@ -424,5 +424,13 @@ extern "C" int pc_emu_apply(int N, int block, int dtype, int shape, int tz, cons
     }
     StencilParams<double> P;
     make_stencil_params(P, Chat, rhohat2, ainv9, cubic != 0, N, phi3, X, Y, Z);
+    if (matkind == 2) {  // nodewise material: the two-pass kernels only ([22][m] FP64 in mat)
+        if (shape != 30) return -1;
+        if (full) cubic ? emu_run_split<double, true, true, 2>(P, block, x, y, mat, shift)
+                        : emu_run_split<double, true, false, 2>(P, block, x, y, mat, shift);
+        else cubic ? emu_run_split<double, false, true, 2>(P, block, x, y, mat, shift)
+                   : emu_run_split<double, false, false, 2>(P, block, x, y, mat, shift);
+        return 0;
+    }
     return emu_t<double>(shape, P, full, cubic != 0, matkind, block, x, y, mat, shift, tz);
 }

@@ -84,7 +84,7 @@ int device_sm_count() {
 
 ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool blocks, int matkind, bool scratch_ok) {
     ApplyConfig c;
-    if (scratch_ok && ((dtype == PC_C128 && apply_kernel_mode() == 0) || apply_kernel_mode() == 3)) {
+    if (scratch_ok && ((dtype == PC_C128 && (apply_kernel_mode() == 0 || matkind == 2)) || apply_kernel_mode() == 3)) {
         // complex128 is bound by GB300's FP64 pipe: fluxes once per node (two-pass kernels)
         c.split = true;
         c.shape = 0;
@@ -151,6 +151,10 @@ ApplyConfig choose_apply_config(int X, int Y, int Z, int nitems, int dtype, bool
     return c;
 }
 
+int voigt_upper_host(int p, int r) {
+    return p <= r ? p * 6 - p * (p - 1) / 2 + (r - p) : r * 6 - r * (r - 1) / 2 + (p - r);
+}
+
 static bool finite_all(const double* v, int n) {
     for (int i = 0; i < n; ++i)
         if (!std::isfinite(v[i])) return false;
@@ -210,32 +214,22 @@ int pc_grid_destroy(pc_grid* g) {
     return PC_OK;
 }
 
-int pc_grid_create(int N, const pc_material* m, pc_grid** out) {
-    if (!out) return fail(PC_EINVAL, "pc_grid_create: null output");
-    *out = nullptr;
-    if (N < 4 || (N & 1)) return fail(PC_EINVAL, "pc_grid_create: N must be even and >= 4 (parity blocks need even grids)");
-    if (N > 1024) return fail(PC_EINVAL, "pc_grid_create: N > 1024 not supported");
-    if (!m) return fail(PC_EINVAL, "pc_grid_create: null material");
-    if (m->phase && m->theta) return fail(PC_EINVAL, "pc_grid_create: give phase or theta, not both");
-    if (!finite_all(&m->C[0][0], 72) || !finite_all(m->rho, 2) || !finite_all(m->a_lat, 9))
-        return fail(PC_EINVAL, "pc_grid_create: non-finite material constants");
-    for (int p = 0; p < 2; ++p) {
-        if (!(m->rho[p] > 0)) return fail(PC_EINVAL, "pc_grid_create: densities must be positive");
-        double scale = 0;
-        for (int e = 0; e < 36; ++e) scale = std::fmax(scale, std::fabs(m->C[p][e]));
-        for (int a = 0; a < 6; ++a)
-            for (int b = a + 1; b < 6; ++b)
-                if (std::fabs(m->C[p][a * 6 + b] - m->C[p][b * 6 + a]) > 1e-12 * scale)
-                    return fail(PC_EINVAL, "pc_grid_create: stiffness must be symmetric");
-    }
+}  // extern "C"
+
+// Lattice, grid size and units of a new grid (no material yet).  a_lat column-major.
+static int grid_init(int N, const double a_lat[9], const char* who, pc_grid** gout) {
+    *gout = nullptr;
+    if (N < 4 || (N & 1)) return fail(PC_EINVAL, std::string(who) + ": N must be even and >= 4 (parity blocks need even grids)");
+    if (N > 1024) return fail(PC_EINVAL, std::string(who) + ": N > 1024 not supported");
+    if (!finite_all(a_lat, 9)) return fail(PC_EINVAL, std::string(who) + ": non-finite lattice basis");
     // A_lat (column-major input) and its determinant
     double A[3][3];
     for (int l = 0; l < 3; ++l)
-        for (int r = 0; r < 3; ++r) A[r][l] = m->a_lat[3 * l + r];
+        for (int r = 0; r < 3; ++r) A[r][l] = a_lat[3 * l + r];
     double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
                  A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
                  A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
-    if (!(std::fabs(det) > 0)) return fail(PC_EINVAL, "pc_grid_create: singular lattice basis");
+    if (!(std::fabs(det) > 0)) return fail(PC_EINVAL, std::string(who) + ": singular lattice basis");
 
     pc_grid* g = new pc_grid();
     g->N = N;
@@ -246,10 +240,6 @@ int pc_grid_create(int N, const pc_material* m, pc_grid** out) {
     g->nb = g->n / 4;
     g->L = std::cbrt(std::fabs(det));
     cudaGetDevice(&g->device);
-    for (int p = 0; p < 2; ++p) {
-        for (int e = 0; e < 36; ++e) g->Chat[p][e] = m->C[p][e] / g->C0;
-        g->rhohat[p] = m->rho[p] / g->rho0;
-    }
     // inverse of A_hat = A_lat / L, row-major (A^-1)_{s m}
     double Ah[3][3];
     for (int r = 0; r < 3; ++r)
@@ -272,6 +262,39 @@ int pc_grid_create(int N, const pc_material* m, pc_grid** out) {
             dev = std::fmax(dev, std::fabs(inv[s][mm] - (s == mm ? 1.0 : 0.0)));
         }
     g->cubic = dev < 1e-12;
+
+    *gout = g;
+    return PC_OK;
+}
+
+extern "C" {
+
+int pc_grid_create(int N, const pc_material* m, pc_grid** out) {
+    if (!out) return fail(PC_EINVAL, "pc_grid_create: null output");
+    *out = nullptr;
+    if (!m) return fail(PC_EINVAL, "pc_grid_create: null material");
+    if (m->phase && m->theta) return fail(PC_EINVAL, "pc_grid_create: give phase or theta, not both");
+    if (!finite_all(&m->C[0][0], 72) || !finite_all(m->rho, 2) || !finite_all(m->a_lat, 9))
+        return fail(PC_EINVAL, "pc_grid_create: non-finite material constants");
+    for (int p = 0; p < 2; ++p) {
+        if (!(m->rho[p] > 0)) return fail(PC_EINVAL, "pc_grid_create: densities must be positive");
+        double scale = 0;
+        for (int e = 0; e < 36; ++e) scale = std::fmax(scale, std::fabs(m->C[p][e]));
+        for (int a = 0; a < 6; ++a)
+            for (int b = a + 1; b < 6; ++b)
+                if (std::fabs(m->C[p][a * 6 + b] - m->C[p][b * 6 + a]) > 1e-12 * scale)
+                    return fail(PC_EINVAL, "pc_grid_create: stiffness must be symmetric");
+    }
+    pc_grid* g = nullptr;
+    PC_TRY(grid_init(N, m->a_lat, "pc_grid_create", &g));
+    for (int p = 0; p < 2; ++p) {
+        for (int e = 0; e < 36; ++e) g->Chat[p][e] = m->C[p][e] / g->C0;
+        g->rhohat[p] = m->rho[p] / g->rho0;
+    }
+    for (int p = 0; p < 2; ++p) {
+        for (int e = 0; e < 36; ++e) g->sigma_cmax = std::fmax(g->sigma_cmax, std::fabs(g->Chat[p][e]));
+        g->sigma_rmax = std::fmax(g->sigma_rmax, g->rhohat[p]);
+    }
 
     // material: full order and the four block orders
     g->matkind = m->theta ? 1 : 0;
@@ -331,6 +354,71 @@ int pc_grid_create(int N, const pc_material* m, pc_grid** out) {
     return PC_OK;
 }
 
+int pc_grid_create_nodewise(int N, const double* C21, const double* rho, const double a_lat[9], pc_grid** out) {
+    if (!out) return fail(PC_EINVAL, "pc_grid_create_nodewise: null output");
+    *out = nullptr;
+    if (!C21 || !rho || !a_lat) return fail(PC_EINVAL, "pc_grid_create_nodewise: null argument");
+    pc_grid* g = nullptr;
+    PC_TRY(grid_init(N, a_lat, "pc_grid_create_nodewise", &g));
+    const int64_t n = g->n, nb = g->nb;
+    // hat units; the reference medium (volume averages) doubles as both phase tables, which only the
+    // preconditioner, the default shift and the launch parameters read for this material kind
+    double Cavg[36] = {0}, ravg = 0.0;
+    for (int64_t l = 0; l < n; ++l) {
+        const double r = rho[l];
+        bool ok = std::isfinite(r) && r > 0;
+        for (int q = 0; q < 21; ++q) ok = ok && std::isfinite(C21[l * 21 + q]);
+        if (!ok) {
+            pc_grid_destroy(g);
+            return fail(PC_EINVAL, "pc_grid_create_nodewise: non-finite stiffness or non-positive density at node " +
+                                       std::to_string(l));
+        }
+        ravg += r / g->rho0;
+        g->sigma_rmax = std::fmax(g->sigma_rmax, r / g->rho0);
+        for (int p = 0; p < 6; ++p)
+            for (int q = 0; q < 6; ++q) {
+                const double c = C21[l * 21 + voigt_upper_host(p, q)] / g->C0;
+                Cavg[p * 6 + q] += c;
+                g->sigma_cmax = std::fmax(g->sigma_cmax, std::fabs(c));
+            }
+    }
+    for (int p = 0; p < 2; ++p) {
+        for (int e = 0; e < 36; ++e) g->Chat[p][e] = Cavg[e] / (double)n;
+        g->rhohat[p] = ravg / (double)n;
+    }
+    g->mean_theta = 0.0;
+    g->matkind = 2;
+    // device layout [22][m]: the 21 entries scaled as the stencil tables (times (N/4)^2 on a cubic
+    // lattice), then the density
+    const double q2 = g->cubic ? (N / 4.0) * (N / 4.0) : 1.0;
+    std::vector<double> full((size_t)22 * n);
+    for (int64_t l = 0; l < n; ++l) {
+        for (int q = 0; q < 21; ++q) full[(size_t)q * n + l] = C21[l * 21 + q] / g->C0 * q2;
+        full[(size_t)21 * n + l] = rho[l] / g->rho0;
+    }
+    cudaError_t e = cudaMalloc(&g->d_err, sizeof(int));
+    if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMalloc(error word)"); }
+    cudaMemset(g->d_err, 0, sizeof(int));
+    e = cudaMalloc(&g->d_mat_full, full.size() * sizeof(double));
+    if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMalloc(material)"); }
+    e = cudaMemcpy(g->d_mat_full, full.data(), full.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMemcpy(material)"); }
+    std::vector<int64_t> idx(nb);
+    std::vector<double> blk((size_t)22 * nb);
+    for (int b = 0; b < 4; ++b) {
+        pc_block_index(N, b, idx.data());
+        for (int q = 0; q < 22; ++q)
+            for (int64_t t = 0; t < nb; ++t) blk[(size_t)q * nb + t] = full[(size_t)q * n + idx[t]];
+        e = cudaMalloc(&g->d_mat_blk[b], blk.size() * sizeof(double));
+        if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMalloc(block material)"); }
+        e = cudaMemcpy(g->d_mat_blk[b], blk.data(), blk.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { pc_grid_destroy(g); return cuda_fail(e, "cudaMemcpy(block material)"); }
+    }
+    fill_params(g);
+    *out = g;
+    return PC_OK;
+}
+
 int pc_set_k(pc_grid* g, const double kappa[3]) {
     if (!g || !kappa) return fail(PC_EINVAL, "pc_set_k: null argument");
     if (!finite_all(kappa, 3)) return fail(PC_EINVAL, "pc_set_k: non-finite kappa");
@@ -358,6 +446,8 @@ int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nit
                int dot_stride, cudaStream_t s, const ApplyConfig* cfg_in) {
     const int X = full ? g->N : g->X, Y = full ? g->N : g->Y, Z = g->Z;
     ApplyConfig cfg = cfg_in ? *cfg_in : apply_config_for(g, full, nitems, dtype);
+    if (g->matkind == 2 && !(dtype == PC_C128 && cfg.split))
+        return fail(PC_EINVAL, "apply: a nodewise material is applied by the complex128 two-pass kernels only");
     void* th = timing_enabled() ? timing_begin(s) : nullptr;
     int rc;
     if (cfg.split) {

@@ -159,7 +159,16 @@ static int launch_apply_split_t(bool full, bool cubic, int matkind, const Stenci
             B.fe[i] = w + 3 * G.ne;
         }
         int rc;
-        if (full) {
+        if (matkind == 2) {
+            if constexpr (sizeof(R) == 8) {
+                if (full) rc = cubic ? launch_split_t<R, true, true, 2>(P, B, G, dp, ds, s)
+                                     : launch_split_t<R, true, false, 2>(P, B, G, dp, ds, s);
+                else rc = cubic ? launch_split_t<R, false, true, 2>(P, B, G, dp, ds, s)
+                                : launch_split_t<R, false, false, 2>(P, B, G, dp, ds, s);
+            } else {
+                rc = fail(PC_EINVAL, "apply: nodewise material needs complex128");
+            }
+        } else if (full) {
             if (cubic) rc = matkind ? launch_split_t<R, true, true, 1>(P, B, G, dp, ds, s) : launch_split_t<R, true, true, 0>(P, B, G, dp, ds, s);
             else rc = matkind ? launch_split_t<R, true, false, 1>(P, B, G, dp, ds, s) : launch_split_t<R, true, false, 0>(P, B, G, dp, ds, s);
         } else {

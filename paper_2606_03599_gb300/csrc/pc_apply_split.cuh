@@ -58,6 +58,15 @@ inline SplitGeom make_split_geom(int X, int Y, int Z) {
 // Complex values of scratch per item: x_e (3 arrays) and f_e (15 arrays).
 inline int64_t split_item_elems(const SplitGeom& G) { return 18 * G.ne; }
 
+// Upper-triangular position (row order, p <= r) of Voigt entry (p, r) among the 21 independent
+// entries of a symmetric 6x6 stiffness.
+PC_HD constexpr int voigt_upper(int p, int r) {
+    return p <= r ? p * 6 - p * (p - 1) / 2 + (r - p) : r * 6 - r * (r - 1) / 2 + (p - r);
+}
+
+// MATK: 0 = phase ids (uint8), 1 = inclusion fraction theta (float), 2 = nodewise material (FP64,
+// component-major [22][m]: the 21 upper-triangular stiffness entries scaled as the kernel's tables
+// (hat units, (N/4)^2 folded in on a cubic lattice), then the density in hat units).
 template <typename R, bool FULL, bool CUBIC, int MATK>
 struct SplitApply {
     using C = typename CT<R>::T;
@@ -146,6 +155,7 @@ struct SplitApply {
 
     static PC_HD MT read_mat(const void* mat, int64_t t) {
         if (MATK == 0) return (MT)(static_cast<const uint8_t*>(mat)[t]);
+        if (MATK == 2) return (MT)0;
         return (MT)(static_cast<const float*>(mat)[t]);
     }
 
@@ -208,7 +218,22 @@ struct SplitApply {
         e[5] = cadd(Gm[1][0], Gm[0][1]);
         const MT mv = read_mat(mat, t);
         C tt[6];
-        if (MATK == 0) {
+        if (MATK == 2) {
+            const R* md = static_cast<const R*>(mat);
+            R cn[21];
+#pragma unroll
+            for (int q = 0; q < 21; ++q) {
+                PC_IDX((int64_t)q * G.m + t, 22 * G.m);
+                cn[q] = md[(int64_t)q * G.m + t];
+            }
+#pragma unroll
+            for (int p = 0; p < 6; ++p) {
+                C acc = cscale(cn[voigt_upper(p, 0)], e[0]);
+#pragma unroll
+                for (int q = 1; q < 6; ++q) acc = cfma(cn[voigt_upper(p, q)], e[q], acc);
+                tt[p] = acc;
+            }
+        } else if (MATK == 0) {
             const int ph = mv != 0 ? 1 : 0;
             const R* Cp = Ct[ph];
             if (uniform_ortho_ok && warp_all(P.ortho[ph] != 0)) {  // normal block and shear diagonal only
@@ -286,7 +311,8 @@ struct SplitApply {
         }
         const MT mv = read_mat(mat, t);
         R rho;
-        if (MATK == 0) rho = P.rho[mv != 0 ? 1 : 0];
+        if (MATK == 2) rho = static_cast<const R*>(mat)[21 * G.m + t];
+        else if (MATK == 0) rho = P.rho[mv != 0 ? 1 : 0];
         else rho = P.rho[0] + (R)mv * (P.rho[1] - P.rho[0]);
         const R sr = shift * rho;
         const int64_t own = eidx(G, a, b, k);

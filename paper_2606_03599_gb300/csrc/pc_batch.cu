@@ -41,11 +41,13 @@ extern "C" int pc_grid_clone(const pc_grid* src, pc_grid** out) {
     g->cubic = src->cubic;
     g->matkind = src->matkind;
     g->mean_theta = src->mean_theta;
+    g->sigma_cmax = src->sigma_cmax;
+    g->sigma_rmax = src->sigma_rmax;
     g->mat_pitch = src->mat_pitch;
     g->device = src->device;
     g->P64 = src->P64;
     g->P32 = src->P32;
-    const size_t esz = g->matkind ? sizeof(float) : sizeof(uint8_t);
+    const size_t esz = g->matkind == 2 ? 22 * sizeof(double) : (g->matkind ? sizeof(float) : sizeof(uint8_t));
     auto dup = [&](const void* from, void** to, size_t bytes) -> int {
         if (!from) return PC_OK;
         PC_CUDA_TRY(cudaMalloc(to, bytes));

@@ -24,15 +24,17 @@ constexpr int kGramThreads = 256;
 constexpr int kGramCB = 2;  // columns of W per register block
 
 template <int MATK>
-__device__ __forceinline__ double node_weight(const void* __restrict__ mat, int64_t t, double rho0, double drho) {
+__device__ __forceinline__ double node_weight(const void* __restrict__ mat, int64_t t, int64_t m, double rho0,
+                                              double drho) {
     if (MATK == 0) return rho0 + drho * (double)static_cast<const uint8_t*>(mat)[t];
     if (MATK == 1) return rho0 + drho * (double)static_cast<const float*>(mat)[t];
+    if (MATK == 2) return static_cast<const double*>(mat)[21 * m + t];
     return 1.0;
 }
 
 // Partial sums of out(i, j) = sum_e conj(A[i][e]) w(e) B[j][e] over the nodes [t0, t1) of chunk
 // blockIdx.x (all three components), for rows i0 .. i0 + RB - 1 and columns j0 .. j0 + CB - 1.
-// MATK: -1 = no weight, 0 = phase ids, 1 = inclusion fractions.
+// MATK: -1 = no weight, 0 = phase ids, 1 = inclusion fractions, 2 = nodewise material.
 template <int RB, int MATK>
 __global__ void __launch_bounds__(kGramThreads)
     ts_gram_kernel(const double2* __restrict__ A, int rows, const double2* __restrict__ B, int cols, int64_t m,
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(kGramThreads)
 #pragma unroll
         for (int j = 0; j < CB; ++j) ar[i][j] = ai[i][j] = 0.0;
     for (int64_t t = t0 + threadIdx.x; t < t1; t += kGramThreads) {
-        const double w = node_weight<MATK>(mat, t, rho0, drho);
+        const double w = node_weight<MATK>(mat, t, m, rho0, drho);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const int64_t e = c * m + t;
@@ -173,6 +175,8 @@ int launch_gram_rb(const double2* A, int rows, const double2* B, int cols, int64
         ts_gram_kernel<RB, -1><<<grid, kGramThreads, 0, s>>>(A, rows, B, cols, m, mat, rho0, drho, ngc, nchunk, part);
     else if (matkind == 0)
         ts_gram_kernel<RB, 0><<<grid, kGramThreads, 0, s>>>(A, rows, B, cols, m, mat, rho0, drho, ngc, nchunk, part);
+    else if (matkind == 2)
+        ts_gram_kernel<RB, 2><<<grid, kGramThreads, 0, s>>>(A, rows, B, cols, m, mat, rho0, drho, ngc, nchunk, part);
     else
         ts_gram_kernel<RB, 1><<<grid, kGramThreads, 0, s>>>(A, rows, B, cols, m, mat, rho0, drho, ngc, nchunk, part);
     note_launch();

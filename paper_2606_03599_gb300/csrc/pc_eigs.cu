@@ -164,8 +164,7 @@ __global__ void resid_stats(const double2* __restrict__ Y, const double2* __rest
     const double2* r = Rv + (int64_t)i * 3 * m;
     double acc[5] = {0, 0, 0, 0, 0};
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
-        const double th = matkind ? (double)(static_cast<const float*>(mat)[t]) : (double)(static_cast<const uint8_t*>(mat)[t]);
-        const double rho = rho0 + th * (rho1 - rho0);
+        const double rho = node_rho_hat<double>(mat, matkind, rho0, rho1, m, t);
         for (int a = 0; a < 3; ++a) {
             const double2 yv = y[a * m + t], rv = r[a * m + t];
             const double yy = yv.x * yv.x + yv.y * yv.y;
@@ -665,6 +664,8 @@ static int build_null(Eigs& E, Space& S) {
 
 static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_options* opt, double* evals,
                     void* evecs, int* block_of, pc_eigs_info* info) {
+    if (g->matkind == 2 && opt->precision == PC_PREC_MIXED)
+        return fail(PC_EINVAL, "pc_eigs: a nodewise material is solved in PC_PREC_FP64 only");
     auto t0 = std::chrono::steady_clock::now();
     PC_TRY(pc_set_k(g, kappa));
     if (!g->sol) g->sol = new Solver();
@@ -892,12 +893,7 @@ int pc_options_default(pc_options* o) {
 
 double pc_default_sigma(const pc_grid* g) {
     if (!g) return NAN;
-    double cmax = 0, rmax = 0;
-    for (int p = 0; p < 2; ++p) {
-        for (int e = 0; e < 36; ++e) cmax = std::fmax(cmax, std::fabs(g->Chat[p][e]));
-        rmax = std::fmax(rmax, g->rhohat[p]);
-    }
-    return -0.30 * cmax / rmax;
+    return -0.30 * g->sigma_cmax / g->sigma_rmax;
 }
 
 int pc_block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* w, void* what, void* stream) {
@@ -950,6 +946,7 @@ int pc_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_o
     if (!(o->tol > 0) || !(o->inner_tol > 0)) return fail(PC_EINVAL, "pc_eigs: tolerances must be positive");
     if (o->precision != PC_PREC_FP64 && o->precision != PC_PREC_MIXED)
         return fail(PC_EINVAL, "pc_eigs: precision must be PC_PREC_FP64 or PC_PREC_MIXED");
+
     if (!std::isnan(sigma) && !std::isfinite(sigma)) return fail(PC_EINVAL, "pc_eigs: bad sigma");
     const int64_t dim = o->full_space ? 3 * g->n : 3 * g->nb;
     if (nev > dim / 8) return fail(PC_EINVAL, "pc_eigs: nev too large for this grid");

@@ -153,6 +153,18 @@ uint32_t wait_limit();
 // PC_OK, or PC_ECUDA with a message when a bounded device wait expired.
 int grid_device_status(pc_grid* g, cudaStream_t s);
 
+int voigt_upper_host(int p, int r);  // position of Voigt entry (p, r) among the 21 upper entries
+
+// Density of node t in hat units for the three material kinds: 0 = phase ids (uint8), 1 =
+// inclusion fractions (float), 2 = nodewise material (FP64, component-major [22][m], entry 21 the
+// density).  m = nodes of the layout.
+template <typename R>
+__host__ __device__ inline R node_rho_hat(const void* mat, int matkind, R rho0, R rho1, int64_t m, int64_t t) {
+    if (matkind == 2) return (R) static_cast<const double*>(mat)[21 * m + t];
+    const R th = matkind ? (R) static_cast<const float*>(mat)[t] : (R) static_cast<const uint8_t*>(mat)[t];
+    return rho0 + th * (rho1 - rho0);
+}
+
 // Launch accounting (pc_stats): every kernel launch of the library calls note_launch.
 void note_launch(int n = 1);
 void note_apply_launch(int n = 1);
@@ -191,7 +203,8 @@ struct pc_grid {
     double rhohat[2];
     double Ainv[9];  // (A_hat^-1)_{s m}, row-major s*3+m
     bool cubic = true;
-    int matkind = 0;  // 0 = uint8 phase ids, 1 = float theta
+    int matkind = 0;  // 0 = uint8 phase ids, 1 = float theta, 2 = nodewise ([22][m] FP64)
+    double sigma_cmax = 0.0, sigma_rmax = 0.0;  // largest |C| entry and density (hat units): default shift
     double mean_theta = 0.0;  // volume fraction of phase 1
     int* d_err = nullptr;     // device error word of the TMA kernels (timed-out waits)
     void* d_mat_full = nullptr;

@@ -41,7 +41,8 @@ int bucket_of(int nitems) {
 std::string tune_key(int X, int Y, int Z, int dtype, bool full, int matkind, bool cubic, int nitems) {
     char buf[160];
     std::snprintf(buf, sizeof(buf), "%d,%d,%d,%s,%s,%s,%s,n%d,sm%d", X, Y, Z, dtype == PC_C64 ? "c64" : "c128",
-                  full ? "full" : "blocks", matkind ? "theta" : "phase", cubic ? "cubic" : "general",
+                  full ? "full" : "blocks", matkind == 2 ? "nodewise" : (matkind ? "theta" : "phase"),
+                  cubic ? "cubic" : "general",
                   bucket_of(nitems), device_sm_count());
     return buf;
 }
@@ -146,6 +147,16 @@ static std::vector<ApplyConfig> candidates(int X, int Y, int Z, int dtype, bool 
     // two-pass kernels: the default for complex128; for complex64 a candidate while the batch's
     // fluxes and extended copies (18 complex64 per extended cell) fit in L2 (126 MB on GB300)
     const double split_mb = (double)split_scratch_bytes(X, Y, Z, nitems, dtype) / (1 << 20);
+    if (matkind == 2) {  // a nodewise material: the complex128 two-pass kernels only
+        if (dtype == PC_C128) {
+            ApplyConfig c;
+            c.split = true;
+            c.tz = Z;
+            c.ctas = split_apply_ctas((int64_t)X * Y * Z);
+            out.push_back(c);
+        }
+        return out;
+    }
     if (dtype == PC_C128 || split_mb <= 96.0) {
         ApplyConfig c;
         c.split = true;

@@ -20,8 +20,7 @@ __global__ void mass_kernel(const C* __restrict__ x, C* __restrict__ y, const vo
                             int matkind, R rho0, R rho1, int64_t m, int ncomp) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += stride) {
-        R th = matkind ? (R)(static_cast<const float*>(mat)[t]) : (R)(static_cast<const uint8_t*>(mat)[t]);
-        R rho = rho0 + th * (rho1 - rho0);
+        const R rho = node_rho_hat<R>(mat, matkind, rho0, rho1, m, t);
         for (int a = 0; a < ncomp; ++a) y[a * m + t] = cscale(rho, x[a * m + t]);
     }
 }

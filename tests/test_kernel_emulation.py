@@ -122,3 +122,48 @@ def test_emulated_kernel_general_lattice_and_fractions(emu, block):
         y = run_emu(emu, pb, block, dtype, shape, tz, kappa, x, 0.5, 1)
         err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
         assert err < (1e-13 if dtype == 2 else 2e-6)
+
+
+@pytest.mark.parametrize("block", [2, -1])
+@pytest.mark.parametrize("lattice", ["cubic", "fcc"])
+def test_emulated_two_pass_nodewise_material(emu, block, lattice):
+    """Nodewise material (every node its own symmetric stiffness and density) in the two-pass
+    complex128 kernels, against the oracle's nodewise pencil."""
+    N = 8
+    n = N ** 3
+    rng = np.random.default_rng(5)
+    cell = two_phase_sphere(N, 0.35, 3)
+    base = O.problem_from_cell(cell, C0=1e9, rho0=1e3)
+    G = rng.standard_normal((n, 6, 6))
+    Cn = base.node_C() + 0.1 * (G + np.transpose(G, (0, 2, 1)))
+    rn = base.node_rho() * (1.0 + 0.2 * rng.uniform(size=n))
+    A = np.eye(3) if lattice == "cubic" else np.array([[0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0]])
+    Ah = A / abs(np.linalg.det(A)) ** (1 / 3)
+    pb = Problem(dims=(N,) * 3, ainv=np.linalg.inv(Ah), C=base.C, rho=base.rho, theta=base.theta,
+                 C_nodes=Cn, rho_nodes=rn)
+    kappa = [0.21, -0.33, 0.4]
+    m = n // 4 if block >= 0 else n
+    x = complex_gaussian((3, m), 11)
+    # the oracle's sparse pencil reads the nodewise material (its C apply takes two phases only)
+    A, M = O.sparse_pencil(pb, kappa, block if block >= 0 else None)
+    ref = ((A - 0.7 * M) @ x.reshape(-1)).reshape(3, m)
+    # the library's device layout: [22][m], the 21 upper entries times (N/4)^2 on a cubic lattice
+    iu = np.triu_indices(6)
+    q2 = (N / 4.0) ** 2 if lattice == "cubic" else 1.0
+    lay = np.concatenate([Cn[:, iu[0], iu[1]].T * q2, rn[None, :]], axis=0)
+    if block >= 0:
+        lay = lay[:, O.block_index(pb.dims, block)]
+    mat = np.ascontiguousarray(lay)
+    dp = ctypes.POINTER(ctypes.c_double)
+    Chat = np.ascontiguousarray(base.C.reshape(72))
+    rho = np.ascontiguousarray(base.rho)
+    ainv = np.ascontiguousarray(pb.ainv.reshape(9))
+    phi = np.ascontiguousarray(2 * np.pi * (np.asarray(kappa, dtype=float) - np.floor(kappa)))
+    xx = np.ascontiguousarray(x.astype(np.complex128))
+    y = np.zeros_like(xx)
+    f = lambda a: a.ctypes.data_as(dp)  # noqa: E731
+    rc = emu.pc_emu_apply(N, block, 2, 30, 0, f(Chat), f(rho), f(ainv), int(lattice == "cubic"), f(phi),
+                          mat.ctypes.data, 2, xx.ctypes.data, y.ctypes.data, 0.7)
+    assert rc == 0
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert err < 1e-13

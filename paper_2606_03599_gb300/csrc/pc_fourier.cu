@@ -22,6 +22,7 @@
 // the same for every block (all points of an orbit share it), so one table of
 // A_ref(m) serves all four blocks.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -330,6 +331,12 @@ __global__ void symbol_table(double* __restrict__ Aref, int* __restrict__ nnull,
     }
 }
 
+int precond_partials(const pc_grid* g) {
+    if (g->X == g->Y && g->Z == 2 * g->X && bloch_dft_supported(g->X, nullptr, nullptr))
+        return std::max(bloch_dft_partials(g->X), unpack_ctas(3 * g->nb));
+    return unpack_ctas(3 * g->nb);
+}
+
 // CTAs per system of the unpack-with-dot kernel (also the count of its partial sums).
 int unpack_ctas(int64_t vs) {
     int64_t g = (vs + 1023) / 1024;
@@ -354,6 +361,9 @@ Precond::~Precond() {
     cudaFree(d_Aref32);
     cudaFree(d_null);
     cudaFree(d_work);
+    cudaFree(d_wn);
+    cudaFree(d_wn32);
+    cudaFree(d_blockids);
 }
 
 namespace pc {
@@ -371,6 +381,26 @@ int precond_create(pc_grid* g) {
     PC_CUDA_TRY(cudaMalloc(&P->d_Aref, sizeof(double) * 9 * g->nb));
     PC_CUDA_TRY(cudaMalloc(&P->d_Aref32, sizeof(float) * 9 * g->nb));
     PC_CUDA_TRY(cudaMalloc(&P->d_null, sizeof(int) * 65));
+    // roots of the own quarter-grid DFT (Bloch-independent) and the block ids
+    P->own_dft = g->X == g->Y && g->Z == 2 * g->X && bloch_dft_supported(g->X, nullptr, nullptr);
+    {
+        const int n = g->X;
+        std::vector<double2> w(n);
+        std::vector<float2> w32(n);
+        for (int j = 0; j < n; ++j) {
+            w[j] = make_double2(std::cos(2 * M_PI * j / n), -std::sin(2 * M_PI * j / n));
+            w32[j] = make_float2((float)w[j].x, (float)w[j].y);
+        }
+        PC_CUDA_TRY(cudaMalloc(&P->d_wn, sizeof(double2) * n));
+        PC_CUDA_TRY(cudaMalloc(&P->d_wn32, sizeof(float2) * n));
+        PC_CUDA_TRY(cudaMemcpy(P->d_wn, w.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
+        PC_CUDA_TRY(cudaMemcpy(P->d_wn32, w32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+        P->wn = P->d_wn;
+        P->wn32 = P->d_wn32;
+        const int ids[4] = {0, 1, 2, 3};
+        PC_CUDA_TRY(cudaMalloc(&P->d_blockids, sizeof(ids)));
+        PC_CUDA_TRY(cudaMemcpy(P->d_blockids, ids, sizeof(ids), cudaMemcpyHostToDevice));
+    }
     // reference medium: volume averages of rho and C over the grid
     const double th = g->mean_theta;
     P->rho_ref = (1 - th) * g->rhohat[0] + th * g->rhohat[1];
@@ -486,6 +516,13 @@ int precond_apply(pc_grid* g, int dtype, int nsys, const void* r, void* z, const
     const int wdt = lower ? PC_C64 : dtype;
     void* W;
     PC_TRY(precond_workspace(g, wdt, nsys, &W));
+    if (P->own_dft) {
+        if (lower && !d_part) return fail(PC_EINVAL, "preconditioner: complex64 transforms need the fused dot");
+        PC_TRY(own_precond(g->X, wdt, dtype, nsys, r, z, W, P, d_sys_block, d_skip, -sigma * P->rho_ref,
+                           1.0 / (double)g->nb, d_part, s));
+        if (npart_out) *npart_out = bloch_dft_partials(g->X);
+        return PC_OK;
+    }
     cufftHandle plan;
     PC_TRY(get_plan(P, g, wdt, nsys, &plan));
     const int64_t vs = 3 * g->nb;
@@ -553,10 +590,11 @@ int block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* in,
     Precond* P = g->pre;
     void* W;
     PC_TRY(precond_workspace(g, dtype, 1, &W));
+    const double sc = 1.0 / std::sqrt((double)g->nb);
+    if (P->own_dft) return own_block_fourier(g->X, dtype, inverse, in, out, W, P, P->d_blockids + block, sc, s);
     cufftHandle plan;
     PC_TRY(get_plan(P, g, dtype, 1, &plan));
     const int64_t vs = 3 * g->nb;
-    const double sc = 1.0 / std::sqrt((double)g->nb);
     const int p12 = block >> 1, p13 = block & 1;
     const int gb = nblocks_for(vs);
     if (dtype == PC_C64) {

@@ -43,6 +43,14 @@ struct Precond {
     std::vector<pc::FftPlan> plans;
     void* d_work = nullptr;
     size_t work_bytes = 0;
+    // own quarter-grid DFT (pc_bloch_dft.cu): the n-th roots e^{-2 pi i j / n}, n = N/2, in both
+    // precisions, and the block ids 0..3 as device ints
+    double2* d_wn = nullptr;
+    float2* d_wn32 = nullptr;
+    const double2* wn = nullptr;
+    const float2* wn32 = nullptr;
+    int* d_blockids = nullptr;
+    bool own_dft = false;  // the own kernels handle this grid's size
 };
 
 namespace pc {
@@ -58,5 +66,15 @@ int precond_apply(pc_grid* g, int dtype, int nsys, const void* r, void* z, const
                   const int* d_skip, double sigma, cudaStream_t s, double* d_part = nullptr,
                   int* npart_out = nullptr, bool fp32_inner = false);
 int unpack_ctas(int64_t vs);
+// Partial sums per system of the preconditioner's fused Re<r, z> (the stride its callers allocate).
+int precond_partials(const pc_grid* g);
+// Own quarter-grid DFT kernels (pc_bloch_dft.cu): supported lengths n = N/2 (n = n1 n2, factors <= 16).
+bool bloch_dft_supported(int n, int* n1, int* n2);
+int bloch_dft_partials(int n);
+// wdt: work precision, vdt: vector precision (PC_C64 / PC_C128); scale = 1 / n_b.
+int own_precond(int n, int wdt, int vdt, int nsys, const void* r, void* z, void* W, const Precond* P,
+                const int* sys_block, const int* skip, double shift_rho, double scale, double* part, cudaStream_t s);
+int own_block_fourier(int n, int dtype, int inverse, const void* in, void* out, void* W, const Precond* P,
+                      const int* d_block, double scale, cudaStream_t s);
 int block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* in, void* out, cudaStream_t s);
 }  // namespace pc

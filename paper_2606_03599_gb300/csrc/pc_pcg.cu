@@ -282,7 +282,7 @@ static int pcg_work(pc_grid* g, int dtype, int nsys, int64_t vs, bool full, PcgW
     const int64_t esz = dtype == PC_C64 ? 8 : 16;
     // partial-sum slots: stencil CTAs, vector CTAs, unpack CTAs (x4 for full space)
     const int nap = std::max(apply_config_for(g, full, 1, dtype).ctas, apply_config_for(g, full, nsys, dtype).ctas);
-    const int npm = std::max(std::max(nap, vec_ctas(vs)), 4 * unpack_ctas(3 * g->nb));
+    const int npm = std::max(std::max(nap, vec_ctas(vs)), 4 * precond_partials(g));
     if (w.cap >= nsys && w.vs == vs && w.npart_max >= npm && w.dtype == dtype) {
         *out = &w;
         return PC_OK;
@@ -504,7 +504,7 @@ static int precond_once_t(pc_grid* g, int block, int dtype, bool fp32_inner, dou
     PC_CUDA_TRY(cudaMallocAsync(&sc.p[0], sizeof(int) * 4, s));
     PC_CUDA_TRY(cudaMemcpyAsync(sc.p[0], hb, sizeof(int) * 4, cudaMemcpyHostToDevice, s));
     // the partial sums of Re<r, z> are not returned; they keep the unpack on the kernels a solve runs
-    PC_CUDA_TRY(cudaMallocAsync(&sc.p[1], sizeof(double) * nsys * unpack_ctas(vs), s));
+    PC_CUDA_TRY(cudaMallocAsync(&sc.p[1], sizeof(double) * nsys * precond_partials(g), s));
     double* d_part = static_cast<double*>(sc.p[1]);
     const void* rin = r;
     void* zout = z;

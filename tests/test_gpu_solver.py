@@ -37,7 +37,9 @@ class Grid:
         self.pc.pc_grid_destroy(self.h)
 
 
-@pytest.mark.parametrize("N", [4, 8])
+# N = 6, 10, 12 run the transform kernels with runtime factors (n = 3, 5, 6), N = 4, 8, 16 the
+# compile-time factorisations (n = 2 x 2 ... 4 x 4 with n = 2 on the runtime path)
+@pytest.mark.parametrize("N", [4, 6, 8, 10, 12, 16])
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_block_fourier_matches_dense_basis(pc, N, dtype):
     import torch

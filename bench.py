@@ -1,14 +1,16 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 parity-blocked band solver.
 
-One step = one Bloch vector of the plain FP64 workload: a seeded two-phase
-simple-cubic cell (N = 48, sphere R = 0.35, seed 2), the Gamma-X-M-Gamma-R-X
-path of 31 k-points (6 intervals per segment), the lowest 20 non-zero bands
-at true relative residual 1e-8, solved on the four parity blocks with the
-shift-invert Krylov-Schur eigensolver and merged.  A step runs every step of
-the hot path: Bloch phases and Fourier symbol tables, fused block applies,
-preconditioned inner CG, Gamma deflation, orthogonalisation and Rayleigh-Ritz,
-FP64 true residuals and the block merge.
+One step = one chunk of --kbatch (default 8) consecutive Bloch vectors of the
+plain FP64 workload: a seeded two-phase simple-cubic cell (N = 48, sphere
+R = 0.35, seed 2), the Gamma-X-M-Gamma-R-X path of 31 k-points (6 intervals per
+segment), the lowest 20 non-zero bands at true relative residual 1e-8, solved on
+the four parity blocks with the shift-invert Krylov-Schur eigensolver and merged.
+The Bloch vectors of a chunk are solved in lockstep (pc_eigs_multi: one batched
+inner PCG, Gram and residual launch over all (Bloch vector, block) spaces).  A
+step runs every step of the hot path: Bloch phases and Fourier symbol tables,
+fused block applies, preconditioned inner CG, Gamma deflation,
+orthogonalisation and Rayleigh-Ritz, FP64 true residuals and the block merge.
 
 Printed JSON (one line, rank 0):
   value     = seconds per k-point for the whole job (max over ranks of the
@@ -41,7 +43,8 @@ METRIC = "block B C B^H apply GDoF/s & HBM frac; sec per k-point for 20 bands @1
 # block applies per k-point of the FP64 band workload, as the GPU arm measures them on GB300
 # (solver.block_applies_per_kpoint); the reference arm scales its per-apply time by it
 APPLIES_PER_KPOINT_MEASURED = 5151
-WORKLOAD = "two-phase SC cell N=48 (R=0.35, seed 2), 31-point Gamma-X-M-Gamma-R-X path, 20 bands, resid 1e-8, FP64"
+WORKLOAD = ("two-phase SC cell N=48 (R=0.35, seed 2), 31-point Gamma-X-M-Gamma-R-X path, 20 bands, resid 1e-8, "
+            "FP64; Bloch vectors solved in lockstep chunks of --kbatch")
 NEV = 20
 TOL = 1e-8
 # algorithmic cost of one stencil apply per node (cubic lattice, binary material):
@@ -160,10 +163,12 @@ def sum_over_ranks(world, v, device="cuda"):
     return float(t.item())
 
 
-def kpoint_index(step, world, rank, nk):
-    """Bloch vector of a timed or warm-up step on one rank: the k-points are dealt round-robin
-    over the ranks (independent problems, no data exchange; weak scaling)."""
-    return (step * world + rank) % nk
+def kpoint_chunk(step, world, rank, nk, kb=1):
+    """Path indices of the Bloch vectors of a timed or warm-up step on one rank: chunk
+    `step * world + rank` of kb consecutive points of the nk-point path (cyclic).  Chunks are dealt
+    round-robin over the ranks (independent problems, no data exchange; weak scaling)."""
+    c = step * world + rank
+    return [(c * kb + j) % nk for j in range(kb)]
 
 
 def cpu_oracle_sample(apply_count_per_kpoint, seconds=15.0):
@@ -586,6 +591,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--kbatch", type=int, default=8,
+                    help="Bloch vectors per step, solved together in lockstep (1 = one pc_eigs per step)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -640,18 +647,26 @@ def main():
 
     cell = config_cell("fp64")
     kpts = sc_path(6)
+    KB = max(1, min(args.kbatch, 32))
     stream = torch.cuda.Stream()
     opt = pc.pc_options_default(tol=TOL, inner_tol=1e-10, precision=pc.PC_PREC_FP64, autotune=1)
     opt.stream = stream.cuda_stream
     g = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
 
-    def kpoint(step):
-        return kpts[kpoint_index(step, world, rank, len(kpts))]
+    def kchunk(step):
+        return np.array([kpts[i] for i in kpoint_chunk(step, world, rank, len(kpts), KB)])
+
+    def solve(gr, ks, o):
+        if KB == 1:
+            ev, _, inf = pc.pc_eigs(gr, ks[0], NEV, opt=o)
+            return ev[None, :], [inf]
+        ev, _, infs = pc.pc_eigs_multi(gr, ks, NEV, opt=o)
+        return ev, infs
 
     # warm-up (untimed)
     for w in range(args.warmup):
-        pc.pc_eigs(g, kpoint(w), NEV, opt=opt)
+        solve(g, kchunk(w), opt)
     torch.cuda.synchronize()
 
     # timed region
@@ -661,20 +676,22 @@ def main():
     pc.pc_stats_timing(1)
     barrier(world)
     torch.cuda.synchronize()
-    step_ms, infos, residuals, evals = [], [], [], []
+    step_ms, infos, residuals, evals, kdone = [], [], [], [], []
     for s in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(float(s))  # L2 flush between timed steps (not timed)
+        ks = kchunk(args.warmup + s)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        ev, blocks, info = pc.pc_eigs(g, kpoint(args.warmup + s), NEV, opt=opt)
+        ev, infs = solve(g, ks, opt)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        infos.append(info)
-        residuals.append(info["max_rel_resid"])
+        infos.append(infs[0])
+        residuals.append(max(i["max_rel_resid"] for i in infs))
         evals.append(ev)
+        kdone.append(ks)
     torch.cuda.synchronize()
     barrier(world)
     st = pc.pc_stats_get()
@@ -682,7 +699,7 @@ def main():
     clk = clocks.stop()
     local_time = sum(step_ms) / 1e3
     t_max = max_over_ranks(world, local_time)
-    kpts_total = sum_over_ranks(world, float(args.steps))
+    kpts_total = sum_over_ranks(world, float(args.steps * KB))
     value = t_max / kpts_total
 
     # dominant kernel: FP64 stencil apply, device time from events on its launch stream; its
@@ -715,47 +732,63 @@ def main():
     if rank == 0 or world > 1:
         phase_pinned = torch.from_numpy(cell.phase).pin_memory()
         e2e_ms = []
-        for s in range(min(args.steps, 4)):
+        for s in range(min(args.steps, 2)):
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             g2 = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=phase_pinned.numpy(), a_lat=cell.a_lat)
-            ev2, _, _ = pc.pc_eigs(g2, kpoint(s), NEV, opt=opt)
+            solve(g2, kchunk(s), opt)
             pc.pc_grid_destroy(g2)
             e1.record(stream)
             e1.synchronize()
             e2e_ms.append(e0.elapsed_time(e1))
         n = cell.N ** 3
-        e2e = {"value": float(np.mean(e2e_ms)) / 1e3, "unit": "s/k-point", "h2d_bytes_per_step": 2 * n,
-               "d2h_bytes_per_step": NEV * 8, "steps": len(e2e_ms)}
+        e2e = {"value": float(np.mean(e2e_ms)) / 1e3 / KB, "unit": "s/k-point", "h2d_bytes_per_step": 2 * n,
+               "d2h_bytes_per_step": KB * NEV * 8, "steps": len(e2e_ms), "k_points_per_step": KB}
 
-    # the same Bloch vectors as the timed steps: mixed precision (complex64 inner PCG + FP64
-    # refinement), the full-space solve (same precision as the main leg) and the main leg with its
-    # preconditioner in FP64 too, for the blocked-vs-full and precision comparisons on this GPU
+    # comparisons on this GPU over the Bloch vectors of the first timed steps: mixed precision
+    # (complex64 inner PCG + FP64 refinement) and the FP64-preconditioner variant, both in lockstep
+    # chunks as the main leg; the blocked FP64 solve and the plain FP64 full-space solve one Bloch
+    # vector at a time (pc_eigs)
     compare = None
     if rank == 0:
         compare = {}
-        nk = args.steps
-        for name, o2 in (("mixed", pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED, autotune=1)),
-                         ("full_space_fp64", pc.pc_options_default(tol=TOL, full_space=1, autotune=1)),
-                         ("fp64_preconditioner", pc.pc_options_default(tol=TOL, precond_fp32=0, autotune=1))):
+        nc = max(1, min(args.steps, 3))
+        cks = [kchunk(args.warmup + s) for s in range(nc)]
+        legs = (("mixed", pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED, autotune=1), True),
+                ("fp64_preconditioner", pc.pc_options_default(tol=TOL, precond_fp32=0, autotune=1), True),
+                ("one_at_a_time_fp64", pc.pc_options_default(tol=TOL, autotune=1), False),
+                ("full_space_fp64", pc.pc_options_default(tol=TOL, full_space=1, autotune=1), False))
+        for name, o2, lockstep in legs:
             o2.stream = stream.cuda_stream
-            pc.pc_eigs(g, kpoint(0), NEV, opt=o2)  # untimed: tunes this leg's launches, builds its state
-            ms, err = [], 0.0
-            for s in range(nk):
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                ev2, _, inf2 = pc.pc_eigs(g, kpoint(args.warmup + s), NEV, opt=o2)
-                e1.record(stream)
-                e1.synchronize()
-                ms.append(e0.elapsed_time(e1))
-                err = max(err, float(np.max(np.abs(ev2 - evals[s]) / evals[s])))
-            compare[name] = {"s_per_kpoint": float(np.mean(ms)) / 1e3, "k_points": nk,
-                             "same_k_points_as_main_leg": True, "max_rel_diff_vs_blocked_fp64": err}
+            pc.pc_eigs(g, cks[0][0], NEV, opt=o2)  # untimed: tunes this leg's launches, builds its state
+            if lockstep and KB > 1:
+                pc.pc_eigs_multi(g, cks[0], NEV, opt=o2)
+            ms, err, nk = [], 0.0, 0
+            for s in range(nc):
+                for j in (range(1) if lockstep else range(KB)):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    if lockstep:
+                        ev2, _ = solve(g, cks[s], o2)
+                    else:
+                        e_, _, _ = pc.pc_eigs(g, cks[s][j], NEV, opt=o2)
+                        ev2 = e_[None, :]
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                    ref = evals[s] if lockstep else evals[s][j:j + 1]
+                    err = max(err, float(np.max(np.abs(ev2 - ref) / ref)))
+                    nk += ev2.shape[0]
+            compare[name] = {"s_per_kpoint": float(np.sum(ms)) / 1e3 / nk, "k_points": nk,
+                             "lockstep": bool(lockstep and KB > 1), "same_k_points_as_main_leg": True,
+                             "max_rel_diff_vs_main_leg": err}
         compare["main_leg_s_per_kpoint"] = value
+        compare["lockstep_speedup_vs_one_at_a_time"] = compare["one_at_a_time_fp64"]["s_per_kpoint"] / value
         compare["blocked_speedup_vs_full_space"] = compare["full_space_fp64"]["s_per_kpoint"] / value
+        compare["mixed_vs_fp64"] = compare["mixed"]["s_per_kpoint"] / value
         compare["mixed_speedup_vs_fp64_full_space"] = (compare["full_space_fp64"]["s_per_kpoint"] /
                                                         compare["mixed"]["s_per_kpoint"])
 
@@ -790,7 +823,7 @@ def main():
             dist.destroy_process_group()
         return
     # block-apply equivalents per k-point (FP64 applies of the timed steps, counted in nodes)
-    applies_per_k = int(round(st["apply_nodes"][1] / (cell.N ** 3 / 4) / args.steps))
+    applies_per_k = int(round(st["apply_nodes"][1] / (cell.N ** 3 / 4) / (args.steps * KB)))
     cpu = None if args.no_cpu else cpu_oracle_sample(applies_per_k)
     if cpu is not None:
         cpu["apply_n160"] = cpu_oracle_apply_rate()
@@ -800,7 +833,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "N": cell.N, "bands": NEV, "tol": TOL, "blocks": 4,
-                   "k_points_per_rank": args.steps, "precision": PRECISION_FP64,
+                   "k_points_per_step": KB, "k_points_per_rank": args.steps * KB, "precision": PRECISION_FP64,
                    "l2": "512 MB buffer written between timed steps (L2 = 129 MB)"},
         "roofline": roofline,
         "apply": apply,
@@ -810,9 +843,9 @@ def main():
         "e2e": e2e,
         "gpu_launches": st["launches"],
         "clocks": clk,
-        "solver": {"pcg_iters_per_kpoint": pcg_total / args.steps,
+        "solver": {"pcg_iters_per_kpoint": pcg_total / (args.steps * KB),
                    "max_pcg_iters": max(i["max_pcg_iters"] for i in infos),
-                   "inner_solves_per_kpoint": sum(i["inner_solves"] for i in infos) / args.steps,
+                   "inner_solves_per_kpoint": sum(i["inner_solves"] for i in infos) / (args.steps * KB),
                    "block_applies_per_kpoint": applies_per_k,
                    "max_true_rel_resid": max(residuals),
                    "step_ms": step_ms},

@@ -130,6 +130,9 @@ typedef struct {
                             iterates, the stencil and the residuals stay FP64, so the solve reaches the
                             same inner_tol (the preconditioner only changes the iteration count).
                             0 = preconditioner in FP64.  Default 1 */
+    int kbatch;          /* pc_eigs_batch only: Bloch vectors of one grid solved together in lockstep
+                            (pc_eigs_multi) per work item; 0 = chosen per grid size (about 2^22 nodes
+                            of systems per launch, at most 16), 1 = one at a time.  Default 0 */
 } pc_options;
 
 /* Statistics of one pc_eigs call. */
@@ -273,12 +276,44 @@ double pc_default_sigma(const pc_grid* g);
 int pc_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_options* opt,
             double* evals, void* evecs, int* block_of, pc_eigs_info* info);
 
+/* pc_eigs at nk Bloch vectors of one grid at once (1 <= nk <= 32; the block subproblems of all
+ * of them are independent, Sec. 6.3): the grid holds one Bloch slot per vector, every
+ * (vector, parity block) pair is one space of the same shift-invert Krylov-Schur iteration, and
+ * each expansion runs one batched inner PCG, one set of Gram / update launches and one true-
+ * residual apply over all unfinished spaces, so a launch serves several Bloch vectors (each
+ * stencil item and preconditioner system carries its slot).  Results equal nk pc_eigs calls up to
+ * rounding (same start vectors, same tests).  kappas: host [nk][3].  evals: host [nk][nev];
+ * block_of: NULL or host [nk][nev]; info: NULL or nk entries -- status, zero_modes and
+ * max_rel_resid per vector; outer_iters, inner_solves, pcg_iters, max_pcg_iters and seconds are
+ * totals of the whole call, repeated in every entry.  Afterwards the grid's current Bloch vector
+ * (pc_set_k) is kappas[0:3].  nk > 1 needs a grid whose block transform runs in the library's own
+ * kernels (pc_eigs_multi_max > 1), else PC_EINVAL.  Returns PC_ENOCONV when some vector did not
+ * converge (its info status says which; the others are valid).  Synchronous. */
+int pc_eigs_multi(pc_grid* g, int nk, const double* kappas, int nev, double sigma, const pc_options* opt,
+                  double* evals, int* block_of, pc_eigs_info* info);
+
+/* Largest nk pc_eigs_multi accepts for this grid (32, or 1 when the grid's quarter-grid length
+ * N/2 has a prime factor above 16 or exceeds 96). */
+int pc_eigs_multi_max(const pc_grid* g);
+
 /* Batched apply: one launch computes y_i = (A_hat - shift_i M_hat) x_i for
  * count vectors that may belong to different parity blocks (blocks[i] in 0..3),
  * or count full-space vectors (every blocks[i] = -1).  x, y: host arrays of
  * `count` device pointers (3 n_b or 3 n elements each); shifts: host array. */
 int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const void* const* x,
                    void* const* y, const double* shifts, void* stream);
+
+/* Bloch slots: set slots 0 .. nk - 1 (1 <= nk <= 32) of the grid to the reduced Bloch vectors
+ * kappas[3 i .. 3 i + 2] (host); slot 0 becomes the current vector of pc_set_k, and the phases and
+ * preconditioner tables of every slot are rebuilt.  pc_set_k is the nk = 1 case. */
+int pc_set_k_multi(pc_grid* g, int nk, const double* kappas);
+
+/* pc_apply_batch with item i at the Bloch vector of slot kslots[i] (host; NULL = all slot 0):
+ * y_i = (A_hat(kappa_{kslots[i]}) - shift_i M_hat) x_i.  The two-pass complex128 kernels and the
+ * plane-pipelined complex64 kernel serve all slots in one launch; other launch shapes run once
+ * per run of equal slots. */
+int pc_apply_batch_k(pc_grid* g, int dtype, int count, const int* blocks, const int* kslots,
+                     const void* const* x, void* const* y, const double* shifts, void* stream);
 
 /* Allocation-free apply with inner product: y = (A_hat - shift M_hat) x on
  * block b (0..3) or the full space (-1), and *dot = Re <x, y> (x^H y), written
@@ -330,9 +365,10 @@ typedef struct {
 } pc_batch_info;
 
 /* Band solves for many (grid, Bloch vector) pairs (the batching of the parity-block method's
- * independent subproblems, Sec. 6.3): every Bloch vector is solved as pc_eigs does (four
- * blocks batched), by `workers` host threads (1..16), each with its own CUDA stream and its own
- * copy of the grid it works on, taking items largest grid first.  With opt->autotune the
+ * independent subproblems, Sec. 6.3): the Bloch vectors of each grid are cut into chunks of
+ * opt->kbatch (0 = sized per grid) and every chunk is solved as pc_eigs_multi does (all blocks
+ * of all its vectors in lockstep), by `workers` host threads (1..16), each with its own CUDA
+ * stream and its own copy of the grid it works on, taking chunks largest grid first.  With opt->autotune the
  * launch shapes of every grid size are tuned before the workers start.  opt->stream, if set,
  * is used for the tuning only.  Returns PC_OK, PC_ENOCONV when some Bloch vectors did not
  * converge (their status says which, the others are valid), or the first hard error. */

@@ -29,6 +29,7 @@ EXPORTED = [
     "pc_eigs", "pc_last_error", "pc_version", "pc_apply_batch", "pc_stats_timing", "pc_stats_reset",
     "pc_stats_get", "pc_block_apply_dot_noalloc", "pc_eig_grad", "pc_autotune", "pc_tuned_config",
     "pc_grid_clone", "pc_eigs_batch", "pc_device_status", "pc_fp64_peak", "pc_grid_create_nodewise",
+    "pc_eigs_multi", "pc_eigs_multi_max", "pc_set_k_multi", "pc_apply_batch_k",
 ]
 
 
@@ -61,7 +62,7 @@ class c_options(ctypes.Structure):
                 ("full_space", ctypes.c_int), ("block_size", ctypes.c_int), ("max_basis", ctypes.c_int),
                 ("max_restarts", ctypes.c_int), ("inner_maxit", ctypes.c_int), ("guard", ctypes.c_int),
                 ("verbose", ctypes.c_int), ("stream", ctypes.c_void_p), ("autotune", ctypes.c_int),
-                ("precond_fp32", ctypes.c_int)]
+                ("precond_fp32", ctypes.c_int), ("kbatch", ctypes.c_int)]
 
 
 class c_batch_job(ctypes.Structure):
@@ -112,6 +113,12 @@ def _load():
         "pc_default_sigma": ([vp], cd),
         "pc_eigs": ([vp, dp, ci, cd, ctypes.POINTER(c_options), dp, vp, ctypes.POINTER(ci),
                      ctypes.POINTER(c_eigs_info)], ci),
+        "pc_eigs_multi": ([vp, ci, dp, ci, cd, ctypes.POINTER(c_options), dp, ctypes.POINTER(ci),
+                           ctypes.POINTER(c_eigs_info)], ci),
+        "pc_eigs_multi_max": ([vp], ci),
+        "pc_set_k_multi": ([vp, ci, dp], ci),
+        "pc_apply_batch_k": ([vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(vp),
+                              ctypes.POINTER(vp), dp, vp], ci),
         "pc_apply_batch": ([vp, ci, ci, ctypes.POINTER(ci), ctypes.POINTER(vp), ctypes.POINTER(vp), dp, vp], ci),
         "pc_block_apply_dot_noalloc": ([vp, ci, ci, vp, vp, cd, vp, vp], ci),
         "pc_eig_grad": ([vp, ci, ci, vp, dp, dp, vp, vp, vp], ci),
@@ -320,6 +327,53 @@ def pc_eigs(g, kappa, nev, sigma=float("nan"), opt=None, evecs=None, raise_on_fa
     d = {f: getattr(info, f) for f, _ in c_eigs_info._fields_}
     d["rc"] = rc
     return ev, np.array(list(bo)), d
+
+
+def pc_eigs_multi(g, kappas, nev, sigma=float("nan"), opt=None, raise_on_fail=True):
+    """Several Bloch vectors of one grid in lockstep.  Returns (evals [nk][nev], block_of [nk][nev],
+    list of per-vector info dicts)."""
+    ks = np.ascontiguousarray(np.asarray(kappas, dtype=np.float64).reshape(-1, 3))
+    nk = ks.shape[0]
+    opt = opt if opt is not None else pc_options_default()
+    ev = np.empty((nk, int(nev)), dtype=np.float64)
+    bo = np.empty((nk, int(nev)), dtype=np.int32)
+    infos = (c_eigs_info * nk)()
+    rc = lib.pc_eigs_multi(g, nk, ks.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nev), float(sigma),
+                           ctypes.byref(opt), ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           bo.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), infos)
+    if raise_on_fail:
+        _check(rc)
+    out = []
+    for i in range(nk):
+        d = {f: getattr(infos[i], f) for f, _ in c_eigs_info._fields_}
+        d["rc"] = rc
+        out.append(d)
+    return ev, bo, out
+
+
+def pc_set_k_multi(g, kappas):
+    """Bloch slots 0 .. nk - 1 of the grid at the reduced vectors kappas ([nk][3])."""
+    ks = np.ascontiguousarray(np.asarray(kappas, dtype=np.float64).reshape(-1, 3))
+    _check(lib.pc_set_k_multi(g, ks.shape[0], ks.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+
+def pc_apply_batch_k(g, blocks, kslots, xs, ys, shifts, stream=None):
+    """pc_apply_batch with each item at the Bloch vector of its slot."""
+    n = len(blocks)
+    bl = (ctypes.c_int * n)(*[int(b) for b in blocks])
+    kl = (ctypes.c_int * n)(*[int(k) for k in kslots])
+    xp = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    yp = (ctypes.c_void_p * n)(*[_ptr(y) for y in ys])
+    sh = (ctypes.c_double * n)(*[float(v) for v in shifts])
+    _check(lib.pc_apply_batch_k(g, _dtype_code(xs[0]), n, bl, kl, xp, yp, sh, _stream(stream)))
+
+
+def pc_eigs_multi_max(g):
+    """Largest number of Bloch vectors pc_eigs_multi solves together on this grid."""
+    r = int(lib.pc_eigs_multi_max(g))
+    if r < 0:
+        _check(r)
+    return r
 
 
 def pc_apply_batch(g, blocks, xs, ys, shifts, stream=None):

@@ -218,6 +218,8 @@ static void emu_run_pipe(const StencilParams<float>& P, int block, const void* x
     std::vector<unsigned char> smem(G.total);
     typename T::Sh sh{smem.data(), &G};
     std::vector<typename T::Regs> regs(G.NC);
+    float2 eph[3];  // the item's Bloch phases
+    for (int l = 0; l < 3; ++l) eph[l] = make_float2(P.ph[l][0], P.ph[l][1]);
     const int64_t W = (int64_t)G.nt * G.Z;  // one item
     for (int cta = 0; cta < ctas; ++cta) {
         std::memset(smem.data(), 0xFF, smem.size());  // poison: reads of unwritten cells show up as NaN
@@ -248,6 +250,7 @@ static void emu_run_pipe(const StencilParams<float>& P, int block, const void* x
             S.x = static_cast<const float2*>(x);
             S.y = static_cast<float2*>(y);
             S.mat = matp.data();
+            S.ph = eph;
             S.shift = (float)shift;
             for (int kp = ks - 2; kp <= ke + 1; ++kp) seq.emplace_back((int)segs.size(), kp);
             segs.push_back(S);
@@ -343,11 +346,11 @@ static void emu_run_split(const StencilParams<R>& P, int block, const void* x, v
     const C* xv = static_cast<const C*>(x);
     for (int c = 0; c < 3; ++c)
         for (int64_t t = 0; t < G.m; ++t) T::fill_x_interior(G, xv, xe.data(), c, t);
-    for (int64_t gi = 0; gi < G.ghosts; ++gi) T::fill_x_ghost(P, G, xv, xe.data(), gi);
+    for (int64_t gi = 0; gi < G.ghosts; ++gi) T::fill_x_ghost(P.ph, G, xv, xe.data(), gi);
     R Ct[2][36];
     for (int i = 0; i < 72; ++i) Ct[i / 36][i % 36] = P.C[i / 36][i % 36];
     for (int64_t t = 0; t < G.m; ++t) T::flux_node(P, Ct, G, p12, p13, xe.data(), mat, fe.data(), t, true);
-    for (int64_t gi = 0; gi < G.ghosts; ++gi) T::fill_f_ghost(P, G, fe.data(), gi);
+    for (int64_t gi = 0; gi < G.ghosts; ++gi) T::fill_f_ghost(P.ph, G, fe.data(), gi);
     for (int64_t t = 0; t < G.m; ++t)
         T::gather_node(P, G, p12, p13, fe.data(), xv, static_cast<C*>(y), mat, (R)shift, t, true);
 }

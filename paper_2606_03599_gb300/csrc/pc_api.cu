@@ -165,10 +165,55 @@ static bool finite_all(const double* v, int n) {
 
 using namespace pc;
 
+namespace pc {
+
+// Bloch state of a reduced wave vector: phases of kappa mod 1, reduced first so that exact
+// lattice vectors give phase 0.
+static GridK make_gridk(const double kappa[3], uint64_t version) {
+    GridK k;
+    bool gamma = true;
+    for (int l = 0; l < 3; ++l) {
+        k.kappa[l] = kappa[l];
+        const double frac = kappa[l] - std::floor(kappa[l]);
+        k.phi[l] = 2.0 * M_PI * frac;
+        if (frac != 0.0) gamma = false;
+    }
+    k.gamma = gamma;
+    k.set = true;
+    k.version = version;
+    return k;
+}
+
+void slot_phases(const pc_grid* g, int slot, double ph[3][2]) {
+    for (int l = 0; l < 3; ++l) {
+        ph[l][0] = std::cos(g->ks[slot].phi[l]);
+        ph[l][1] = std::sin(g->ks[slot].phi[l]);
+    }
+}
+
+}  // namespace pc
+
 static void fill_params(pc_grid* g) {
     make_stencil_params(g->P64, g->Chat, g->rhohat, g->Ainv, g->cubic, g->N, g->k.phi, g->X, g->Y, g->Z);
     make_stencil_params(g->P32, g->Chat, g->rhohat, g->Ainv, g->cubic, g->N, g->k.phi, g->X, g->Y, g->Z);
 }
+
+namespace pc {
+
+int grid_set_kslots(pc_grid* g, int nk, const double* kappas) {
+    if (!g || !kappas) return fail(PC_EINVAL, "set_k: null argument");
+    if (nk < 1 || nk > kMaxKSlots) return fail(PC_EINVAL, "set_k: slot count out of range");
+    if (!finite_all(kappas, 3 * nk)) return fail(PC_EINVAL, "set_k: non-finite kappa");
+    const uint64_t v = g->k.version + 1;
+    for (int i = 0; i < nk; ++i) g->ks[i] = make_gridk(kappas + 3 * i, v);
+    g->k = g->ks[0];
+    g->nk = nk;
+    g->kset_version += 1;
+    fill_params(g);
+    return precond_set_k(g);
+}
+
+}  // namespace pc
 
 extern "C" {
 
@@ -421,98 +466,106 @@ int pc_grid_create_nodewise(int N, const double* C21, const double* rho, const d
 
 int pc_set_k(pc_grid* g, const double kappa[3]) {
     if (!g || !kappa) return fail(PC_EINVAL, "pc_set_k: null argument");
-    if (!finite_all(kappa, 3)) return fail(PC_EINVAL, "pc_set_k: non-finite kappa");
-    bool gamma = true;
-    for (int l = 0; l < 3; ++l) {
-        g->k.kappa[l] = kappa[l];
-        // phase of kappa mod 1, reduced first so that exact lattice vectors give phase 0
-        double frac = kappa[l] - std::floor(kappa[l]);
-        g->k.phi[l] = 2.0 * M_PI * frac;
-        if (frac != 0.0) gamma = false;
-    }
-    g->k.gamma = gamma;
-    g->k.set = true;
-    g->k.version += 1;
-    fill_params(g);
-    return precond_set_k(g);
+    return grid_set_kslots(g, 1, kappa);
 }
 
 }  // extern "C"
 
 namespace pc {
 
-// Launch one batch of stencil applies on grid g (items share the layout kind).
-int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nitems, double* dot_partials,
-               int dot_stride, cudaStream_t s, const ApplyConfig* cfg_in) {
+template <typename R>
+static StencilParams<R> params_at(const pc_grid* g, const StencilParams<R>& base, int X, int Y, int Z, int slot) {
+    StencilParams<R> P = base;
+    P.X = X;
+    P.Y = Y;
+    P.Z = Z;
+    double ph[3][2];
+    slot_phases(g, slot, ph);
+    for (int l = 0; l < 3; ++l) {
+        P.ph[l][0] = (R)ph[l][0];
+        P.ph[l][1] = (R)ph[l][1];
+    }
+    return P;
+}
+
+// One launch of items whose kernel takes grid-uniform Bloch phases (all items in `slot`), or, for
+// the two-pass and plane-pipelined kernels, each item's own phases from item_ph.
+static int apply_launch(pc_grid* g, int dtype, bool full, const ApplyConfig& cfg, const ApplyItem* items,
+                        const double* item_ph, int nitems, int slot, double* dot_partials, int dot_stride,
+                        cudaStream_t s) {
     const int X = full ? g->N : g->X, Y = full ? g->N : g->Y, Z = g->Z;
-    ApplyConfig cfg = cfg_in ? *cfg_in : apply_config_for(g, full, nitems, dtype);
-    if (g->matkind == 2 && !(dtype == PC_C128 && cfg.split))
-        return fail(PC_EINVAL, "apply: a nodewise material is applied by the complex128 two-pass kernels only");
-    void* th = timing_enabled() ? timing_begin(s) : nullptr;
-    int rc;
     if (cfg.split) {
         const size_t need = split_scratch_bytes(X, Y, Z, nitems, dtype);
-        rc = PC_OK;
         if (g->split_bytes < need) {
             // grown outside stream capture: the first launch of every batch shape runs eagerly
             cudaFree(g->d_split);
             g->d_split = nullptr;
             g->split_bytes = 0;
             cudaError_t e = cudaMalloc(&g->d_split, need);
-            if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(split apply scratch)");
-            else g->split_bytes = need;
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(split apply scratch)");
+            g->split_bytes = need;
         }
-        if (rc == PC_OK && dtype == PC_C64) {
-            StencilParams<float> P = g->P32;
-            P.X = X;
-            P.Y = Y;
-            P.Z = Z;
-            rc = launch_apply_split_f32(full, g->cubic, g->matkind, P, items, nitems, g->d_split, g->split_bytes,
-                                        dot_partials, dot_stride, s);
-        } else if (rc == PC_OK) {
-            StencilParams<double> P = g->P64;
-            P.X = X;
-            P.Y = Y;
-            P.Z = Z;
-            rc = launch_apply_split_f64(full, g->cubic, g->matkind, P, items, nitems, g->d_split, g->split_bytes,
-                                        dot_partials, dot_stride, s);
-        }
-    } else if (dtype == PC_C64 && cfg.pipe) {
-        StencilParams<float> P = g->P32;
-        P.X = X;
-        P.Y = Y;
-        P.Z = Z;
+        if (dtype == PC_C64)
+            return launch_apply_split_f32(full, g->cubic, g->matkind, params_at(g, g->P32, X, Y, Z, slot), items,
+                                          item_ph, nitems, g->d_split, g->split_bytes, dot_partials, dot_stride, s);
+        return launch_apply_split_f64(full, g->cubic, g->matkind, params_at(g, g->P64, X, Y, Z, slot), items,
+                                      item_ph, nitems, g->d_split, g->split_bytes, dot_partials, dot_stride, s);
+    }
+    if (dtype == PC_C64 && (cfg.pipe || cfg.row)) {
         std::vector<const void*> mats(nitems);
         for (int i = 0; i < nitems; ++i) mats[i] = items[i].block >= 0 ? g->d_mat_row[items[i].block] : nullptr;
-        rc = launch_apply_pipe_f32(g->cubic, g->matkind, P, items, mats.data(), nitems, cfg.ctas, dot_partials,
-                                   dot_stride, g->d_err, s);
-    } else if (dtype == PC_C64 && cfg.row) {
-        StencilParams<float> P = g->P32;
-        P.X = X;
-        P.Y = Y;
-        P.Z = Z;
-        std::vector<const void*> mats(nitems);
-        for (int i = 0; i < nitems; ++i) mats[i] = items[i].block >= 0 ? g->d_mat_row[items[i].block] : nullptr;
-        rc = launch_apply_row_f32(g->cubic, g->matkind, P, items, mats.data(), nitems, cfg.ctas, dot_partials,
-                                  dot_stride, g->d_err, s);
-    } else if (dtype == PC_C64) {
-        StencilParams<float> P = g->P32;
-        P.X = X;
-        P.Y = Y;
-        P.Z = Z;
-        rc = cfg.tma ? launch_apply_tma_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz,
-                                            dot_partials, dot_stride, g->d_err, s)
-                     : launch_apply_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
-                                        dot_stride, s);
+        const StencilParams<float> P = params_at(g, g->P32, X, Y, Z, slot);
+        if (cfg.pipe)
+            return launch_apply_pipe_f32(g->cubic, g->matkind, P, items, item_ph, mats.data(), nitems, cfg.ctas,
+                                         dot_partials, dot_stride, g->d_err, s);
+        return launch_apply_row_f32(g->cubic, g->matkind, P, items, mats.data(), nitems, cfg.ctas, dot_partials,
+                                    dot_stride, g->d_err, s);
+    }
+    if (dtype == PC_C64) {
+        const StencilParams<float> P = params_at(g, g->P32, X, Y, Z, slot);
+        return cfg.tma ? launch_apply_tma_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz,
+                                              dot_partials, dot_stride, g->d_err, s)
+                       : launch_apply_f32(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz,
+                                          dot_partials, dot_stride, s);
+    }
+    const StencilParams<double> P = params_at(g, g->P64, X, Y, Z, slot);
+    return cfg.tma ? launch_apply_tma_f64(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz,
+                                          dot_partials, dot_stride, g->d_err, s)
+                   : launch_apply_f64(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
+                                      dot_stride, s);
+}
+
+// Launch one batch of stencil applies on grid g (items share the layout kind; each item at the
+// Bloch vector of its slot).  The two-pass and plane-pipelined kernels take every item's phases,
+// so one launch serves several Bloch vectors; the other kernels run once per run of equal slots.
+int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nitems, double* dot_partials,
+               int dot_stride, cudaStream_t s, const ApplyConfig* cfg_in) {
+    const int X = full ? g->N : g->X, Y = full ? g->N : g->Y, Z = g->Z;
+    ApplyConfig cfg = cfg_in ? *cfg_in : apply_config_for(g, full, nitems, dtype);
+    if (g->matkind == 2 && !(dtype == PC_C128 && cfg.split))
+        return fail(PC_EINVAL, "apply: a nodewise material is applied by the complex128 two-pass kernels only");
+    bool uniform = true;
+    std::vector<double> iph((size_t)6 * std::max(nitems, 1));
+    for (int i = 0; i < nitems; ++i) {
+        const int ks = items[i].kslot;
+        if (ks < 0 || ks >= g->nk) return fail(PC_EINVAL, "apply: item Bloch slot out of range");
+        if (ks != items[0].kslot) uniform = false;
+        slot_phases(g, ks, reinterpret_cast<double(*)[2]>(&iph[(size_t)6 * i]));
+    }
+    void* th = timing_enabled() ? timing_begin(s) : nullptr;
+    int rc = PC_OK;
+    const bool per_item = cfg.split || (dtype == PC_C64 && cfg.pipe);
+    if (uniform || per_item) {
+        rc = apply_launch(g, dtype, full, cfg, items, iph.data(), nitems, nitems ? items[0].kslot : 0, dot_partials,
+                          dot_stride, s);
     } else {
-        StencilParams<double> P = g->P64;
-        P.X = X;
-        P.Y = Y;
-        P.Z = Z;
-        rc = cfg.tma ? launch_apply_tma_f64(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz,
-                                            dot_partials, dot_stride, g->d_err, s)
-                     : launch_apply_f64(full, g->cubic, g->matkind, cfg.shape, P, items, nitems, cfg.tz, dot_partials,
-                                        dot_stride, s);
+        for (int i = 0; i < nitems && rc == PC_OK;) {
+            int j = i;
+            while (j < nitems && items[j].kslot == items[i].kslot) ++j;
+            rc = apply_launch(g, dtype, full, cfg, items + i, iph.data() + 6 * i, j - i, items[i].kslot, dot_partials,
+                              dot_stride, s);
+            i = j;
+        }
     }
     if (th) timing_end(th, s, dtype == PC_C64 ? 0 : 1, (double)nitems * X * Y * Z);
     return rc;
@@ -553,8 +606,8 @@ int pc_block_apply_many(pc_grid* g, int block, int dtype, int count, const void*
     return grid_apply(g, dtype, block < 0, items.data(), count, nullptr, 0, (cudaStream_t)stream, nullptr);
 }
 
-int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const void* const* x, void* const* y,
-                   const double* shifts, void* stream) {
+int pc_apply_batch_k(pc_grid* g, int dtype, int count, const int* blocks, const int* kslots, const void* const* x,
+                     void* const* y, const double* shifts, void* stream) {
     if (!g || !blocks || !x || !y || !shifts) return fail(PC_EINVAL, "pc_apply_batch: null argument");
     if (dtype != PC_C64 && dtype != PC_C128) return fail(PC_EINVAL, "pc_apply_batch: bad dtype");
     if (count < 0) return fail(PC_EINVAL, "pc_apply_batch: negative count");
@@ -567,6 +620,8 @@ int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const vo
             return fail(PC_EINVAL, "pc_apply_batch: blocks must all be 0..3 or all -1");
         if (!x[i] || !y[i] || x[i] == y[i]) return fail(PC_EINVAL, "pc_apply_batch: null or aliased vector");
         if (!std::isfinite(shifts[i])) return fail(PC_EINVAL, "pc_apply_batch: non-finite shift");
+        if (kslots && (kslots[i] < 0 || kslots[i] >= g->nk))
+            return fail(PC_EINVAL, "pc_apply_batch: Bloch slot out of range");
         items[i].x = x[i];
         items[i].y = y[i];
         items[i].mat = grid_mat(g, blocks[i]);
@@ -574,8 +629,19 @@ int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const vo
         items[i].block = blocks[i];
         items[i].dot_slot = -1;
         items[i].skip = nullptr;
+        items[i].kslot = kslots ? kslots[i] : 0;
     }
     return grid_apply(g, dtype, full, items.data(), count, nullptr, 0, (cudaStream_t)stream, nullptr);
+}
+
+int pc_apply_batch(pc_grid* g, int dtype, int count, const int* blocks, const void* const* x, void* const* y,
+                   const double* shifts, void* stream) {
+    return pc_apply_batch_k(g, dtype, count, blocks, nullptr, x, y, shifts, stream);
+}
+
+int pc_set_k_multi(pc_grid* g, int nk, const double* kappas) {
+    if (!g || !kappas) return fail(PC_EINVAL, "pc_set_k_multi: null argument");
+    return grid_set_kslots(g, nk, kappas);
 }
 
 int pc_device_status(pc_grid* g, void* stream) {

@@ -129,6 +129,7 @@ inline bool pipe_geom_fits(const PipeGeom& G) {
 struct PipeBatch {
     ApplyItem it[kPipeMaxItems];
     const void* mat_row[kPipeMaxItems];  // row-padded material of each item's block
+    float2 ph[kPipeMaxItems][3];         // (cos, sin) of each item's three Bloch phases
     int n;
     int* err;             // device error word (1 when a bounded wait expired)
     uint32_t wait_limit;  // mbarrier polls before a wait gives up
@@ -143,6 +144,7 @@ struct PipeSeg {
     const float2* x;
     float2* y;
     const void* mat;
+    const float2* ph;  // (cos, sin) of the item's three Bloch phases
     float shift;
 };
 
@@ -216,9 +218,10 @@ struct PipeTile {
     };
 
     // exp(i w phi_axis), w in {-1, 0, 1}
-    static PC_HD C phase_of(const StencilParams<float>& P, int axis, int w) {
+    static PC_HD C phase_of(const PipeSeg& S, int axis, int w) {
         if (w == 0) return cmk(1.f, 0.f);
-        return cmk(P.ph[axis][0], w < 0 ? -P.ph[axis][1] : P.ph[axis][1]);
+        const float2 e = S.ph[axis];
+        return cmk(e.x, w < 0 ? -e.y : e.y);
     }
     static PC_HD int plane_wrap(const PipeGeom& G, int kp) { return kp < 0 ? -1 : (kp >= G.Z ? 1 : 0); }
     // Bloch phase of slot row s of a plane with plane wrap wk (rows -1 and Y of the grid are wrapped)
@@ -226,7 +229,7 @@ struct PipeTile {
                                 C& ph) {
         const int wr = (s == 0 && S.top) ? -1 : ((s == S.Vt + 1 && S.bot) ? 1 : 0);
         if (wr == 0 && wk == 0) return false;
-        ph = cmul(phase_of(P, 1, wr), phase_of(P, 2, wk));
+        ph = cmul(phase_of(S, 1, wr), phase_of(S, 2, wk));
         return true;
     }
 
@@ -284,7 +287,7 @@ struct PipeTile {
             C ph;
             bool need = row_phase(P, G, S, s, wk, ph);
             if (wa) {
-                ph = need ? cmul(ph, phase_of(P, 0, -1)) : phase_of(P, 0, -1);
+                ph = need ? cmul(ph, phase_of(S, 0, -1)) : phase_of(S, 0, -1);
                 need = true;
             }
             if (need) {
@@ -507,7 +510,7 @@ struct PipeTile {
         int ca = r.a + i0;
         const bool wa = ca >= X;
         if (wa) ca -= X;
-        const C pha = phase_of(P, 0, 1);
+        const C pha = phase_of(S, 0, 1);
         const float4* fa4 = sh.fA(buf);
         const float2* fb2 = sh.fB(buf);
         const bool fin = p >= S.ks && p < S.ke, start = kf + 1 >= S.ks && kf + 1 < S.ke;

@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(XC > 0 ? (XC * TC + 31) / 32 * 32 + 32 : kPipe
         S.x = static_cast<const float2*>(it.x);
         S.y = static_cast<float2*>(it.y);
         S.mat = B.mat_row[item];
+        S.ph = B.ph[item];
         S.shift = (float)it.shift;
         S.top = S.b0 == 0;
         S.bot = S.b0 + S.Vt == G.Y;
@@ -286,8 +287,9 @@ inline bool pipe_packed() {
 }
 
 template <bool CUBIC, int MATK, int XC, int TC, bool PK>
-static int launch_pipe_pk(const StencilParams<float>& P, const ApplyItem* items, const void* const* mats, int nitems,
-                          const PipeGeom& G, int ctas, double* dp, int ds, int* err, cudaStream_t s) {
+static int launch_pipe_pk(const StencilParams<float>& P, const ApplyItem* items, const double* iph,
+                          const void* const* mats, int nitems, const PipeGeom& G, int ctas, double* dp, int ds,
+                          int* err, cudaStream_t s) {
     auto kern = apply_pipe_kernel<CUBIC, MATK, XC, TC, PK>;
     const int smem = G.total;
     if (!pipe_geom_fits(G)) return fail(PC_EINVAL, "apply_pipe: shared memory layout exceeds 227 KB");
@@ -314,6 +316,9 @@ static int launch_pipe_pk(const StencilParams<float>& P, const ApplyItem* items,
         for (int i = 0; i < B.n; ++i) {
             B.it[i] = items[base + i];
             B.mat_row[i] = mats[base + i];
+            for (int l = 0; l < 3; ++l)
+                B.ph[i][l] = make_float2((float)iph[(size_t)6 * (base + i) + 2 * l],
+                                         (float)iph[(size_t)6 * (base + i) + 2 * l + 1]);
         }
         const int64_t W = (int64_t)B.n * G.nt * G.Z;
         kern<<<ctas, G.NC + 32, smem, s>>>(P, B, G, W, dp, ds);
@@ -326,10 +331,12 @@ static int launch_pipe_pk(const StencilParams<float>& P, const ApplyItem* items,
 }
 
 template <bool CUBIC, int MATK, int XC, int TC>
-static int launch_pipe_t(const StencilParams<float>& P, const ApplyItem* items, const void* const* mats, int nitems,
-                         const PipeGeom& G, int ctas, double* dp, int ds, int* err, cudaStream_t s) {
-    return pipe_packed() ? launch_pipe_pk<CUBIC, MATK, XC, TC, true>(P, items, mats, nitems, G, ctas, dp, ds, err, s)
-                         : launch_pipe_pk<CUBIC, MATK, XC, TC, false>(P, items, mats, nitems, G, ctas, dp, ds, err, s);
+static int launch_pipe_t(const StencilParams<float>& P, const ApplyItem* items, const double* iph,
+                         const void* const* mats, int nitems, const PipeGeom& G, int ctas, double* dp, int ds,
+                         int* err, cudaStream_t s) {
+    return pipe_packed()
+               ? launch_pipe_pk<CUBIC, MATK, XC, TC, true>(P, items, iph, mats, nitems, G, ctas, dp, ds, err, s)
+               : launch_pipe_pk<CUBIC, MATK, XC, TC, false>(P, items, iph, mats, nitems, G, ctas, dp, ds, err, s);
 }
 
 }  // namespace pc
@@ -337,7 +344,7 @@ static int launch_pipe_t(const StencilParams<float>& P, const ApplyItem* items, 
 namespace pc {
 // Launchers of the compile-time-width kernels (cubic lattice, phase ids); nonzero return = error,
 // *handled = false when the width is not one of them.
-int launch_pipe_widths(int X, const StencilParams<float>& P, const ApplyItem* items, const void* const* mats,
-                       int nitems, const PipeGeom& G, int ctas, double* dp, int ds, int* err, cudaStream_t s,
-                       bool* handled);
+int launch_pipe_widths(int X, const StencilParams<float>& P, const ApplyItem* items, const double* iph,
+                       const void* const* mats, int nitems, const PipeGeom& G, int ctas, double* dp, int ds, int* err,
+                       cudaStream_t s, bool* handled);
 }  // namespace pc

@@ -17,6 +17,7 @@ struct SplitBatch {
     ApplyItem it[kSplitMaxItems];
     C* xe[kSplitMaxItems];  // extended x of each item
     C* fe[kSplitMaxItems];  // extended fluxes of each item
+    R ph[kSplitMaxItems][3][2];  // (cos, sin) of each item's Bloch phases
     int n;
 };
 
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(kSplitThreads)
         const int nghost = gridDim.x - nint;
         for (int64_t gi = (blockIdx.x - nint) * (int64_t)kSplitThreads + threadIdx.x; gi < G.ghosts;
              gi += (int64_t)nghost * kSplitThreads)
-            T::fill_x_ghost(P, G, x, xe, gi);
+            T::fill_x_ghost(B.ph[blockIdx.z], G, x, xe, gi);
     }
 }
 
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(kSplitThreads)
     if (item_skipped(it)) return;
     for (int64_t gi = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; gi < G.ghosts;
          gi += (int64_t)gridDim.x * kSplitThreads)
-        T::fill_f_ghost(P, G, B.fe[blockIdx.y], gi);
+        T::fill_f_ghost(B.ph[blockIdx.y], G, B.fe[blockIdx.y], gi);
 }
 
 // Pass 4: outputs and optional Re<x, y> partials (one per CTA, fixed order); blockIdx.y = item.
@@ -142,7 +143,7 @@ size_t split_scratch_bytes(int X, int Y, int Z, int nitems, int dtype) {
 
 template <typename R>
 static int launch_apply_split_t(bool full, bool cubic, int matkind, const StencilParams<R>& P, const ApplyItem* items,
-                                int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s) {
+                                const double* item_ph, int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s) {
     using C = typename CT<R>::T;
     const SplitGeom G = make_split_geom(P.X, P.Y, P.Z);
     const int64_t per = split_item_elems(G);
@@ -154,6 +155,7 @@ static int launch_apply_split_t(bool full, bool cubic, int matkind, const Stenci
         if ((size_t)B.n * per * sizeof(C) > scratch_bytes) return fail(PC_EINVAL, "apply: split scratch too small");
         for (int i = 0; i < B.n; ++i) {
             B.it[i] = items[base + i];
+            for (int e = 0; e < 6; ++e) B.ph[i][e / 2][e % 2] = (R)item_ph[(size_t)6 * (base + i) + e];
             C* w = static_cast<C*>(scratch) + (int64_t)i * per;
             B.xe[i] = w;
             B.fe[i] = w + 3 * G.ne;
@@ -181,13 +183,17 @@ static int launch_apply_split_t(bool full, bool cubic, int matkind, const Stenci
 }
 
 int launch_apply_split_f64(bool full, bool cubic, int matkind, const StencilParams<double>& P, const ApplyItem* items,
-                           int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s) {
-    return launch_apply_split_t<double>(full, cubic, matkind, P, items, nitems, scratch, scratch_bytes, dp, ds, s);
+                           const double* item_ph, int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds,
+                           cudaStream_t s) {
+    return launch_apply_split_t<double>(full, cubic, matkind, P, items, item_ph, nitems, scratch, scratch_bytes, dp, ds,
+                                        s);
 }
 
 int launch_apply_split_f32(bool full, bool cubic, int matkind, const StencilParams<float>& P, const ApplyItem* items,
-                           int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s) {
-    return launch_apply_split_t<float>(full, cubic, matkind, P, items, nitems, scratch, scratch_bytes, dp, ds, s);
+                           const double* item_ph, int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds,
+                           cudaStream_t s) {
+    return launch_apply_split_t<float>(full, cubic, matkind, P, items, item_ph, nitems, scratch, scratch_bytes, dp, ds,
+                                       s);
 }
 
 }  // namespace pc

@@ -76,12 +76,14 @@ struct SplitApply {
         return (a + 1) + (int64_t)G.Xe * ((b + 1) + (int64_t)G.Ye * (k + 1));
     }
 
-    static PC_HD C phase(const StencilParams<R>& P, int wa, int wb, int wk) {
+    // exp(i (wa phi_1 + wb phi_2 + wk phi_3)), w in {-1, 0, 1}; kph[l] = (cos phi_l, sin phi_l) of
+    // the item's Bloch vector
+    static PC_HD C phase(const R (*kph)[2], int wa, int wb, int wk) {
         C ph = cmk((R)1, (R)0);
         const int w[3] = {wa, wb, wk};
 #pragma unroll
         for (int l = 0; l < 3; ++l)
-            if (w[l] != 0) ph = cmul(ph, cmk(P.ph[l][0], w[l] < 0 ? -P.ph[l][1] : P.ph[l][1]));
+            if (w[l] != 0) ph = cmul(ph, cmk(kph[l][0], w[l] < 0 ? -kph[l][1] : kph[l][1]));
         return ph;
     }
 
@@ -128,27 +130,27 @@ struct SplitApply {
     }
 
     // Pass 1, ghost cell gi (all three components): the wrapped node times its Bloch phase.
-    static PC_HD void fill_x_ghost(const StencilParams<R>& P, const SplitGeom& G, const C* x, C* xe, int64_t gi) {
+    static PC_HD void fill_x_ghost(const R (*kph)[2], const SplitGeom& G, const C* x, C* xe, int64_t gi) {
         int a, b, k, wa, wb, wk;
         ghost_cell(G, gi, a, b, k);
         const int aw = wrap1(a, G.X, wa), bw = wrap1(b, G.Y, wb), kw = wrap1(k, G.Z, wk);
         const int64_t src = aw + (int64_t)G.X * (bw + (int64_t)G.Y * kw), dst = eidx(G, a, b, k);
         PC_IDX(src, G.m);
         PC_IDX(dst, G.ne);
-        const C ph = phase(P, wa, wb, wk);
+        const C ph = phase(kph, wa, wb, wk);
 #pragma unroll
         for (int c = 0; c < 3; ++c) xe[c * G.ne + dst] = cmul(x[c * G.m + src], ph);
     }
 
     // Pass 3, ghost cell gi of the flux arrays F_0..F_3 (12 arrays).
-    static PC_HD void fill_f_ghost(const StencilParams<R>& P, const SplitGeom& G, C* fe, int64_t gi) {
+    static PC_HD void fill_f_ghost(const R (*kph)[2], const SplitGeom& G, C* fe, int64_t gi) {
         int a, b, k, wa, wb, wk;
         ghost_cell(G, gi, a, b, k);
         if (a < 0) return;  // the gather reads a in [0, X] only
         const int aw = wrap1(a, G.X, wa), bw = wrap1(b, G.Y, wb), kw = wrap1(k, G.Z, wk);
         const int64_t src = eidx(G, aw, bw, kw), dst = eidx(G, a, b, k);
         PC_IDX(src, G.ne);
-        const C ph = phase(P, wa, wb, wk);
+        const C ph = phase(kph, wa, wb, wk);
 #pragma unroll
         for (int f = 0; f < 12; ++f) fe[f * G.ne + dst] = cmul(fe[f * G.ne + src], ph);
     }

@@ -1,12 +1,15 @@
 // Batched band solves: many Bloch vectors on several grids (ragged sizes) at once.
 //
-// The four parity blocks of one Bloch vector are already solved together by pc_eigs (one
-// batched PCG over all blocks, persistent stencil launches, CUDA-graph replay of the PCG
-// chunks).  This executor adds the outer level: a pool of host worker threads, each with its
-// own CUDA stream and its own copy of the grid it is working on, takes (grid, Bloch vector)
-// items from a shared queue ordered largest grid first, so small grids fill the GPU next to
-// large ones and no grid handle is ever used by two threads.  Launch shapes are tuned once per
-// grid size before the workers start.
+// Two levels.  On the device, pc_eigs_multi solves a chunk of Bloch vectors of one grid in
+// lockstep: every (Bloch vector, parity block) pair is a space of the same Krylov-Schur
+// iteration, and one stencil launch, one preconditioner launch and one Gram launch serve all
+// unfinished spaces (each item of a launch carries its Bloch slot; the Fourier tables are per
+// slot).  On the host, a pool of worker threads, each with its own CUDA stream and its own copy
+// of the grid it is working on, takes (grid, chunk of Bloch vectors) items from a shared queue
+// ordered largest grid first, so small grids fill the GPU next to large ones and no grid handle
+// is ever used by two threads.  Chunks are sized so that a launch covers about 2^22 nodes of
+// systems (small grids take many Bloch vectors per chunk, the largest one).  Launch shapes are
+// tuned once per grid size before the workers start.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -85,27 +88,37 @@ extern "C" int pc_eigs_batch(pc_batch_job* jobs, int njobs, const pc_options* op
     }
     if (workers < 1) workers = 1;
     if (workers > 16) workers = 16;
-    if (workers > total) workers = (int)std::max<int64_t>(1, total);
     auto t0 = std::chrono::steady_clock::now();
 
-    // work items, largest grids first (k order kept within a grid)
+    // work items (chunks of Bloch vectors of one grid), largest grids first (k order kept)
     struct Item {
-        int job, k;
+        int job, k, nk;
+    };
+    const bool full = opt.full_space != 0;
+    const int bs = std::max(1, std::min(opt.block_size, 16));
+    const int nper = full ? 1 : 4;
+    auto chunk_of = [&](const pc_grid* g) {
+        const int64_t m = full ? g->n : g->nb;
+        int64_t K = opt.kbatch > 0 ? opt.kbatch : ((int64_t)1 << 22) / std::max<int64_t>(1, (int64_t)bs * nper * m);
+        K = std::max<int64_t>(1, std::min<int64_t>(K, opt.kbatch > 0 ? kMaxKSlots : 16));
+        return (int)std::min<int64_t>(K, pc_eigs_multi_max(g));
     };
     std::vector<Item> items;
-    for (int j = 0; j < njobs; ++j)
-        for (int k = 0; k < jobs[j].nk; ++k) items.push_back({j, k});
+    for (int j = 0; j < njobs; ++j) {
+        const int K = chunk_of(jobs[j].grid);
+        for (int k = 0; k < jobs[j].nk; k += K) items.push_back({j, k, std::min(K, jobs[j].nk - k)});
+    }
     std::stable_sort(items.begin(), items.end(),
                      [&](const Item& a, const Item& b) { return jobs[a.job].grid->n > jobs[b.job].grid->n; });
 
     // tune the launch shapes of every grid size once, before the workers compete for the GPU
+    if (workers > (int)items.size()) workers = (int)std::max<size_t>(1, items.size());
     if (opt.autotune) {
         for (int j = 0; j < njobs; ++j) {
             if (jobs[j].nk == 0) continue;
             pc_grid* g = jobs[j].grid;
             PC_TRY(pc_set_k(g, jobs[j].kappas));
-            const bool full = opt.full_space != 0;
-            const int nsys = std::max(1, std::min(opt.block_size, 16)) * (full ? 1 : 4);
+            const int nsys = bs * nper * std::min(chunk_of(g), jobs[j].nk);
             const bool mixed = opt.precision == PC_PREC_MIXED;
             PC_TRY(autotune_layout(g, mixed ? PC_C64 : PC_C128, full, nsys, (cudaStream_t)opt.stream, 0));
             if (mixed) PC_TRY(autotune_layout(g, PC_C128, full, nsys, (cudaStream_t)opt.stream, 0));
@@ -150,20 +163,28 @@ extern "C" int pc_eigs_batch(pc_batch_job* jobs, int njobs, const pc_options* op
                 }
                 cur_job = it.job;
             }
-            pc_eigs_info inf;
-            std::memset(&inf, 0, sizeof(inf));
-            int rc = pc_eigs(clone, J.kappas + 3 * it.k, J.nev, J.sigma, &o, J.evals + (size_t)it.k * J.nev, nullptr,
-                             J.block_of ? J.block_of + (size_t)it.k * J.nev : nullptr, &inf);
-            if (J.status) J.status[it.k] = rc;
+            std::vector<pc_eigs_info> inf(it.nk);
+            std::memset(inf.data(), 0, sizeof(pc_eigs_info) * it.nk);
+            int rc = pc_eigs_multi(clone, it.nk, J.kappas + 3 * it.k, J.nev, J.sigma, &o,
+                                   J.evals + (size_t)it.k * J.nev,
+                                   J.block_of ? J.block_of + (size_t)it.k * J.nev : nullptr, inf.data());
+            const bool soft = rc == PC_OK || rc == PC_ENOCONV;  // per Bloch vector statuses are valid
+            int nfail = 0;
+            for (int q = 0; q < it.nk; ++q) {
+                const int st = soft ? inf[q].status : rc;
+                if (J.status) J.status[it.k + q] = st;
+                if (st != PC_OK) ++nfail;
+            }
             if (rc != PC_OK) {
-                failed.fetch_add(1);
+                failed.fetch_add(nfail);
                 std::lock_guard<std::mutex> lk(mu);
                 if (first_msg.empty()) first_msg = pc_last_error();
                 if (rc != PC_ENOCONV && rc != PC_EBREAKDOWN) hard = rc;
             }
-            pcg.fetch_add(inf.pcg_iters);
+            pcg.fetch_add(inf[0].pcg_iters);
             std::lock_guard<std::mutex> lk(mu);
-            if (std::isfinite(inf.max_rel_resid)) max_res = std::max(max_res, inf.max_rel_resid);
+            for (int q = 0; q < it.nk; ++q)
+                if (std::isfinite(inf[q].max_rel_resid)) max_res = std::max(max_res, inf[q].max_rel_resid);
         }
         if (clone) pc_grid_destroy(clone);
         cudaStreamSynchronize(s);

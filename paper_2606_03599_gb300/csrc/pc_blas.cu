@@ -183,6 +183,164 @@ int launch_gram_rb(const double2* A, int rows, const double2* B, int cols, int64
     return PC_OK;
 }
 
+// ---------------------------------------------------------------- batched forms (several spaces)
+// The outer loop runs the same product for every active space of a solve (the four parity blocks
+// times the Bloch vectors solved together); one launch serves them all, job j in blockIdx.z.
+constexpr int kMaxJobs = 64;
+
+struct GramBatch {
+    GramJob j[kMaxJobs];
+    int64_t off[kMaxJobs + 1];  // prefix sums of the jobs' result entries
+    int n;
+};
+
+template <int RB, int MATK>
+__global__ void __launch_bounds__(kGramThreads)
+    ts_gram_batch_kernel(const __grid_constant__ GramBatch B, int64_t m, double rho0, double drho, int ngc,
+                         int nchunk, double* __restrict__ part) {
+    constexpr int CB = kGramCB;
+    const GramJob& J = B.j[blockIdx.z];
+    const int rows = J.rows, cols = J.cols;
+    const int rg = blockIdx.y / ngc, cg = blockIdx.y % ngc;
+    const int i0 = rg * RB, j0 = cg * CB;
+    if (i0 >= rows || j0 >= cols) return;  // this job has fewer register blocks than the launch
+    const double2* __restrict__ A = J.A;
+    const double2* __restrict__ Bm = J.B;
+    const void* __restrict__ mat = J.mat;
+    const int64_t vs = 3 * m;
+    const int64_t t0 = (int64_t)blockIdx.x * m / nchunk, t1 = (int64_t)(blockIdx.x + 1) * m / nchunk;
+    double ar[RB][CB], ai[RB][CB];
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int j = 0; j < CB; ++j) ar[i][j] = ai[i][j] = 0.0;
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += kGramThreads) {
+        const double w = node_weight<MATK>(mat, t, m, rho0, drho);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int64_t e = c * m + t;
+            double2 b[CB];
+#pragma unroll
+            for (int j = 0; j < CB; ++j) {
+                b[j] = (j0 + j < cols) ? Bm[(int64_t)(j0 + j) * vs + e] : make_double2(0.0, 0.0);
+                if (MATK >= 0) b[j] = make_double2(w * b[j].x, w * b[j].y);
+            }
+#pragma unroll
+            for (int i = 0; i < RB; ++i) {
+                if (i0 + i < rows) {
+                    const double2 a = A[(int64_t)(i0 + i) * vs + e];
+#pragma unroll
+                    for (int j = 0; j < CB; ++j) {  // conj(a) b
+                        ar[i][j] = fma(a.x, b[j].x, fma(a.y, b[j].y, ar[i][j]));
+                        ai[i][j] = fma(a.x, b[j].y, fma(-a.y, b[j].x, ai[i][j]));
+                    }
+                }
+            }
+        }
+    }
+    constexpr int NV = RB * CB * 2;
+    __shared__ double red[kGramThreads / 32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < RB; ++i)
+#pragma unroll
+        for (int j = 0; j < CB; ++j) {
+            double vr = ar[i][j], vi = ai[i][j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                vr += __shfl_down_sync(0xffffffffu, vr, o);
+                vi += __shfl_down_sync(0xffffffffu, vi, o);
+            }
+            if (lane == 0) {
+                red[warp][(i * CB + j) * 2 + 0] = vr;
+                red[warp][(i * CB + j) * 2 + 1] = vi;
+            }
+        }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        const int v = threadIdx.x, ij = v >> 1, ri = v & 1;
+        const int gi = i0 + ij / CB, gj = j0 + ij % CB;
+        if (gi < rows && gj < cols) {
+            double s = 0.0;
+            for (int q = 0; q < kGramThreads / 32; ++q) s += red[q][v];
+            part[((B.off[blockIdx.z] + gi + (int64_t)gj * rows) * 2 + ri) * nchunk + blockIdx.x] = s;
+        }
+    }
+}
+
+// Entry e of the concatenated results (job order) = fixed-order sum of its chunk partials.
+__global__ void ts_gram_batch_reduce(const __grid_constant__ GramBatch B, const double* __restrict__ part,
+                                     int nchunk) {
+    const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= B.off[B.n]) return;
+    double re = 0.0, im = 0.0;
+    for (int c = lane; c < nchunk; c += 32) {
+        re += part[(e * 2 + 0) * nchunk + c];
+        im += part[(e * 2 + 1) * nchunk + c];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+        int j = 0;
+        while (e >= B.off[j + 1]) ++j;
+        B.j[j].out[e - B.off[j]] = make_double2(re, im);
+    }
+}
+
+struct UpdateBatch {
+    UpdateJob j[kMaxJobs];
+    int n;
+};
+
+template <int CB>
+__global__ void __launch_bounds__(256)
+    ts_update_batch_kernel(const __grid_constant__ UpdateBatch U, int64_t vs) {
+    extern __shared__ double2 hs[];  // [k][CB]
+    const UpdateJob& J = U.j[blockIdx.z];
+    const int k = J.k, cols = J.cols;
+    const int j0 = blockIdx.y * CB;
+    if (j0 >= cols) return;
+    const double2* __restrict__ h = J.h;
+    for (int q = threadIdx.x; q < k * CB; q += blockDim.x) {
+        const int kk = q / CB, j = q % CB;
+        hs[q] = (j0 + j < cols) ? h[kk + (int64_t)(j0 + j) * k] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const double2* __restrict__ A = J.A;
+    double2* __restrict__ C = J.C;
+    const double alpha = J.alpha, beta = J.beta;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
+        double cr[CB], ci[CB];
+#pragma unroll
+        for (int j = 0; j < CB; ++j) cr[j] = ci[j] = 0.0;
+        for (int kk = 0; kk < k; ++kk) {
+            const double2 a = A[(int64_t)kk * vs + e];
+#pragma unroll
+            for (int j = 0; j < CB; ++j) {
+                const double2 hv = hs[kk * CB + j];
+                cr[j] = fma(a.x, hv.x, fma(-a.y, hv.y, cr[j]));
+                ci[j] = fma(a.x, hv.y, fma(a.y, hv.x, ci[j]));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CB; ++j) {
+            if (j0 + j >= cols) continue;
+            double2* cp = C + (int64_t)(j0 + j) * vs + e;
+            double2 o = make_double2(alpha * cr[j], alpha * ci[j]);
+            if (beta != 0.0) {
+                const double2 cv = *cp;
+                o.x = fma(beta, cv.x, o.x);
+                o.y = fma(beta, cv.y, o.y);
+            }
+            *cp = o;
+        }
+    }
+}
+
 }  // namespace
 
 int ts_gram(const double2* A, int rows, const double2* B, int cols, int64_t m, const void* mat, int matkind,
@@ -240,6 +398,87 @@ int ts_update(const double2* A, int k, const double2* d_h, int cols, double2* C,
         ts_update_kernel<4><<<dim3((unsigned)gx, ngc), 256, smem, s>>>(A, k, d_h, cols, C, vs, alpha, beta);
     note_launch();
     PC_CUDA_TRY(cudaGetLastError());
+    return PC_OK;
+}
+
+int ts_gram_batch(const GramJob* jobs, int njobs, int64_t m, int matkind, double rho0, double rho1, double* d_part,
+                  size_t part_cap, cudaStream_t s) {
+    for (int base = 0; base < njobs; base += kMaxJobs) {
+        GramBatch B;
+        B.n = 0;
+        B.off[0] = 0;
+        int maxr = 0, maxc = 0;
+        bool weighted = false;
+        for (int i = base; i < njobs && B.n < kMaxJobs; ++i) {
+            const GramJob& J = jobs[i];
+            if (J.rows <= 0 || J.cols <= 0) continue;
+            if (!J.A || !J.B || !J.out) return fail(PC_EINVAL, "ts_gram_batch: bad job");
+            if (B.n > 0 && (J.mat != nullptr) != weighted) return fail(PC_EINVAL, "ts_gram_batch: mixed weights");
+            weighted = J.mat != nullptr;
+            B.j[B.n] = J;
+            B.off[B.n + 1] = B.off[B.n] + (int64_t)J.rows * J.cols;
+            ++B.n;
+            maxr = std::max(maxr, J.rows);
+            maxc = std::max(maxc, J.cols);
+        }
+        if (B.n == 0) continue;
+        const int RB = maxr <= 2 ? 2 : (maxr <= 4 ? 4 : 8);
+        const int nrg = (maxr + RB - 1) / RB, ngc = (maxc + kGramCB - 1) / kGramCB;
+        const int64_t entries = B.off[B.n];
+        int64_t nchunk = (2LL * device_sm_count() + (int64_t)nrg * ngc * B.n - 1) / ((int64_t)nrg * ngc * B.n);
+        nchunk = std::min<int64_t>(nchunk, std::max<int64_t>(1, m / 512));
+        nchunk = std::min<int64_t>(nchunk, (int64_t)(part_cap / (2 * entries)));
+        if (nchunk < 1) return fail(PC_EINVAL, "ts_gram_batch: partial-sum scratch too small");
+        const dim3 grid((unsigned)nchunk, nrg * ngc, B.n);
+        const double drho = rho1 - rho0;
+        const int mk = weighted ? matkind : -1;
+#define PC_GRAM_B(RBV, MKV) \
+    ts_gram_batch_kernel<RBV, MKV><<<grid, kGramThreads, 0, s>>>(B, m, rho0, drho, ngc, (int)nchunk, d_part)
+#define PC_GRAM_MK(RBV)                  \
+    if (mk < 0) PC_GRAM_B(RBV, -1);      \
+    else if (mk == 0) PC_GRAM_B(RBV, 0); \
+    else if (mk == 2) PC_GRAM_B(RBV, 2); \
+    else PC_GRAM_B(RBV, 1);
+        if (RB == 2) { PC_GRAM_MK(2) }
+        else if (RB == 4) { PC_GRAM_MK(4) }
+        else { PC_GRAM_MK(8) }
+#undef PC_GRAM_MK
+#undef PC_GRAM_B
+        note_launch();
+        ts_gram_batch_reduce<<<(unsigned)((entries + 7) / 8), 256, 0, s>>>(B, d_part, (int)nchunk);
+        note_launch();
+        PC_CUDA_TRY(cudaGetLastError());
+    }
+    return PC_OK;
+}
+
+int ts_update_batch(const UpdateJob* jobs, int njobs, int64_t vs, cudaStream_t s) {
+    for (int base = 0; base < njobs; base += kMaxJobs) {
+        UpdateBatch U;
+        U.n = 0;
+        int maxk = 0, maxc = 0;
+        for (int i = base; i < njobs && U.n < kMaxJobs; ++i) {
+            const UpdateJob& J = jobs[i];
+            if (J.cols <= 0) continue;
+            if (J.k <= 0 || !J.A || !J.h || !J.C) return fail(PC_EINVAL, "ts_update_batch: bad job");
+            U.j[U.n++] = J;
+            maxk = std::max(maxk, J.k);
+            maxc = std::max(maxc, J.cols);
+        }
+        if (U.n == 0) continue;
+        const int CB = maxc <= 2 ? 2 : 4;
+        const size_t smem = sizeof(double2) * (size_t)maxk * CB;
+        if (smem > 48 * 1024) return fail(PC_EINVAL, "ts_update_batch: too many basis columns");
+        const int ngc = (maxc + CB - 1) / CB;
+        int64_t gx = (vs + 255) / 256;
+        gx = std::min<int64_t>(gx, std::max<int64_t>(1, 8LL * device_sm_count() / ((int64_t)ngc * U.n)));
+        if (CB == 2)
+            ts_update_batch_kernel<2><<<dim3((unsigned)gx, ngc, U.n), 256, smem, s>>>(U, vs);
+        else
+            ts_update_batch_kernel<4><<<dim3((unsigned)gx, ngc, U.n), 256, smem, s>>>(U, vs);
+        note_launch();
+        PC_CUDA_TRY(cudaGetLastError());
+    }
     return PC_OK;
 }
 

@@ -206,7 +206,8 @@ template <int N1, int N2, typename C, typename Ci>
 __global__ void __launch_bounds__(kPlaneThreads)
     bdft_plane_fwd(const Ci* __restrict__ w, C* __restrict__ W, const C* __restrict__ wn_g, const C* __restrict__ twa,
                    const C* __restrict__ twb, const C* __restrict__ twk, int n_rt, int n1, int n2, int nplanes,
-                   int64_t sys_stride_in, int64_t sys_stride_out, const int* __restrict__ skip, int conj_tw) {
+                   int64_t sys_stride_in, int64_t sys_stride_out, const int* __restrict__ skip, int conj_tw,
+                   const int* __restrict__ sys_k, int64_t tab_stride) {
     extern __shared__ __align__(16) unsigned char smem_bdft[];
     const int n = N1 > 0 ? N1 * N2 : n_rt;
     const int pp = planes_per_cta(n), nn = n * n;
@@ -227,7 +228,8 @@ __global__ void __launch_bounds__(kPlaneThreads)
             const int par = pl & 1, comp = (pl >> 1) % 3, sys = pl / 6;
             if (!(skip && skip[sys])) {
                 const int b = t / n, a = t - b * n;
-                C tw = cmul(cmul(twa[a], twb[b]), twk[kp]);
+                const int64_t to = sys_k ? (int64_t)sys_k[sys] * tab_stride : 0;
+                C tw = cmul(cmul(twa[to + a], twb[to + b]), twk[to + kp]);
                 if (conj_tw) tw = conj_c(tw);
                 v = cmul(conv_c<C>(w[sys * sys_stride_in + comp * nb + (int64_t)(2 * kp + par) * plane + t]), tw);
             }
@@ -261,7 +263,8 @@ __global__ void __launch_bounds__(kPlaneThreads)
     bdft_plane_inv(const C* __restrict__ W, Co* __restrict__ z, const Co* __restrict__ r, const C* __restrict__ wn_g,
                    const C* __restrict__ twa, const C* __restrict__ twb, const C* __restrict__ twk, int n_rt, int n1,
                    int n2, int nplanes, int64_t sys_stride_in, int64_t sys_stride_out, double scale,
-                   const int* __restrict__ skip, double* __restrict__ part, int npart) {
+                   const int* __restrict__ skip, double* __restrict__ part, int npart, const int* __restrict__ sys_k,
+                   int64_t tab_stride) {
     extern __shared__ __align__(16) unsigned char smem_bdft[];
     using R = typename RTy<C>::R;
     const int n = N1 > 0 ? N1 * N2 : n_rt;
@@ -305,7 +308,8 @@ __global__ void __launch_bounds__(kPlaneThreads)
         const int par = pl & 1, comp = (pl >> 1) % 3, sys = pl / 6;
         if (skip && skip[sys]) continue;
         const int b = t / n, a = t - b * n;
-        const C tw = conj_c(cmul(cmul(twa[a], twb[b]), twk[kp]));
+        const int64_t to = sys_k ? (int64_t)sys_k[sys] * tab_stride : 0;
+        const C tw = conj_c(cmul(cmul(twa[to + a], twb[to + b]), twk[to + kp]));
         const int64_t off = sys * sys_stride_out + comp * nb + (int64_t)(2 * kp + par) * plane + t;
         const Co v = conv_c<Co>(scale_c(sc, cmul(buf[e], tw)));
         z[off] = v;
@@ -350,7 +354,8 @@ __global__ void __launch_bounds__(kPencilThreads)
     bdft_pencil(C* __restrict__ W, C* __restrict__ out, const C* __restrict__ wn_g, const R* __restrict__ Aref,
                 const TT* __restrict__ ea, const TT* __restrict__ eb, const TT* __restrict__ eg,
                 const int* __restrict__ sys_block, const int* __restrict__ skip, int n_rt, int n1, int n2,
-                int64_t sys_stride, double shift_rho_d, double scale_d, int mode) {
+                int64_t sys_stride, double shift_rho_d, double scale_d, int mode, const int* __restrict__ sys_k,
+                int64_t tab_stride, int64_t aref_stride) {
     const int n = N1 > 0 ? N1 * N2 : n_rt;
     extern __shared__ __align__(16) unsigned char smem_bdft[];
     const int PT = pencil_tile(n);
@@ -365,6 +370,13 @@ __global__ void __launch_bounds__(kPencilThreads)
     if (skip && skip[sys]) return;
     const int b = sys_block[sys];
     const int p12 = b >> 1, p13 = b & 1;
+    if (sys_k) {  // this system's Bloch slot
+        const int ks = sys_k[sys];
+        ea += ks * tab_stride;
+        eb += ks * tab_stride;
+        eg += ks * tab_stride;
+        if (Aref) Aref += ks * aref_stride;
+    }
     const int p0 = tile * PT, pw = min(PT, n - p0);
     const int64_t nb = (int64_t)2 * n * n * n, plane = (int64_t)n * n;
     for (int j = threadIdx.x; j < n; j += blockDim.x) wn[j] = wn_g[j];
@@ -495,24 +507,27 @@ int allow_smem(K kern, size_t bytes) {
 template <int N1, int N2, typename C, typename V, typename TT>
 static int precond_launch(int n, int n1, int n2, int nsys, const V* r, V* z, C* W, const C* wn, const C* twa,
                           const C* twb, const C* twk, const TT* ea, const TT* eb, const TT* eg,
-                          const typename RTy<C>::R* Aref, const int* sys_block, const int* skip, double shift_rho,
-                          double scale, double* part, cudaStream_t s) {
+                          const typename RTy<C>::R* Aref, const int* sys_block, const int* sys_k, int64_t tab_stride,
+                          const int* skip, double shift_rho, double scale, double* part, cudaStream_t s) {
     using R = typename RTy<C>::R;
     const int64_t vs = (int64_t)6 * n * n * n;
+    const int64_t aref_stride = (int64_t)9 * 2 * n * n * n;
     const size_t sp = plane_smem<C>(n), sq = pencil_smem<C>(n);
     PC_TRY(allow_smem(bdft_plane_fwd<N1, N2, C, V>, sp));
     PC_TRY(allow_smem(bdft_pencil<N1, N2, C, R, TT>, sq));
     PC_TRY(allow_smem(bdft_plane_inv<N1, N2, C, V>, sp));
     const int planes = nsys * 6 * n, pctas = (planes + planes_per_cta(n) - 1) / planes_per_cta(n);
     bdft_plane_fwd<N1, N2, C, V><<<pctas, kPlaneThreads, sp, s>>>(r, W, wn, twa, twb, twk, n, n1, n2, planes, vs, vs,
-                                                               skip, 0);
+                                                               skip, 0, sys_k, tab_stride);
     note_launch();
     const int tiles = n / pencil_tile(n);
     bdft_pencil<N1, N2, C, R, TT><<<nsys * n * tiles, kPencilThreads, sq, s>>>(
-        W, nullptr, wn, Aref, ea, eb, eg, sys_block, skip, n, n1, n2, vs, shift_rho, scale, 0);
+        W, nullptr, wn, Aref, ea, eb, eg, sys_block, skip, n, n1, n2, vs, shift_rho, scale, 0, sys_k, tab_stride,
+        aref_stride);
     note_launch();
     bdft_plane_inv<N1, N2, C, V><<<pctas, kPlaneThreads, sp, s>>>(W, z, r, wn, twa, twb, twk, n, n1, n2, planes, vs,
-                                                               vs, 1.0, skip, part, bloch_dft_partials(n));
+                                                               vs, 1.0, skip, part, bloch_dft_partials(n), sys_k,
+                                                               tab_stride);
     note_launch();
     PC_CUDA_TRY(cudaGetLastError());
     return PC_OK;
@@ -532,17 +547,18 @@ static int fourier_launch(int n, int n1, int n2, int inverse, const C* in, C* ou
     const int tiles = n / pencil_tile(n);
     if (!inverse) {
         bdft_plane_fwd<N1, N2, C, C><<<pctas, kPlaneThreads, sp, s>>>(in, W, wn, twa, twb, twk, n, n1, n2, planes, vs,
-                                                                   vs, nullptr, 0);
+                                                                   vs, nullptr, 0, nullptr, 0);
         note_launch();
-        bdft_pencil<N1, N2, C, R, C><<<n * tiles, kPencilThreads, sq, s>>>(W, out, wn, nullptr, ea, eb, eg, d_block,
-                                                                        nullptr, n, n1, n2, vs, 0.0, scale, 1);
+        bdft_pencil<N1, N2, C, R, C><<<n * tiles, kPencilThreads, sq, s>>>(
+            W, out, wn, nullptr, ea, eb, eg, d_block, nullptr, n, n1, n2, vs, 0.0, scale, 1, nullptr, 0, 0);
         note_launch();
     } else {
-        bdft_pencil<N1, N2, C, R, C><<<n * tiles, kPencilThreads, sq, s>>>(W, const_cast<C*>(in), wn, nullptr, ea, eb, eg,
-                                                                        d_block, nullptr, n, n1, n2, vs, 0.0, 1.0, 2);
+        bdft_pencil<N1, N2, C, R, C><<<n * tiles, kPencilThreads, sq, s>>>(
+            W, const_cast<C*>(in), wn, nullptr, ea, eb, eg, d_block, nullptr, n, n1, n2, vs, 0.0, 1.0, 2, nullptr, 0, 0);
         note_launch();
         bdft_plane_inv<N1, N2, C, C><<<pctas, kPlaneThreads, sp, s>>>(W, out, nullptr, wn, twa, twb, twk, n, n1, n2,
-                                                                   planes, vs, vs, scale, nullptr, nullptr, 0);
+                                                                   planes, vs, vs, scale, nullptr, nullptr, 0, nullptr,
+                                                                   0);
         note_launch();
     }
     PC_CUDA_TRY(cudaGetLastError());
@@ -570,34 +586,38 @@ int bloch_dft_partials(int n) { return 6 * n; }
 
 template <typename C, typename V, typename TT>
 static int own_precond_t(int n, int nsys, const V* r, V* z, C* W, const C* wn, const C* twa, const C* twb,
-                         const C* twk, const TT* ea, const TT* eb, const TT* eg,
-                         const typename RTy<C>::R* Aref, const int* sys_block, const int* skip, double shift_rho,
-                         double scale, double* part, cudaStream_t s) {
+                         const C* twk, const TT* ea, const TT* eb, const TT* eg, const typename RTy<C>::R* Aref,
+                         const int* sys_block, const int* sys_k, int64_t tab_stride, const int* skip,
+                         double shift_rho, double scale, double* part, cudaStream_t s) {
     int n1, n2;
     if (!bloch_dft_supported(n, &n1, &n2)) return fail(PC_EINVAL, "block DFT: unsupported size");
-#define PC_DFT_CASE(A, B)                                                                                        \
-    if (n1 == A && n2 == B)                                                                                      \
-        return precond_launch<A, B>(n, n1, n2, nsys, r, z, W, wn, twa, twb, twk, ea, eb, eg, Aref, sys_block, skip, \
-                                    shift_rho, scale, part, s);
+#define PC_DFT_CASE(A, B)                                                                                   \
+    if (n1 == A && n2 == B)                                                                                 \
+        return precond_launch<A, B>(n, n1, n2, nsys, r, z, W, wn, twa, twb, twk, ea, eb, eg, Aref, sys_block, \
+                                    sys_k, tab_stride, skip, shift_rho, scale, part, s);
     PC_DFT_SIZES(PC_DFT_CASE)
 #undef PC_DFT_CASE
-    return precond_launch<0, 0>(n, n1, n2, nsys, r, z, W, wn, twa, twb, twk, ea, eb, eg, Aref, sys_block, skip,
-                                shift_rho, scale, part, s);
+    return precond_launch<0, 0>(n, n1, n2, nsys, r, z, W, wn, twa, twb, twk, ea, eb, eg, Aref, sys_block, sys_k,
+                                tab_stride, skip, shift_rho, scale, part, s);
 }
 
 int own_precond(int n, int wdt, int vdt, int nsys, const void* r, void* z, void* W, const Precond* P,
-                const int* sys_block, const int* skip, double shift_rho, double scale, double* part, cudaStream_t s) {
+                const int* sys_block, const int* sys_k, const int* skip, double shift_rho, double scale,
+                double* part, cudaStream_t s) {
+    const int64_t ts = P->tab_len;
     if (wdt == PC_C64 && vdt == PC_C64)
         return own_precond_t<float2, float2, float2>(n, nsys, (const float2*)r, (float2*)z, (float2*)W, P->wn32,
                                                      P->twa32, P->twb32, P->twk32, P->ea32, P->eb32, P->egh32,
-                                                     P->d_Aref32, sys_block, skip, shift_rho, scale, part, s);
+                                                     P->d_Aref32, sys_block, sys_k, ts, skip, shift_rho, scale, part,
+                                                     s);
     if (wdt == PC_C64 && vdt == PC_C128)
         return own_precond_t<float2, double2, float2>(n, nsys, (const double2*)r, (double2*)z, (float2*)W, P->wn32,
                                                       P->twa32, P->twb32, P->twk32, P->ea32, P->eb32, P->egh32,
-                                                      P->d_Aref32, sys_block, skip, shift_rho, scale, part, s);
+                                                      P->d_Aref32, sys_block, sys_k, ts, skip, shift_rho, scale, part,
+                                                      s);
     return own_precond_t<double2, double2, double2>(n, nsys, (const double2*)r, (double2*)z, (double2*)W, P->wn,
                                                     P->twa, P->twb, P->twk, P->ea, P->eb, P->egh, P->d_Aref,
-                                                    sys_block, skip, shift_rho, scale, part, s);
+                                                    sys_block, sys_k, ts, skip, shift_rho, scale, part, s);
 }
 
 // Block transform of one vector of block b: forward (what = T^H w, modes [comp][r < 2n][q][p]) or
@@ -617,12 +637,14 @@ static int own_fourier_t(int n, int inverse, const C* in, C* out, C* W, const C*
 }
 
 int own_block_fourier(int n, int dtype, int inverse, const void* in, void* out, void* W, const Precond* P,
-                      const int* d_block, double scale, cudaStream_t s) {
+                      const int* d_block, int kslot, double scale, cudaStream_t s) {
+    const size_t o = (size_t)kslot * P->tab_len;  // the slot's tables
     if (dtype == PC_C64)
-        return own_fourier_t<float2>(n, inverse, (const float2*)in, (float2*)out, (float2*)W, P->wn32, P->twa32,
-                                     P->twb32, P->twk32, P->ea32, P->eb32, P->egh32, d_block, scale, s);
-    return own_fourier_t<double2>(n, inverse, (const double2*)in, (double2*)out, (double2*)W, P->wn, P->twa, P->twb,
-                                  P->twk, P->ea, P->eb, P->egh, d_block, scale, s);
+        return own_fourier_t<float2>(n, inverse, (const float2*)in, (float2*)out, (float2*)W, P->wn32, P->twa32 + o,
+                                     P->twb32 + o, P->twk32 + o, P->ea32 + o, P->eb32 + o, P->egh32 + o, d_block,
+                                     scale, s);
+    return own_fourier_t<double2>(n, inverse, (const double2*)in, (double2*)out, (double2*)W, P->wn, P->twa + o,
+                                  P->twb + o, P->twk + o, P->ea + o, P->eb + o, P->egh + o, d_block, scale, s);
 }
 
 }  // namespace pc

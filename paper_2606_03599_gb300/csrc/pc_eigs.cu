@@ -251,7 +251,8 @@ static int ctas_for(int64_t n) {
 
 // ================================================================== solver context
 struct Space {
-    int block = 0;         // 0..3 or -1
+    int block = 0;          // 0..3 or -1
+    int kslot = 0;          // Bloch slot of the grid this space solves at
     int64_t m = 0, vs = 0;  // nodes, elements per vector
     double2* V = nullptr;   // basis [mcap][vs]
     int m_exp = 0;          // expanded columns
@@ -272,19 +273,20 @@ struct Eigs {
     cudaStream_t s = nullptr;
     double sigma = 0;
     int bs = 4, mmax = 32, mcap = 36;
-    std::vector<Space> sp;
+    std::vector<Space> sp;  // space (kslot, block) at index kslot * (spaces per Bloch vector) + block
     double2 *W = nullptr, *MW = nullptr, *T = nullptr, *RHS = nullptr;
     double2 *Y = nullptr, *AY = nullptr;
+    int ycols = 0;  // columns of Y and AY (Ritz candidates checked per batch)
     float* X32 = nullptr;
     float* R32 = nullptr;
     double* dpart = nullptr;
     double* dscale = nullptr;
     cd* dsmall = nullptr;  // device scratch for small GEMM results
+    size_t dsmall_cap = 0;
     double* gpart = nullptr;  // partial sums of the Gram kernels
     size_t gpart_cap = 0;
-    int ycap = 0;
     long long pcg_iters = 0;
-    int max_pcg = 0, solves = 0, expansions = 0, cholqr_single = 0;
+    int max_pcg = 0, solves = 0, expansions = 0, cholqr_single = 0, syncs = 0;
     std::vector<void*> allocs;
     ~Eigs() {
         for (void* p : allocs) cudaFree(p);
@@ -307,10 +309,23 @@ static int gram_m(Eigs& E, const Space& S, const double2* A, int rows, const dou
                    reinterpret_cast<double2*>(dh), E.gpart, E.gpart_cap, E.s);
 }
 
+static int gram_batch(Eigs& E, const std::vector<GramJob>& jobs) {
+    if (jobs.empty()) return PC_OK;
+    pc_grid* g = E.g;
+    return ts_gram_batch(jobs.data(), (int)jobs.size(), E.sp[0].m, g->matkind, g->rhohat[0], g->rhohat[1], E.gpart,
+                         E.gpart_cap, E.s);
+}
+
+static int update_batch(Eigs& E, const std::vector<UpdateJob>& jobs) {
+    if (jobs.empty()) return PC_OK;
+    return ts_update_batch(jobs.data(), (int)jobs.size(), E.sp[0].vs, E.s);
+}
+
 static int to_host(Eigs& E, const cd* d, size_t n, std::vector<cd>& out) {
     out.resize(n);
     PC_CUDA_TRY(cudaMemcpyAsync(out.data(), d, sizeof(cd) * n, cudaMemcpyDeviceToHost, E.s));
     PC_CUDA_TRY(cudaStreamSynchronize(E.s));
+    ++E.syncs;
     return PC_OK;
 }
 
@@ -335,7 +350,8 @@ static int project_null(Eigs& E, Space& S, double2* Wv, int cols) {
 
 // M-orthonormalise the cols columns of Wv in place (CholQR2); returns R (cols x cols, upper) with
 // Wv_in = Wv_out R.  Rank-deficient columns are replaced by random vectors orthogonalised against
-// V[:, 0:nv] (their R columns are set to zero).
+// V[:, 0:nv] (their R columns are set to zero).  One space at a time (start blocks and the rare
+// rank-deficient Krylov block); the expansions run the batched form in expand().
 static int cholqr2(Eigs& E, Space& S, double2* Wv, int cols, int nv, std::vector<cd>& Rtot, uint64_t seed) {
     Rtot.assign((size_t)cols * cols, cd(0, 0));
     for (int i = 0; i < cols; ++i) Rtot[i + i * cols] = 1.0;
@@ -388,14 +404,18 @@ static int cholqr2(Eigs& E, Space& S, double2* Wv, int cols, int nv, std::vector
 }
 
 // W (stacked [nsys][vs]) = Op applied to the right-hand sides RHS = M V (stacked), i.e. solves of
-// (A - sigma M) W = RHS, FP64 PCG or complex64 PCG with FP64 residual refinement.
-static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t vs) {
+// (A - sigma M) W = RHS, FP64 PCG or complex64 PCG with FP64 residual refinement.  System i is
+// in block blocks[i] at Bloch slot kslots[i]; systems with live[i] == 0 have a zero right-hand
+// side (the PCG marks them done at its start) and get no refinement apply.
+static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, const std::vector<int>& kslots,
+                    const std::vector<char>& live, int64_t vs) {
     pc_grid* g = E.g;
     const pc_options& o = *E.o;
     std::vector<PcgResult> res(nsys);
+    const int* ks = g->nk > 1 ? kslots.data() : nullptr;
     if (o.precision == PC_PREC_FP64) {
         PC_TRY(pcg_solve(g, PC_C128, nsys, blocks.data(), E.sigma, E.RHS, E.W, o.inner_tol, o.inner_maxit, res.data(),
-                         E.s, o.precond_fp32 != 0));
+                         E.s, o.precond_fp32 != 0, ks));
         for (auto& r : res) {
             E.pcg_iters += r.iters;
             E.max_pcg = std::max(E.max_pcg, r.iters);
@@ -403,7 +423,7 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t v
                 return fail(PC_EBREAKDOWN, "PCG breakdown: sigma is not below the spectrum");
             if (r.status == PC_ENAN) return fail(PC_ENAN, "PCG met NaN");
         }
-        E.solves += nsys;
+        for (int i = 0; i < nsys; ++i) E.solves += live[i] ? 1 : 0;
         return PC_OK;
     }
     // mixed precision: x = 0, res = rhs; repeat { d = PCG32(res/|res|); x += |res| d; res = rhs - (A - sigma M) x }
@@ -413,11 +433,26 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t v
     PC_CUDA_TRY(cudaMemcpyAsync(E.MW, E.RHS, sizeof(double2) * nsys * vs, cudaMemcpyDeviceToDevice, E.s));
     std::vector<double> bnorm(nsys), rnorm(nsys), part((size_t)nsys * nc);
     const double tol32 = 1e-4;
+    std::vector<ApplyItem> items;
+    for (int i = 0; i < nsys; ++i) {
+        if (!live[i]) continue;
+        ApplyItem it;
+        it.x = E.W + i * vs;
+        it.y = E.MW + i * vs;
+        it.mat = grid_mat(g, blocks[i]);
+        it.shift = E.sigma;
+        it.block = blocks[i];
+        it.dot_slot = -1;
+        it.skip = nullptr;
+        it.kslot = kslots[i];
+        items.push_back(it);
+    }
     for (int sweep = 0; sweep < 40; ++sweep) {
         sq_norms<double2><<<vg, 256, 0, E.s>>>(E.MW, vs, E.dpart, nc);
         note_launch();
         PC_CUDA_TRY(cudaMemcpyAsync(part.data(), E.dpart, sizeof(double) * nsys * nc, cudaMemcpyDeviceToHost, E.s));
         PC_CUDA_TRY(cudaStreamSynchronize(E.s));
+        ++E.syncs;
         bool all = true;
         std::vector<double> sc(nsys);
         for (int i = 0; i < nsys; ++i) {
@@ -427,13 +462,14 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t v
             if (sweep == 0) bnorm[i] = rnorm[i];
             if (rnorm[i] > o.inner_tol * bnorm[i]) all = false;
             sc[i] = rnorm[i] > 0 ? 1.0 / rnorm[i] : 0.0;
+            if (!std::isfinite(rnorm[i])) return fail(PC_ENAN, "refinement met NaN");
         }
         if (all) break;
-        if (!std::isfinite(rnorm[0])) return fail(PC_ENAN, "refinement met NaN");
         PC_CUDA_TRY(cudaMemcpyAsync(E.dscale, sc.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, E.s));
         to_c64_scaled<<<vg, 256, 0, E.s>>>(E.MW, (float2*)E.R32, E.dscale, vs);
         note_launch();
-        PC_TRY(pcg_solve(g, PC_C64, nsys, blocks.data(), E.sigma, E.R32, E.X32, tol32, o.inner_maxit, res.data(), E.s));
+        PC_TRY(pcg_solve(g, PC_C64, nsys, blocks.data(), E.sigma, E.R32, E.X32, tol32, o.inner_maxit, res.data(), E.s,
+                         false, ks));
         for (auto& r : res) {
             E.pcg_iters += r.iters;
             E.max_pcg = std::max(E.max_pcg, r.iters);
@@ -444,22 +480,12 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, int64_t v
         axpy_c64_into_c128<<<vg, 256, 0, E.s>>>((const float2*)E.X32, E.W, E.dscale, vs);
         note_launch();
         // residual in FP64: MW = RHS - (A - sigma M) W
-        std::vector<ApplyItem> items(nsys);
-        for (int i = 0; i < nsys; ++i) {
-            items[i].x = E.W + i * vs;
-            items[i].y = E.MW + i * vs;
-            items[i].mat = grid_mat(g, blocks[i]);
-            items[i].shift = E.sigma;
-            items[i].block = blocks[i];
-            items[i].dot_slot = -1;
-            items[i].skip = nullptr;
-        }
-        PC_TRY(grid_apply(g, PC_C128, blocks[0] < 0, items.data(), nsys, nullptr, 0, E.s, nullptr));
+        PC_TRY(grid_apply(g, PC_C128, blocks[0] < 0, items.data(), (int)items.size(), nullptr, 0, E.s, nullptr));
         sub_from<<<ctas_for(nsys * vs), 256, 0, E.s>>>(E.RHS, E.MW, nsys * vs);
         note_launch();
         PC_CUDA_TRY(cudaGetLastError());
     }
-    E.solves += nsys;
+    for (int i = 0; i < nsys; ++i) E.solves += live[i] ? 1 : 0;
     return PC_OK;
 }
 
@@ -472,48 +498,92 @@ static void ritz(Eigs& E, Space& S) {
     herm_eig_desc(m, Hm, S.theta, S.S);
 }
 
-// True residuals of the leading ncand Ritz pairs; returns their Rayleigh quotients and residuals.
-static int check_pairs(Eigs& E, Space& S, int ncand, std::vector<double>& lam, std::vector<double>& rel) {
+// True residuals of the leading ncand[c] Ritz pairs of spaces chk[c] (all in one apply); returns
+// their Rayleigh quotients and residuals per space.  Candidates go through Y / AY in groups of at
+// most E.ycols columns.
+static int check_pairs(Eigs& E, const std::vector<int>& chk, const std::vector<int>& ncand,
+                       std::vector<std::vector<double>>& lam, std::vector<std::vector<double>>& rel) {
     pc_grid* g = E.g;
-    const int m = S.m_exp;
-    std::vector<cd> Sk((size_t)m * ncand);
-    for (int j = 0; j < ncand; ++j)
-        for (int i = 0; i < m; ++i) Sk[i + j * m] = S.S[i + j * m];
-    PC_TRY(gemm_nn_host(E, S.V, m, Sk, ncand, E.Y, S.vs, kOne, kZero));
-    std::vector<ApplyItem> items(ncand);
-    std::vector<double> lr(ncand);
-    for (int i = 0; i < ncand; ++i) {
-        lr[i] = E.sigma + 1.0 / S.theta[i];
-        items[i].x = E.Y + i * S.vs;
-        items[i].y = E.AY + i * S.vs;
-        items[i].mat = grid_mat(g, S.block);
-        items[i].shift = lr[i];
-        items[i].block = S.block;
-        items[i].dot_slot = -1;
-        items[i].skip = nullptr;
-    }
-    PC_TRY(grid_apply(g, PC_C128, S.block < 0, items.data(), ncand, nullptr, 0, E.s, nullptr));
-    const int nc = ctas_for(S.m);
-    resid_stats<<<dim3(nc, ncand), 256, 0, E.s>>>(E.Y, E.AY, grid_mat(g, S.block), g->matkind, g->rhohat[0],
-                                                   g->rhohat[1], S.m, E.dpart, nc);
-    note_launch();
-    PC_CUDA_TRY(cudaGetLastError());
-    std::vector<double> part((size_t)ncand * 5 * nc);
-    PC_CUDA_TRY(cudaMemcpyAsync(part.data(), E.dpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, E.s));
-    PC_CUDA_TRY(cudaStreamSynchronize(E.s));
-    lam.resize(ncand);
-    rel.resize(ncand);
-    for (int i = 0; i < ncand; ++i) {
-        double q[5];
-        for (int k = 0; k < 5; ++k) {
-            double a = 0;
-            for (int c = 0; c < nc; ++c) a += part[((size_t)i * 5 + k) * nc + c];
-            q[k] = a;
+    const int64_t vs = E.sp[0].vs, m = E.sp[0].m;
+    const int nc = ctas_for(m);
+    lam.assign(chk.size(), {});
+    rel.assign(chk.size(), {});
+    size_t c0 = 0;
+    while (c0 < chk.size()) {
+        size_t c1 = c0;
+        int cols = 0;
+        while (c1 < chk.size() && (cols + ncand[c1] <= E.ycols || c1 == c0)) cols += ncand[c1++];
+        // Ritz vectors Y = V S_k of every space of the group (one upload, one launch)
+        std::vector<cd> hs;
+        std::vector<size_t> so;
+        for (size_t c = c0; c < c1; ++c) {
+            const Space& S = E.sp[chk[c]];
+            so.push_back(hs.size());
+            for (int j = 0; j < ncand[c]; ++j)
+                for (int i = 0; i < S.m_exp; ++i) hs.push_back(S.S[i + j * S.m_exp]);
         }
-        const double d = q[2] / q[3];  // Rayleigh-quotient correction of lambda
-        lam[i] = lr[i] + d;
-        const double r2 = std::max(0.0, q[0] - 2.0 * d * q[4] + d * d * q[1]);
-        rel[i] = std::sqrt(r2) / (std::fabs(lam[i]) * std::sqrt(q[1]));
+        if (hs.size() > E.dsmall_cap) return fail(PC_EINVAL, "eigensolver: small-matrix scratch too small");
+        PC_CUDA_TRY(cudaMemcpyAsync(E.dsmall, hs.data(), sizeof(cd) * hs.size(), cudaMemcpyHostToDevice, E.s));
+        std::vector<UpdateJob> uj;
+        std::vector<ApplyItem> items;
+        std::vector<double> lr;
+        int col = 0;
+        for (size_t c = c0; c < c1; ++c) {
+            const Space& S = E.sp[chk[c]];
+            uj.push_back({S.V, S.m_exp, reinterpret_cast<const double2*>(E.dsmall + so[c - c0]), ncand[c],
+                          E.Y + (int64_t)col * vs, 1.0, 0.0});
+            for (int i = 0; i < ncand[c]; ++i) {
+                ApplyItem it;
+                it.x = E.Y + (int64_t)(col + i) * vs;
+                it.y = E.AY + (int64_t)(col + i) * vs;
+                it.mat = grid_mat(g, S.block);
+                it.shift = E.sigma + 1.0 / S.theta[i];
+                it.block = S.block;
+                it.dot_slot = -1;
+                it.skip = nullptr;
+                it.kslot = S.kslot;
+                items.push_back(it);
+                lr.push_back(it.shift);
+            }
+            col += ncand[c];
+        }
+        PC_TRY(update_batch(E, uj));
+        PC_TRY(grid_apply(g, PC_C128, E.sp[chk[c0]].block < 0, items.data(), (int)items.size(), nullptr, 0, E.s,
+                          nullptr));
+        col = 0;
+        for (size_t c = c0; c < c1; ++c) {
+            const Space& S = E.sp[chk[c]];
+            resid_stats<<<dim3(nc, ncand[c]), 256, 0, E.s>>>(E.Y + (int64_t)col * vs, E.AY + (int64_t)col * vs,
+                                                             grid_mat(g, S.block), g->matkind, g->rhohat[0],
+                                                             g->rhohat[1], m, E.dpart + (size_t)col * 5 * nc, nc);
+            note_launch();
+            col += ncand[c];
+        }
+        PC_CUDA_TRY(cudaGetLastError());
+        std::vector<double> part((size_t)cols * 5 * nc);
+        PC_CUDA_TRY(cudaMemcpyAsync(part.data(), E.dpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost, E.s));
+        PC_CUDA_TRY(cudaStreamSynchronize(E.s));
+        ++E.syncs;
+        col = 0;
+        for (size_t c = c0; c < c1; ++c) {
+            auto& L = lam[c];
+            auto& Rl = rel[c];
+            L.resize(ncand[c]);
+            Rl.resize(ncand[c]);
+            for (int i = 0; i < ncand[c]; ++i, ++col) {
+                double q[5];
+                for (int k = 0; k < 5; ++k) {
+                    double a = 0;
+                    for (int t = 0; t < nc; ++t) a += part[((size_t)col * 5 + k) * nc + t];
+                    q[k] = a;
+                }
+                const double d = q[2] / q[3];  // Rayleigh-quotient correction of lambda
+                L[i] = lr[col] + d;
+                const double r2 = std::max(0.0, q[0] - 2.0 * d * q[4] + d * d * q[1]);
+                Rl[i] = std::sqrt(r2) / (std::fabs(L[i]) * std::sqrt(q[1]));
+            }
+        }
+        c0 = c1;
     }
     return PC_OK;
 }
@@ -541,46 +611,193 @@ static int restart(Eigs& E, Space& S, int keep) {
     return PC_OK;
 }
 
-// One expansion of every active space: solves, projection, CGS2, CholQR2, Rayleigh-Ritz,
-// convergence tests and restarts.
+// Upper-triangular product R_a R_b (n x n, column-major).
+static std::vector<cd> upper_mul(int n, const std::vector<cd>& Ra, const std::vector<cd>& Rb) {
+    std::vector<cd> out((size_t)n * n, cd(0, 0));
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            cd acc = 0;
+            for (int k = 0; k < n; ++k) acc += Ra[i + k * n] * Rb[k + j * n];
+            out[i + j * n] = acc;
+        }
+    return out;
+}
+
+// One expansion of every active space: solves (one batched PCG over all of them), projection off
+// the null bases, CGS2 and the first CholQR Gram (batched, one copy to the host), the CholQR update
+// (batched, a second pass only for ill-conditioned blocks), Rayleigh-Ritz, the true residuals of
+// the candidate pairs (one batched apply) and restarts.
 static int expand(Eigs& E, std::vector<int>& active, double tol) {
+    pc_grid* g = E.g;
     const int bs = E.bs, ld = E.mcap;
     const int64_t vs = E.sp[active[0]].vs;
-    const int nsys = bs * (int)active.size();
-    std::vector<int> blocks;
-    for (size_t a = 0; a < active.size(); ++a) {
-        Space& S = E.sp[active[a]];
-        PC_TRY(mass(E, S, S.V + (int64_t)S.m_exp * vs, E.RHS + (int64_t)a * bs * vs, bs));
-        for (int j = 0; j < bs; ++j) blocks.push_back(S.block);
-    }
-    PC_TRY(apply_op(E, nsys, blocks, vs));
-    E.expansions += (int)active.size();
-    for (size_t a = 0; a < active.size(); ++a) {
-        Space& S = E.sp[active[a]];
-        double2* Wv = E.W + (int64_t)a * bs * vs;
-        PC_TRY(project_null(E, S, Wv, bs));
-        const int nv = S.m_exp + bs;  // columns of V present
-        // CGS2 on the device: both passes' coefficients stay in device scratch, one copy to the host
-        std::vector<cd> h(nv * bs, cd(0, 0));
-        for (int rep = 0; rep < 2; ++rep) {
-            cd* dh = E.dsmall + (size_t)rep * nv * bs;
-            PC_TRY(gram_m(E, S, S.V, nv, Wv, bs, dh));
-            PC_TRY(ts_update(S.V, nv, reinterpret_cast<const double2*>(dh), bs, Wv, vs, -1.0, 1.0, E.s));
-        }
-        {
-            std::vector<cd> hh;
-            PC_TRY(to_host(E, E.dsmall, (size_t)2 * nv * bs, hh));
-            for (size_t i = 0; i < h.size(); ++i) h[i] = hh[i] + hh[h.size() + i];
-        }
-        std::vector<cd> R;
-        PC_TRY(cholqr2(E, S, Wv, bs, nv, R, 0xC0FFEEull + 7919ull * (uint64_t)E.expansions + (uint64_t)a));
-        const int c0 = S.m_exp;
+    const int nA = (int)active.size();
+    // Every space keeps its own systems (space i: systems i bs .. i bs + bs - 1) whether it is
+    // active or not, so the batched PCG sees the same systems at every expansion and replays one
+    // captured graph for the whole solve; finished spaces get a zero right-hand side, which the
+    // PCG retires at its start.
+    const int nS = (int)E.sp.size(), nsys = bs * nS;
+    std::vector<int> blocks(nsys), kslots(nsys);
+    std::vector<char> live(nsys, 0);
+    for (int i = 0; i < nS; ++i)
         for (int j = 0; j < bs; ++j) {
-            for (int i = 0; i < nv; ++i) S.H[i + (c0 + j) * ld] = h[i + j * nv];
-            for (int i = 0; i < bs; ++i) S.H[(nv + i) + (c0 + j) * ld] = R[i + j * bs];
+            blocks[i * bs + j] = E.sp[i].block;
+            kslots[i * bs + j] = E.sp[i].kslot;
         }
-        PC_CUDA_TRY(cudaMemcpyAsync(S.V + (int64_t)nv * vs, Wv, sizeof(double2) * bs * vs, cudaMemcpyDeviceToDevice,
-                                    E.s));
+    for (int a = 0; a < nA; ++a)
+        for (int j = 0; j < bs; ++j) live[active[a] * bs + j] = 1;
+    for (int i = 0; i < nS; ++i) {
+        Space& S = E.sp[i];
+        double2* rhs = E.RHS + (int64_t)i * bs * vs;
+        if (live[i * bs]) PC_TRY(mass(E, S, S.V + (int64_t)S.m_exp * vs, rhs, bs));
+        else PC_CUDA_TRY(cudaMemsetAsync(rhs, 0, sizeof(double2) * bs * vs, E.s));
+    }
+    PC_TRY(apply_op(E, nsys, blocks, kslots, live, vs));
+    E.expansions += nA;
+    auto Wv = [&](int a) { return E.W + (int64_t)active[a] * bs * vs; };
+    auto dsm = [&](size_t off) { return reinterpret_cast<double2*>(E.dsmall + off); };
+    // device scratch layout: [null coefficients][CGS2 coefficients, both passes][Gram][R^-1]
+    std::vector<size_t> oz(nA), oh(nA), og(nA), oi(nA);
+    size_t off = 0;
+    for (int a = 0; a < nA; ++a) {
+        oz[a] = off;
+        off += (size_t)E.sp[active[a]].nz * bs;
+    }
+    const size_t h0 = off;
+    for (int a = 0; a < nA; ++a) {
+        oh[a] = off;
+        off += (size_t)2 * (E.sp[active[a]].m_exp + bs) * bs;
+    }
+    for (int a = 0; a < nA; ++a) {
+        og[a] = off;
+        off += (size_t)bs * bs;
+    }
+    const size_t h1 = off;
+    for (int a = 0; a < nA; ++a) {
+        oi[a] = off;
+        off += (size_t)bs * bs;
+    }
+    if (off > E.dsmall_cap) return fail(PC_EINVAL, "eigensolver: small-matrix scratch too small");
+    {  // exact projection off the null bases
+        std::vector<GramJob> gj;
+        std::vector<UpdateJob> uj;
+        for (int a = 0; a < nA; ++a) {
+            Space& S = E.sp[active[a]];
+            if (S.nz == 0) continue;
+            gj.push_back({S.Z, S.nz, Wv(a), bs, grid_mat(g, S.block), dsm(oz[a])});
+            uj.push_back({S.Z, S.nz, dsm(oz[a]), bs, Wv(a), -1.0, 1.0});
+        }
+        PC_TRY(gram_batch(E, gj));
+        PC_TRY(update_batch(E, uj));
+    }
+    for (int rep = 0; rep < 2; ++rep) {  // CGS2 against the basis
+        std::vector<GramJob> gj;
+        std::vector<UpdateJob> uj;
+        for (int a = 0; a < nA; ++a) {
+            Space& S = E.sp[active[a]];
+            const int nv = S.m_exp + bs;
+            const size_t o = oh[a] + (size_t)rep * nv * bs;
+            gj.push_back({S.V, nv, Wv(a), bs, grid_mat(g, S.block), dsm(o)});
+            uj.push_back({S.V, nv, dsm(o), bs, Wv(a), -1.0, 1.0});
+        }
+        PC_TRY(gram_batch(E, gj));
+        PC_TRY(update_batch(E, uj));
+    }
+    {
+        std::vector<GramJob> gj;
+        for (int a = 0; a < nA; ++a) {
+            Space& S = E.sp[active[a]];
+            gj.push_back({Wv(a), bs, Wv(a), bs, grid_mat(g, S.block), dsm(og[a])});
+        }
+        PC_TRY(gram_batch(E, gj));
+    }
+    std::vector<cd> hh;
+    PC_TRY(to_host(E, E.dsmall + h0, h1 - h0, hh));
+    // host: CGS2 coefficients, Cholesky factors of the new blocks
+    std::vector<std::vector<cd>> hcoef(nA), Rtot(nA);
+    std::vector<char> ok(nA, 1), second(nA, 0);
+    std::vector<cd> hri(off - h1, cd(0, 0));
+    for (int a = 0; a < nA; ++a) {
+        Space& S = E.sp[active[a]];
+        const int nv = S.m_exp + bs;
+        hcoef[a].resize((size_t)nv * bs);
+        for (size_t i = 0; i < hcoef[a].size(); ++i)
+            hcoef[a][i] = hh[oh[a] - h0 + i] + hh[oh[a] - h0 + (size_t)nv * bs + i];
+        std::vector<cd> G(hh.begin() + (og[a] - h0), hh.begin() + (og[a] - h0) + (size_t)bs * bs), R, Ri;
+        if (!chol_upper(bs, G, R)) {
+            ok[a] = 0;  // rank-deficient block: the one-space path below replaces it
+            continue;
+        }
+        bool wc = true;
+        for (int j = 0; j < bs && wc; ++j)
+            for (int i = 0; i < j; ++i)
+                if (std::abs(G[i + j * bs]) > 0.1 * std::sqrt(G[i + i * bs].real() * G[j + j * bs].real())) wc = false;
+        second[a] = wc ? 0 : 1;
+        if (wc) ++E.cholqr_single;
+        upper_inverse(bs, R, Ri);
+        std::copy(Ri.begin(), Ri.end(), hri.begin() + (oi[a] - h1));
+        Rtot[a] = R;
+    }
+    PC_CUDA_TRY(cudaMemcpyAsync(E.dsmall + h1, hri.data(), sizeof(cd) * hri.size(), cudaMemcpyHostToDevice, E.s));
+    {  // V[:, nv:nv+bs] = W R^-1
+        std::vector<UpdateJob> uj;
+        for (int a = 0; a < nA; ++a) {
+            if (!ok[a]) continue;
+            Space& S = E.sp[active[a]];
+            const int nv = S.m_exp + bs;
+            uj.push_back({Wv(a), bs, dsm(oi[a]), bs, S.V + (int64_t)nv * vs, 1.0, 0.0});
+        }
+        PC_TRY(update_batch(E, uj));
+    }
+    bool any2 = false;
+    for (int a = 0; a < nA; ++a) any2 = any2 || (ok[a] && second[a]);
+    if (any2) {  // second CholQR pass of the ill-conditioned blocks
+        std::vector<GramJob> gj;
+        for (int a = 0; a < nA; ++a) {
+            if (!ok[a] || !second[a]) continue;
+            Space& S = E.sp[active[a]];
+            double2* Vn = S.V + (int64_t)(S.m_exp + bs) * vs;
+            gj.push_back({Vn, bs, Vn, bs, grid_mat(g, S.block), dsm(og[a])});
+        }
+        PC_TRY(gram_batch(E, gj));
+        PC_TRY(to_host(E, E.dsmall + h0, h1 - h0, hh));
+        std::vector<UpdateJob> uj;
+        for (int a = 0; a < nA; ++a) {
+            if (!ok[a] || !second[a]) continue;
+            std::vector<cd> G(hh.begin() + (og[a] - h0), hh.begin() + (og[a] - h0) + (size_t)bs * bs), R, Ri;
+            if (!chol_upper(bs, G, R)) return fail(PC_ENOCONV, "eigensolver: Krylov block lost rank twice");
+            upper_inverse(bs, R, Ri);
+            std::copy(Ri.begin(), Ri.end(), hri.begin() + (oi[a] - h1));
+            Rtot[a] = upper_mul(bs, R, Rtot[a]);
+            Space& S = E.sp[active[a]];
+            uj.push_back({S.V + (int64_t)(S.m_exp + bs) * vs, bs, dsm(oi[a]), bs, Wv(a), 1.0, 0.0});
+        }
+        PC_CUDA_TRY(cudaMemcpyAsync(E.dsmall + h1, hri.data(), sizeof(cd) * hri.size(), cudaMemcpyHostToDevice, E.s));
+        PC_TRY(update_batch(E, uj));
+        for (int a = 0; a < nA; ++a) {
+            if (!ok[a] || !second[a]) continue;
+            Space& S = E.sp[active[a]];
+            PC_CUDA_TRY(cudaMemcpyAsync(S.V + (int64_t)(S.m_exp + bs) * vs, Wv(a), sizeof(double2) * bs * vs,
+                                        cudaMemcpyDeviceToDevice, E.s));
+        }
+    }
+    for (int a = 0; a < nA; ++a) {  // rank-deficient blocks, one space at a time
+        if (ok[a]) continue;
+        Space& S = E.sp[active[a]];
+        const int nv = S.m_exp + bs;
+        PC_TRY(cholqr2(E, S, Wv(a), bs, nv, Rtot[a], 0xC0FFEEull + 7919ull * (uint64_t)E.expansions + (uint64_t)a));
+        PC_CUDA_TRY(cudaMemcpyAsync(S.V + (int64_t)nv * vs, Wv(a), sizeof(double2) * bs * vs,
+                                    cudaMemcpyDeviceToDevice, E.s));
+    }
+    // Rayleigh-Ritz and the candidates for a true-residual check
+    std::vector<int> chk, nck;
+    for (int a = 0; a < nA; ++a) {
+        Space& S = E.sp[active[a]];
+        const int nv = S.m_exp + bs, c0 = S.m_exp;
+        for (int j = 0; j < bs; ++j) {
+            for (int i = 0; i < nv; ++i) S.H[i + (c0 + j) * ld] = hcoef[a][i + j * nv];
+            for (int i = 0; i < bs; ++i) S.H[(nv + i) + (c0 + j) * ld] = Rtot[a][i + j * bs];
+        }
         S.m_exp += bs;
         ritz(E, S);
         // residual estimates of the Ritz pairs: || H[m:m+bs, 0:m] s_i ||
@@ -599,17 +816,27 @@ static int expand(Eigs& E, std::vector<int>& active, double tol) {
         int ntest = 0;
         while (ntest < ncand && est[ntest] < 1e-3) ++ntest;
         if (ntest >= std::min(S.target, m) && ntest > 0) {
-            std::vector<double> lam, rel;
-            PC_TRY(check_pairs(E, S, ntest, lam, rel));
+            chk.push_back(active[a]);
+            nck.push_back(ntest);
+        }
+    }
+    if (!chk.empty()) {
+        std::vector<std::vector<double>> lam, rel;
+        PC_TRY(check_pairs(E, chk, nck, lam, rel));
+        for (size_t c = 0; c < chk.size(); ++c) {
+            Space& S = E.sp[chk[c]];
             int nc = 0;
-            while (nc < ntest && rel[nc] <= tol) ++nc;
+            while (nc < nck[c] && rel[c][nc] <= tol) ++nc;
             S.nconv = nc;
             if (nc >= S.target) {
-                S.lam.assign(lam.begin(), lam.begin() + nc);
-                S.res.assign(rel.begin(), rel.begin() + nc);
+                S.lam.assign(lam[c].begin(), lam[c].begin() + nc);
+                S.res.assign(rel[c].begin(), rel[c].begin() + nc);
                 S.done = true;
             }
         }
+    }
+    for (int a = 0; a < nA; ++a) {
+        Space& S = E.sp[active[a]];
         if (!S.done && S.m_exp + bs > E.mmax) {
             int keep = std::max(S.target + bs, E.mmax / 2);
             keep = std::min(keep, S.m_exp - bs);
@@ -619,13 +846,15 @@ static int expand(Eigs& E, std::vector<int>& active, double tol) {
     return PC_OK;
 }
 
-// Null basis of a space from the vanishing symbol blocks: T_sigma (e_m (x) e_alpha), M-orthonormalised.
+// Null basis of a space from the vanishing symbol blocks of its Bloch slot:
+// T_sigma (e_m (x) e_alpha), M-orthonormalised.
 static int build_null(Eigs& E, Space& S) {
     pc_grid* g = E.g;
     Precond* P = g->pre;
     S.nz = 0;
-    if (!P || P->null_modes.empty()) return PC_OK;
-    const int nm = (int)P->null_modes.size();
+    if (!P || S.kslot >= (int)P->null_slot.size() || P->null_slot[S.kslot].empty()) return PC_OK;
+    const std::vector<int>& modes = P->null_slot[S.kslot];
+    const int nm = (int)modes.size();
     const int blocks_needed = S.block < 0 ? 4 : 1;
     S.nz = 3 * nm * blocks_needed;
     PC_TRY(E.alloc(&S.Z, (size_t)S.nz * S.vs));
@@ -639,15 +868,15 @@ static int build_null(Eigs& E, Space& S) {
             for (int a = 0; a < 3; ++a, ++col) {
                 PC_CUDA_TRY(cudaMemsetAsync(delta, 0, sizeof(double2) * 3 * nb, E.s));
                 const double2 one = make_double2(1.0, 0.0);
-                PC_CUDA_TRY(cudaMemcpyAsync(delta + a * nb + P->null_modes[mi], &one, sizeof(double2),
+                PC_CUDA_TRY(cudaMemcpyAsync(delta + a * nb + modes[mi], &one, sizeof(double2),
                                             cudaMemcpyHostToDevice, E.s));
                 PC_CUDA_TRY(cudaStreamSynchronize(E.s));
                 double2* dst = S.Z + (int64_t)col * S.vs;
                 if (S.block < 0) {
-                    PC_TRY(block_fourier(g, b, PC_C128, 1, delta, E.T + 3 * nb, E.s));
+                    PC_TRY(block_fourier(g, b, PC_C128, 1, delta, E.T + 3 * nb, E.s, S.kslot));
                     PC_TRY(launch_transfer(PC_C128, E.T + 3 * nb, dst, g->N, b, 1, E.s));
                 } else {
-                    PC_TRY(block_fourier(g, b, PC_C128, 1, delta, dst, E.s));
+                    PC_TRY(block_fourier(g, b, PC_C128, 1, delta, dst, E.s, S.kslot));
                 }
             }
     }
@@ -662,12 +891,17 @@ static int build_null(Eigs& E, Space& S) {
     return PC_OK;
 }
 
-static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_options* opt, double* evals,
-                    void* evecs, int* block_of, pc_eigs_info* info) {
+// Lowest nev eigenvalues at nk Bloch vectors of one grid, solved in lockstep: the grid's slots
+// 0 .. nk - 1 hold the vectors, every (slot, block) pair is a space, and one expansion advances all
+// unfinished spaces together.  evals / block_of: [nk][nev]; info: nk entries (see pc_eigs_multi).
+static int run_eigs(pc_grid* g, int nk, const double* kappas, int nev, double sigma, const pc_options* opt,
+                    double* evals, void* evecs, int* block_of, pc_eigs_info* info) {
     if (g->matkind == 2 && opt->precision == PC_PREC_MIXED)
         return fail(PC_EINVAL, "pc_eigs: a nodewise material is solved in PC_PREC_FP64 only");
     auto t0 = std::chrono::steady_clock::now();
-    PC_TRY(pc_set_k(g, kappa));
+    PC_TRY(grid_set_kslots(g, nk, kappas));
+    if (nk > 1 && !precond_multi_k(g))
+        return fail(PC_EINVAL, "pc_eigs_multi: this grid size solves one Bloch vector at a time");
     if (!g->sol) g->sol = new Solver();
     Eigs E;
     E.g = g;
@@ -688,7 +922,8 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
     } sg{E.s, own_stream};
 
     const bool full = opt->full_space != 0;
-    const int nspace = full ? 1 : 4;
+    const int nper = full ? 1 : 4;  // spaces per Bloch vector
+    const int nspace = nper * nk;
     const int64_t m = full ? g->n : g->nb, vs = 3 * m;
     if (opt->autotune) {
         // stencil launch shapes for the batches this solve runs (inner PCG, and the FP64 residual
@@ -701,59 +936,75 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
     const int share = full ? nev : (nev + 3) / 4;
     const int guard = std::max(0, opt->guard);
     const int ymax = std::max(E.mmax, share + guard + 16);
+    // Ritz candidates checked per batched apply: every space's at once while that stays within
+    // about 2 GB of vectors, else in groups
+    const int64_t cols_2gb = std::max<int64_t>(1, ((int64_t)2 << 30) / (vs * (int64_t)sizeof(double2)));
+    E.ycols = (int)std::max<int64_t>(ymax, std::min<int64_t>((int64_t)nspace * ymax, cols_2gb));
     PC_TRY(E.alloc(&E.W, (size_t)E.bs * nspace * vs));
     PC_TRY(E.alloc(&E.RHS, (size_t)E.bs * nspace * vs));
     PC_TRY(E.alloc(&E.MW, (size_t)std::max(E.bs * nspace, ymax) * vs));
     PC_TRY(E.alloc(&E.T, (size_t)std::max<int64_t>(E.mcap, 8) * vs));
-    PC_TRY(E.alloc(&E.Y, (size_t)ymax * vs));
-    PC_TRY(E.alloc(&E.AY, (size_t)ymax * vs));
-    PC_TRY(E.alloc(&E.dpart, (size_t)std::max(ymax * 5, E.bs * nspace) * 304));
+    PC_TRY(E.alloc(&E.Y, (size_t)E.ycols * vs));
+    PC_TRY(E.alloc(&E.AY, (size_t)std::max(E.ycols, ymax) * vs));
+    PC_TRY(E.alloc(&E.dpart, (size_t)std::max(E.ycols * 5, E.bs * nspace) * 304));
     PC_TRY(E.alloc(&E.dscale, (size_t)E.bs * nspace));
-    PC_TRY(E.alloc(&E.dsmall, (size_t)2 * E.mcap * std::max(E.mcap, ymax)));
-    E.gpart_cap = (size_t)2 * E.mcap * std::max(E.mcap, 16) * 160;
+    E.dsmall_cap = (size_t)2 * E.mcap * std::max(E.mcap, ymax) +
+                   (size_t)nspace * (2 * E.mcap * E.bs + 2 * E.bs * E.bs + 48 * E.bs) +
+                   (size_t)E.ycols * E.mcap;
+    PC_TRY(E.alloc(&E.dsmall, E.dsmall_cap));
+    E.gpart_cap = (size_t)2 * E.mcap * std::max(E.mcap, 16) * 160 + (size_t)nspace * 2 * E.mcap * E.bs * 160;
     PC_TRY(E.alloc(&E.gpart, E.gpart_cap));
     if (opt->precision == PC_PREC_MIXED) {
         PC_TRY(E.alloc(&E.X32, (size_t)2 * E.bs * nspace * vs));
         PC_TRY(E.alloc(&E.R32, (size_t)2 * E.bs * nspace * vs));
     }
-    int zero_modes = 0;
+    std::vector<int> zero_modes(nk, 0);
     for (int i = 0; i < nspace; ++i) {
         Space& S = E.sp[i];
-        S.block = full ? -1 : i;
+        const int b = i % nper;
+        S.block = full ? -1 : b;
+        S.kslot = i / nper;
         S.m = m;
         S.vs = vs;
         S.target = share + (full ? guard : 1);
         PC_TRY(E.alloc(&S.V, (size_t)E.mcap * vs));
         S.H.assign((size_t)E.mcap * E.mcap, cd(0, 0));
         PC_TRY(build_null(E, S));
-        zero_modes += S.nz;
-        fill_random<<<ctas_for(E.bs * vs), 256, 0, E.s>>>(S.V, E.bs * vs, 0x5EED0000ull + (uint64_t)(i + 1) * 1000003ull);
+        zero_modes[S.kslot] += S.nz;
+        // the start block depends on the block only, so every Bloch vector starts as a solve of
+        // that vector alone would
+        fill_random<<<ctas_for(E.bs * vs), 256, 0, E.s>>>(S.V, E.bs * vs, 0x5EED0000ull + (uint64_t)(b + 1) * 1000003ull);
         note_launch();
         PC_CUDA_TRY(cudaGetLastError());
         PC_TRY(project_null(E, S, S.V, E.bs));
         std::vector<cd> R;
-        PC_TRY(cholqr2(E, S, S.V, E.bs, 0, R, 0xABCDEFull + i));
+        PC_TRY(cholqr2(E, S, S.V, E.bs, 0, R, 0xABCDEFull + b));
         S.m_exp = 0;
     }
     const int max_exp = std::max(1, opt->max_restarts) * std::max(1, (E.mmax / E.bs));
     int status = PC_OK;
-    std::vector<double> merged;
-    std::vector<int> mblock;
+    std::vector<std::vector<double>> merged(nk);
+    std::vector<std::vector<int>> mblock(nk);
+    std::vector<char> kdone(nk, 0);
     for (int outer = 0;; ++outer) {
-        std::vector<int> active;
-        for (int i = 0; i < nspace; ++i)
-            if (!E.sp[i].done) active.push_back(i);
-        if (active.empty()) {
-            // merge and check completeness
+        // merge the Bloch vectors whose spaces have all finished; reopen the ones that may hide a
+        // lower eigenvalue
+        for (int ks = 0; ks < nk; ++ks) {
+            if (kdone[ks]) continue;
+            bool all_done = true;
+            for (int b = 0; b < nper; ++b) all_done = all_done && E.sp[ks * nper + b].done;
+            if (!all_done) continue;
             std::vector<std::pair<double, int>> all;
-            for (int i = 0; i < nspace; ++i)
-                for (double l : E.sp[i].lam) all.push_back({l, E.sp[i].block});
+            for (int b = 0; b < nper; ++b) {
+                const Space& S = E.sp[ks * nper + b];
+                for (double l : S.lam) all.push_back({l, S.block});
+            }
             std::sort(all.begin(), all.end());
             bool ok = (int)all.size() >= nev;
             if (ok && !full) {
                 const double cut = all[nev - 1].first;
-                for (int i = 0; i < nspace; ++i) {
-                    Space& S = E.sp[i];
+                for (int b = 0; b < nper; ++b) {
+                    Space& S = E.sp[ks * nper + b];
                     if (S.lam.empty() || S.lam.back() < cut) {  // may hide more eigenvalues below the cut
                         S.target += 2;
                         S.done = false;
@@ -761,22 +1012,23 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
                     }
                 }
             } else if (!ok) {
-                for (int i = 0; i < nspace; ++i) {
-                    E.sp[i].target += 2;
-                    E.sp[i].done = false;
+                for (int b = 0; b < nper; ++b) {
+                    E.sp[ks * nper + b].target += 2;
+                    E.sp[ks * nper + b].done = false;
                 }
             }
             if (ok) {
-                merged.clear();
-                mblock.clear();
                 for (int i = 0; i < nev; ++i) {
-                    merged.push_back(all[i].first);
-                    mblock.push_back(all[i].second);
+                    merged[ks].push_back(all[i].first);
+                    mblock[ks].push_back(all[i].second);
                 }
-                break;
+                kdone[ks] = 1;
             }
-            continue;
         }
+        std::vector<int> active;
+        for (int i = 0; i < nspace; ++i)
+            if (!E.sp[i].done) active.push_back(i);
+        if (active.empty()) break;  // every Bloch vector merged
         if (E.expansions >= max_exp * nspace) {
             status = PC_ENOCONV;
             break;
@@ -784,35 +1036,42 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
         PC_TRY(expand(E, active, opt->tol));
         if (opt->verbose) {
             for (int i : active)
-                std::fprintf(stderr, "[pc_eigs] space %d m=%d target=%d nconv=%d done=%d\n", E.sp[i].block,
-                             E.sp[i].m_exp, E.sp[i].target, E.sp[i].nconv, (int)E.sp[i].done);
+                std::fprintf(stderr, "[pc_eigs] k %d space %d m=%d target=%d nconv=%d done=%d\n", E.sp[i].kslot,
+                             E.sp[i].block, E.sp[i].m_exp, E.sp[i].target, E.sp[i].nconv, (int)E.sp[i].done);
         }
     }
     if (opt->verbose)
-        std::fprintf(stderr, "[pc_eigs] expansions=%d single-pass CholQR=%d solves=%d pcg=%lld\n", E.expansions,
-                     E.cholqr_single, E.solves, E.pcg_iters);
-    double maxres = 0;
+        std::fprintf(stderr, "[pc_eigs] Bloch vectors=%d expansions=%d single-pass CholQR=%d solves=%d pcg=%lld "
+                     "host syncs=%d\n", nk, E.expansions, E.cholqr_single, E.solves, E.pcg_iters, E.syncs);
     const double to_si = g->C0 / (g->rho0 * g->L * g->L);
-    if (status == PC_OK) {
-        for (int i = 0; i < nev; ++i) {
-            evals[i] = merged[i] * to_si;
-            if (block_of) block_of[i] = mblock[i];
-        }
-        for (auto& S : E.sp)
-            for (size_t i = 0; i < S.res.size(); ++i)
-                if (std::find(merged.begin(), merged.end(), S.lam[i]) != merged.end()) maxres = std::max(maxres, S.res[i]);
-    } else {
-        // best effort: whatever converged, then NaN
-        std::vector<std::pair<double, int>> all;
-        for (auto& S : E.sp)
-            for (double l : S.lam) all.push_back({l, S.block});
-        std::sort(all.begin(), all.end());
-        for (int i = 0; i < nev; ++i) {
-            evals[i] = i < (int)all.size() ? all[i].first * to_si : NAN;
-            if (block_of) block_of[i] = i < (int)all.size() ? all[i].second : -2;
+    std::vector<double> maxres(nk, 0.0);
+    for (int ks = 0; ks < nk; ++ks) {
+        double* ev = evals + (size_t)ks * nev;
+        int* bo = block_of ? block_of + (size_t)ks * nev : nullptr;
+        if (kdone[ks]) {
+            for (int i = 0; i < nev; ++i) {
+                ev[i] = merged[ks][i] * to_si;
+                if (bo) bo[i] = mblock[ks][i];
+            }
+            for (int b = 0; b < nper; ++b) {
+                const Space& S = E.sp[ks * nper + b];
+                for (size_t i = 0; i < S.res.size(); ++i)
+                    if (std::find(merged[ks].begin(), merged[ks].end(), S.lam[i]) != merged[ks].end())
+                        maxres[ks] = std::max(maxres[ks], S.res[i]);
+            }
+        } else {
+            // best effort: whatever converged, then NaN
+            std::vector<std::pair<double, int>> all;
+            for (int b = 0; b < nper; ++b)
+                for (double l : E.sp[ks * nper + b].lam) all.push_back({l, E.sp[ks * nper + b].block});
+            std::sort(all.begin(), all.end());
+            for (int i = 0; i < nev; ++i) {
+                ev[i] = i < (int)all.size() ? all[i].first * to_si : NAN;
+                if (bo) bo[i] = i < (int)all.size() ? all[i].second : -2;
+            }
         }
     }
-    if (evecs && status == PC_OK) {
+    if (evecs && nk == 1 && status == PC_OK) {
         // recompute Ritz vectors for the merged values and write them in full-space layout
         double2* out = static_cast<double2*>(evecs);
         PC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double2) * (size_t)nev * 3 * g->n, E.s));
@@ -830,7 +1089,7 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
             for (int j = 0; j < ncand; ++j) {
                 int slot = -1;
                 for (int q = 0; q < nev && slot < 0; ++q)
-                    if (!used[q] && mblock[q] == S.block && merged[q] == S.lam[j]) slot = q;
+                    if (!used[q] && mblock[0][q] == S.block && merged[0][q] == S.lam[j]) slot = q;
                 if (slot < 0) continue;
                 used[slot] = 1;
                 double2* dst = out + (size_t)slot * 3 * g->n;
@@ -845,14 +1104,18 @@ static int run_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, co
     }
     PC_CUDA_TRY(cudaStreamSynchronize(E.s));
     if (info) {
-        info->status = status;
-        info->outer_iters = E.expansions;
-        info->inner_solves = E.solves;
-        info->pcg_iters = E.pcg_iters;
-        info->max_pcg_iters = E.max_pcg;
-        info->zero_modes = zero_modes;
-        info->max_rel_resid = maxres;
-        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int ks = 0; ks < nk; ++ks) {
+            pc_eigs_info& I = info[ks];
+            I.status = kdone[ks] ? PC_OK : PC_ENOCONV;
+            I.outer_iters = E.expansions;
+            I.inner_solves = E.solves;
+            I.pcg_iters = E.pcg_iters;
+            I.max_pcg_iters = E.max_pcg;
+            I.zero_modes = zero_modes[ks];
+            I.max_rel_resid = maxres[ks];
+            I.seconds = secs;
+        }
     }
     if (status != PC_OK) return fail(status, "pc_eigs: outer iteration cap reached");
     return PC_OK;
@@ -888,6 +1151,7 @@ int pc_options_default(pc_options* o) {
     o->stream = nullptr;
     o->autotune = 0;
     o->precond_fp32 = 1;
+    o->kbatch = 0;
     return PC_OK;
 }
 
@@ -936,23 +1200,46 @@ int pc_shift_invert_pcg(pc_grid* g, int block, int dtype, double sigma, const vo
     return PC_OK;
 }
 
+static int check_eigs_args(const pc_grid* g, int nev, double sigma, const pc_options* o, const char* who) {
+    if (nev < 1) return fail(PC_EINVAL, std::string(who) + ": nev must be >= 1");
+    if (!(o->tol > 0) || !(o->inner_tol > 0)) return fail(PC_EINVAL, std::string(who) + ": tolerances must be positive");
+    if (o->precision != PC_PREC_FP64 && o->precision != PC_PREC_MIXED)
+        return fail(PC_EINVAL, std::string(who) + ": precision must be PC_PREC_FP64 or PC_PREC_MIXED");
+    if (!std::isnan(sigma) && !std::isfinite(sigma)) return fail(PC_EINVAL, std::string(who) + ": bad sigma");
+    const int64_t dim = o->full_space ? 3 * g->n : 3 * g->nb;
+    if (nev > dim / 8) return fail(PC_EINVAL, std::string(who) + ": nev too large for this grid");
+    return PC_OK;
+}
+
 int pc_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_options* opt, double* evals,
             void* evecs, int* block_of, pc_eigs_info* info) {
     if (!g || !kappa || !evals) return fail(PC_EINVAL, "pc_eigs: null argument");
-    if (nev < 1) return fail(PC_EINVAL, "pc_eigs: nev must be >= 1");
     pc_options def;
     pc_options_default(&def);
     const pc_options* o = opt ? opt : &def;
-    if (!(o->tol > 0) || !(o->inner_tol > 0)) return fail(PC_EINVAL, "pc_eigs: tolerances must be positive");
-    if (o->precision != PC_PREC_FP64 && o->precision != PC_PREC_MIXED)
-        return fail(PC_EINVAL, "pc_eigs: precision must be PC_PREC_FP64 or PC_PREC_MIXED");
-
-    if (!std::isnan(sigma) && !std::isfinite(sigma)) return fail(PC_EINVAL, "pc_eigs: bad sigma");
-    const int64_t dim = o->full_space ? 3 * g->n : 3 * g->nb;
-    if (nev > dim / 8) return fail(PC_EINVAL, "pc_eigs: nev too large for this grid");
-    const int rc = run_eigs(g, kappa, nev, sigma, o, evals, evecs, block_of, info);
+    PC_TRY(check_eigs_args(g, nev, sigma, o, "pc_eigs"));
+    const int rc = run_eigs(g, 1, kappa, nev, sigma, o, evals, evecs, block_of, info);
     const int st = grid_device_status(g, (cudaStream_t)o->stream);
     return st != PC_OK ? st : rc;
+}
+
+int pc_eigs_multi(pc_grid* g, int nk, const double* kappas, int nev, double sigma, const pc_options* opt,
+                  double* evals, int* block_of, pc_eigs_info* info) {
+    if (!g || !kappas || !evals) return fail(PC_EINVAL, "pc_eigs_multi: null argument");
+    if (nk < 1 || nk > kMaxKSlots) return fail(PC_EINVAL, "pc_eigs_multi: nk must be in 1..32");
+    pc_options def;
+    pc_options_default(&def);
+    const pc_options* o = opt ? opt : &def;
+    PC_TRY(check_eigs_args(g, nev, sigma, o, "pc_eigs_multi"));
+    const int rc = run_eigs(g, nk, kappas, nev, sigma, o, evals, nullptr, block_of, info);
+    const int st = grid_device_status(g, (cudaStream_t)o->stream);
+    return st != PC_OK ? st : rc;
+}
+
+int pc_eigs_multi_max(const pc_grid* g) {
+    if (!g) return fail(PC_EINVAL, "pc_eigs_multi_max: null grid");
+    const bool own = g->X == g->Y && g->Z == 2 * g->X && bloch_dft_supported(g->X, nullptr, nullptr);
+    return own ? kMaxKSlots : 1;
 }
 
 }  // extern "C"

@@ -374,13 +374,8 @@ int precond_create(pc_grid* g) {
     Precond* P = new Precond();
     g->pre = P;
     const int X = g->X, Y = g->Y, Z = g->Z;
-    // tables: ea[X], eb[Y], egh[Z2], egf[Z], twa[X], twb[Y], twk[Z2]
+    // tables per slot: ea[X], eb[Y], egh[Z2], egf[Z], twa[X], twb[Y], twk[Z2]
     P->tab_len = X + Y + Z / 2 + Z + X + Y + Z / 2;
-    PC_CUDA_TRY(cudaMalloc(&P->d_tabs, sizeof(double2) * P->tab_len));
-    PC_CUDA_TRY(cudaMalloc(&P->d_tabs32, sizeof(float2) * P->tab_len));
-    PC_CUDA_TRY(cudaMalloc(&P->d_Aref, sizeof(double) * 9 * g->nb));
-    PC_CUDA_TRY(cudaMalloc(&P->d_Aref32, sizeof(float) * 9 * g->nb));
-    PC_CUDA_TRY(cudaMalloc(&P->d_null, sizeof(int) * 65));
     // roots of the own quarter-grid DFT (Bloch-independent) and the block ids
     P->own_dft = g->X == g->Y && g->Z == 2 * g->X && bloch_dft_supported(g->X, nullptr, nullptr);
     {
@@ -408,31 +403,31 @@ int precond_create(pc_grid* g) {
     return PC_OK;
 }
 
-int precond_set_k(pc_grid* g) {
-    PC_TRY(precond_create(g));
+bool precond_multi_k(const pc_grid* g) { return g->pre != nullptr && g->pre->own_dft; }
+
+// Room for nk slots of tables (grown, never shrunk); the slot-0 pointers follow the allocation.
+static int precond_slots(pc_grid* g, int nk) {
     Precond* P = g->pre;
-    const int X = g->X, Y = g->Y, Z = g->Z, Z2 = Z / 2, N = g->N;
-    std::vector<double2> h(P->tab_len);
-    double2* ea = h.data();
-    double2* eb = ea + X;
-    double2* egh = eb + Y;
-    double2* egf = egh + Z2;
-    double2* twa = egf + Z;
-    double2* twb = twa + X;
-    double2* twk = twb + Y;
-    const double* phi = g->k.phi;
-    auto ex = [](double ang) { return make_double2(std::cos(ang), -std::sin(ang)); };  // e^{-i ang}
-    for (int p = 0; p < X; ++p) ea[p] = ex((phi[0] + 2 * M_PI * p) / N);
-    for (int q = 0; q < Y; ++q) eb[q] = ex((phi[1] + 2 * M_PI * q) / N);
-    for (int r = 0; r < Z2; ++r) egh[r] = ex((phi[2] + 2 * M_PI * r) / N);
-    for (int r = 0; r < Z; ++r) egf[r] = ex((phi[2] + 2 * M_PI * r) / N);
-    for (int a = 0; a < X; ++a) twa[a] = ex(a * phi[0] / X);
-    for (int b = 0; b < Y; ++b) twb[b] = ex(b * phi[1] / Y);
-    for (int k = 0; k < Z2; ++k) twk[k] = ex(k * phi[2] / Z2);
-    PC_CUDA_TRY(cudaMemcpy(P->d_tabs, h.data(), sizeof(double2) * P->tab_len, cudaMemcpyHostToDevice));
-    std::vector<float2> h32(P->tab_len);
-    for (int i = 0; i < P->tab_len; ++i) h32[i] = make_float2((float)h[i].x, (float)h[i].y);
-    PC_CUDA_TRY(cudaMemcpy(P->d_tabs32, h32.data(), sizeof(float2) * P->tab_len, cudaMemcpyHostToDevice));
+    if (P->nslots < nk) {
+        cudaFree(P->d_tabs);
+        cudaFree(P->d_tabs32);
+        cudaFree(P->d_Aref);
+        cudaFree(P->d_Aref32);
+        cudaFree(P->d_null);
+        P->d_tabs = nullptr;
+        P->d_tabs32 = nullptr;
+        P->d_Aref = nullptr;
+        P->d_Aref32 = nullptr;
+        P->d_null = nullptr;
+        P->nslots = 0;
+        PC_CUDA_TRY(cudaMalloc(&P->d_tabs, sizeof(double2) * P->tab_len * nk));
+        PC_CUDA_TRY(cudaMalloc(&P->d_tabs32, sizeof(float2) * P->tab_len * nk));
+        PC_CUDA_TRY(cudaMalloc(&P->d_Aref, sizeof(double) * 9 * g->nb * nk));
+        PC_CUDA_TRY(cudaMalloc(&P->d_Aref32, sizeof(float) * 9 * g->nb * nk));
+        PC_CUDA_TRY(cudaMalloc(&P->d_null, sizeof(int) * 65 * nk));
+        P->nslots = nk;
+    }
+    const int X = g->X, Y = g->Y, Z2 = g->Z / 2, Z = g->Z;
     P->ea32 = P->d_tabs32;
     P->eb32 = P->ea32 + X;
     P->egh32 = P->eb32 + Y;
@@ -446,21 +441,62 @@ int precond_set_k(pc_grid* g) {
     P->twa = P->egf + Z;
     P->twb = P->twa + X;
     P->twk = P->twb + Y;
+    return PC_OK;
+}
+
+// Phase tables, reference symbol and null modes of one slot.
+static int precond_fill_slot(pc_grid* g, int slot) {
+    Precond* P = g->pre;
+    const int X = g->X, Y = g->Y, Z = g->Z, Z2 = Z / 2, N = g->N;
+    const size_t to = (size_t)slot * P->tab_len;
+    std::vector<double2> h(P->tab_len);
+    double2* ea = h.data();
+    double2* eb = ea + X;
+    double2* egh = eb + Y;
+    double2* egf = egh + Z2;
+    double2* twa = egf + Z;
+    double2* twb = twa + X;
+    double2* twk = twb + Y;
+    const double* phi = g->ks[slot].phi;
+    auto ex = [](double ang) { return make_double2(std::cos(ang), -std::sin(ang)); };  // e^{-i ang}
+    for (int p = 0; p < X; ++p) ea[p] = ex((phi[0] + 2 * M_PI * p) / N);
+    for (int q = 0; q < Y; ++q) eb[q] = ex((phi[1] + 2 * M_PI * q) / N);
+    for (int r = 0; r < Z2; ++r) egh[r] = ex((phi[2] + 2 * M_PI * r) / N);
+    for (int r = 0; r < Z; ++r) egf[r] = ex((phi[2] + 2 * M_PI * r) / N);
+    for (int a = 0; a < X; ++a) twa[a] = ex(a * phi[0] / X);
+    for (int b = 0; b < Y; ++b) twb[b] = ex(b * phi[1] / Y);
+    for (int k = 0; k < Z2; ++k) twk[k] = ex(k * phi[2] / Z2);
+    PC_CUDA_TRY(cudaMemcpy(P->d_tabs + to, h.data(), sizeof(double2) * P->tab_len, cudaMemcpyHostToDevice));
+    std::vector<float2> h32(P->tab_len);
+    for (int i = 0; i < P->tab_len; ++i) h32[i] = make_float2((float)h[i].x, (float)h[i].y);
+    PC_CUDA_TRY(cudaMemcpy(P->d_tabs32 + to, h32.data(), sizeof(float2) * P->tab_len, cudaMemcpyHostToDevice));
     SymbolParams sp;
     sp.X = X; sp.Y = Y; sp.Z = Z;
     sp.q = N / 4.0;
     for (int e = 0; e < 9; ++e) sp.Ainv[e] = g->Ainv[e];
     for (int e = 0; e < 36; ++e) sp.Cref[e] = P->Cref[e];
     sp.null_tol = 1e-9;
-    PC_CUDA_TRY(cudaMemset(P->d_null, 0, sizeof(int) * 65));
-    symbol_table<<<nblocks_for(g->nb), 256>>>(P->d_Aref, P->d_null, P->d_null + 1, P->ea, P->eb, P->egf, sp);
+    double* aref = P->d_Aref + (size_t)slot * 9 * g->nb;
+    int* dn = P->d_null + (size_t)slot * 65;
+    PC_CUDA_TRY(cudaMemset(dn, 0, sizeof(int) * 65));
+    symbol_table<<<nblocks_for(g->nb), 256>>>(aref, dn, dn + 1, P->ea + to, P->eb + to, P->egf + to, sp);
     note_launch();
-    table_to_f32<<<nblocks_for(9 * g->nb), 256>>>(P->d_Aref, P->d_Aref32, 9 * g->nb);
+    table_to_f32<<<nblocks_for(9 * g->nb), 256>>>(aref, P->d_Aref32 + (size_t)slot * 9 * g->nb, 9 * g->nb);
     note_launch();
     PC_CUDA_TRY(cudaGetLastError());
     int hn[65];
-    PC_CUDA_TRY(cudaMemcpy(hn, P->d_null, sizeof(hn), cudaMemcpyDeviceToHost));
-    P->null_modes.assign(hn + 1, hn + 1 + (hn[0] < 64 ? hn[0] : 64));
+    PC_CUDA_TRY(cudaMemcpy(hn, dn, sizeof(hn), cudaMemcpyDeviceToHost));
+    P->null_slot[slot].assign(hn + 1, hn + 1 + (hn[0] < 64 ? hn[0] : 64));
+    return PC_OK;
+}
+
+int precond_set_k(pc_grid* g) {
+    PC_TRY(precond_create(g));
+    Precond* P = g->pre;
+    PC_TRY(precond_slots(g, g->nk));
+    P->null_slot.assign(g->nk, std::vector<int>());
+    for (int slot = 0; slot < g->nk; ++slot) PC_TRY(precond_fill_slot(g, slot));
+    P->null_modes = P->null_slot[0];
     return PC_OK;
 }
 
@@ -509,8 +545,10 @@ int precond_workspace(pc_grid* g, int dtype, int nsys, void** W) {
 
 // z_s = P_ref r_s for nsys systems (vectors contiguous with stride 3 n_b), blocks in d_sys_block.
 int precond_apply(pc_grid* g, int dtype, int nsys, const void* r, void* z, const int* d_sys_block,
-                  const int* d_skip, double sigma, cudaStream_t s, double* d_part, int* npart_out, bool fp32_inner) {
+                  const int* d_skip, double sigma, cudaStream_t s, double* d_part, int* npart_out, bool fp32_inner,
+                  const int* d_sys_k) {
     if (!g->pre || !g->k.set) return fail(PC_ESTATE, "preconditioner: pc_set_k first");
+    if (d_sys_k && !g->pre->own_dft) return fail(PC_EINVAL, "preconditioner: several Bloch slots need the own DFT");
     Precond* P = g->pre;
     const bool lower = dtype == PC_C128 && fp32_inner;  // complex128 vectors, complex64 transforms
     const int wdt = lower ? PC_C64 : dtype;
@@ -518,7 +556,7 @@ int precond_apply(pc_grid* g, int dtype, int nsys, const void* r, void* z, const
     PC_TRY(precond_workspace(g, wdt, nsys, &W));
     if (P->own_dft) {
         if (lower && !d_part) return fail(PC_EINVAL, "preconditioner: complex64 transforms need the fused dot");
-        PC_TRY(own_precond(g->X, wdt, dtype, nsys, r, z, W, P, d_sys_block, d_skip, -sigma * P->rho_ref,
+        PC_TRY(own_precond(g->X, wdt, dtype, nsys, r, z, W, P, d_sys_block, d_sys_k, d_skip, -sigma * P->rho_ref,
                            1.0 / (double)g->nb, d_part, s));
         if (npart_out) *npart_out = bloch_dft_partials(g->X);
         return PC_OK;
@@ -585,13 +623,17 @@ int precond_apply(pc_grid* g, int dtype, int nsys, const void* r, void* z, const
 }
 
 // Block Fourier transform of one vector (forward: what = T^H w; inverse: w = T what).
-int block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* in, void* out, cudaStream_t s) {
+int block_fourier(pc_grid* g, int block, int dtype, int inverse, const void* in, void* out, cudaStream_t s,
+                  int kslot) {
     if (!g->pre || !g->k.set) return fail(PC_ESTATE, "pc_block_fourier: pc_set_k first");
+    if (kslot < 0 || kslot >= g->nk) return fail(PC_EINVAL, "block transform: Bloch slot out of range");
     Precond* P = g->pre;
     void* W;
     PC_TRY(precond_workspace(g, dtype, 1, &W));
     const double sc = 1.0 / std::sqrt((double)g->nb);
-    if (P->own_dft) return own_block_fourier(g->X, dtype, inverse, in, out, W, P, P->d_blockids + block, sc, s);
+    if (P->own_dft)
+        return own_block_fourier(g->X, dtype, inverse, in, out, W, P, P->d_blockids + block, kslot, sc, s);
+    if (kslot != 0) return fail(PC_EINVAL, "block transform: Bloch slots other than 0 need the own DFT");
     cufftHandle plan;
     PC_TRY(get_plan(P, g, dtype, 1, &plan));
     const int64_t vs = 3 * g->nb;

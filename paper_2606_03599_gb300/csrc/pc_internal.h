@@ -54,7 +54,12 @@ struct ApplyItem {
     int block;        // 0..3 or -1 (full)
     int dot_slot;     // >= 0: write <x, y> partials to dot scratch slot, else -1
     const int* skip;  // optional device flag: nonzero = skip this item (converged system)
+    int kslot = 0;    // Bloch-vector slot of the grid (0 = the vector pc_set_k sets)
 };
+
+// Bloch-vector slots of one grid: a solve over several Bloch vectors at once keeps each vector's
+// phases and preconditioner tables in its own slot, and items of one launch may differ in slot.
+constexpr int kMaxKSlots = 32;
 
 // ---------------------------------------------------------------- kernels (launch wrappers)
 // Fused stencil apply over a batch of items sharing params and layout kind.
@@ -71,9 +76,10 @@ int launch_apply_row_f32(bool cubic, int matkind, const StencilParams<float>& P,
                          const void* const* mats, int nitems, int ctas, double* dp, int ds, int* err, cudaStream_t s);
 int row_apply_ctas(int X, int Y, int Z, int matkind, int nitems, int minseg = 12);
 // Plane-pipelined kernel (complex64 parity blocks, even X): producer warp + consumer warps.
+// item_ph: (cos, sin) of the three Bloch phases of each item ([nitems][3][2]).
 int launch_apply_pipe_f32(bool cubic, int matkind, const StencilParams<float>& P, const ApplyItem* items,
-                          const void* const* mats, int nitems, int ctas, double* dp, int ds, int* err,
-                          cudaStream_t s);
+                          const double* item_ph, const void* const* mats, int nitems, int ctas, double* dp, int ds,
+                          int* err, cudaStream_t s);
 int pipe_apply_ctas(int X, int Y, int Z, int matkind, int nitems, int minseg = 12);
 bool pipe_geom_ok(int X, int Y, int Z, int matkind);
 bool row_geom_fits(int X, int Y, int Z, int matkind);
@@ -81,10 +87,13 @@ int device_sm_count();
 int launch_apply_tma_f64(bool full, bool cubic, int matkind, int shape, const StencilParams<double>& P,
                          const ApplyItem* items, int nitems, int tz, double* dp, int ds, int* err, cudaStream_t s);
 // Two-pass complex128 apply (fluxes once per node through memory): scratch of split_scratch_bytes.
+// item_ph as for the plane-pipelined kernel (every item its own Bloch phases).
 int launch_apply_split_f64(bool full, bool cubic, int matkind, const StencilParams<double>& P, const ApplyItem* items,
-                           int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s);
+                           const double* item_ph, int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds,
+                           cudaStream_t s);
 int launch_apply_split_f32(bool full, bool cubic, int matkind, const StencilParams<float>& P, const ApplyItem* items,
-                           int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds, cudaStream_t s);
+                           const double* item_ph, int nitems, void* scratch, size_t scratch_bytes, double* dp, int ds,
+                           cudaStream_t s);
 size_t split_scratch_bytes(int X, int Y, int Z, int nitems, int dtype);
 int split_apply_ctas(int64_t m);
 
@@ -180,8 +189,13 @@ void timing_free(TimedSet* t);
 long long launch_count();
 long long apply_launch_count();
 
-// Per-k rebuild of the preconditioner tables; release of solver workspaces.
+// Per-k rebuild of the preconditioner tables (every slot in use); release of solver workspaces.
 int precond_set_k(pc_grid* g);
+// Sets slots 0 .. nk - 1 to the reduced Bloch vectors kappas[3 i .. 3 i + 2] (slot 0 also becomes
+// the grid's current vector) and rebuilds the per-slot tables.  nk in [1, kMaxKSlots].
+int grid_set_kslots(pc_grid* g, int nk, const double* kappas);
+// (cos, sin) of the three Bloch phases of a slot.
+void slot_phases(const pc_grid* g, int slot, double ph[3][2]);
 void release_solver_state(pc_grid* g);
 
 // ---------------------------------------------------------------- grid object
@@ -211,7 +225,10 @@ struct pc_grid {
     void* d_mat_blk[4] = {nullptr, nullptr, nullptr, nullptr};
     void* d_mat_row[4] = {nullptr, nullptr, nullptr, nullptr};  // block material, rows padded to 16 bytes
     int mat_pitch = 0;                                          // elements per padded row
-    pc::GridK k;
+    pc::GridK k;                    // the Bloch vector of slot 0 (pc_set_k)
+    pc::GridK ks[pc::kMaxKSlots];   // all slots; ks[0] mirrors k
+    int nk = 1;                     // slots in use
+    uint64_t kset_version = 0;      // incremented whenever any slot changes
     pc::StencilParams<double> P64;
     pc::StencilParams<float> P32;
     // scratch owned by the grid

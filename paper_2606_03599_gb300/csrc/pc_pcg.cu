@@ -54,15 +54,14 @@ __global__ void pcg_start(const C* __restrict__ b, C* __restrict__ x, C* __restr
     if (threadIdx.x == 0) part[(int64_t)s * npart + blockIdx.x] = sum;
 }
 
-// bb = sum part_bb, rz = sum part_rz; init flags.
-__global__ void pcg_start_reduce(PcgScal* sc, int* done, const double* part_bb, int sbb, int nbb,
-                                 const double* part_rz, int nrz) {
+// bb = sum part_bb; init the scalars and flags: a zero right-hand side is solved by x = 0 and
+// its system is retired before the first preconditioner application.
+__global__ void pcg_start_bb(PcgScal* sc, int* done, const double* part_bb, int sbb, int nbb) {
     const int s = blockIdx.x;
     double bb = reduce_partials(part_bb + (int64_t)s * sbb, nbb);
-    double rz = reduce_partials(part_rz + (int64_t)s * nrz, nrz);
     if (threadIdx.x == 0) {
         PcgScal v;
-        v.rz = rz;
+        v.rz = 0;
         v.pq = 0;
         v.alpha = 0;
         v.beta = 0;
@@ -72,11 +71,28 @@ __global__ void pcg_start_reduce(PcgScal* sc, int* done, const double* part_bb, 
         v.pad = 0;
         v.status = PC_OK;
         v.done = 0;
-        if (!isfinite(bb) || !isfinite(rz)) {
+        if (!isfinite(bb)) {
             v.status = PC_ENAN;
             v.done = 1;
         } else if (bb == 0.0) {
             v.done = 1;  // zero right-hand side: x = 0 is exact
+        }
+        sc[s] = v;
+        done[s] = v.done;
+    }
+}
+
+// rz = sum part_rz of the systems still running.
+__global__ void pcg_start_rz(PcgScal* sc, int* done, const double* part_rz, int nrz) {
+    const int s = blockIdx.x;
+    if (done[s]) return;
+    double rz = reduce_partials(part_rz + (int64_t)s * nrz, nrz);
+    if (threadIdx.x == 0) {
+        PcgScal v = sc[s];
+        v.rz = rz;
+        if (!isfinite(rz)) {
+            v.status = PC_ENAN;
+            v.done = 1;
         } else if (!(rz > 0.0)) {
             v.status = PC_EBREAKDOWN;  // preconditioner not positive definite
             v.done = 1;
@@ -259,11 +275,12 @@ void PcgWork::release() {
     cudaFree(sc);
     cudaFree(done);
     cudaFree(blocks);
+    cudaFree(kslots);
     cudaFreeHost(h_sc);
     R = Z = P = Q = nullptr;
     part = nullptr;
     sc = nullptr;
-    done = blocks = nullptr;
+    done = blocks = kslots = nullptr;
     h_sc = nullptr;
     cap = 0;
 }
@@ -300,6 +317,7 @@ static int pcg_work(pc_grid* g, int dtype, int nsys, int64_t vs, bool full, PcgW
     PC_CUDA_TRY(cudaMalloc(&w.sc, sizeof(PcgScal) * nsys));
     PC_CUDA_TRY(cudaMalloc(&w.done, sizeof(int) * nsys));
     PC_CUDA_TRY(cudaMalloc(&w.blocks, sizeof(int) * 4 * nsys));
+    PC_CUDA_TRY(cudaMalloc(&w.kslots, sizeof(int) * 4 * nsys));
     PC_CUDA_TRY(cudaMallocHost(&w.h_sc, sizeof(PcgScal) * nsys));
     w.cap = nsys;
     *out = &w;
@@ -307,11 +325,17 @@ static int pcg_work(pc_grid* g, int dtype, int nsys, int64_t vs, bool full, PcgW
 }
 
 template <typename C>
-static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* Bv, void* Xv,
-                       double tol, int maxit, PcgResult* res, cudaStream_t s, bool pre32) {
+static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, const int* kslots, double sigma,
+                       const void* Bv, void* Xv, double tol, int maxit, PcgResult* res, cudaStream_t s, bool pre32) {
     const bool full = blocks[0] < 0;
     for (int i = 0; i < nsys; ++i)
         if ((blocks[i] < 0) != full) return fail(PC_EINVAL, "pcg: mixing full-space and block systems");
+    bool multi_k = false;  // systems at Bloch slots other than 0
+    for (int i = 0; kslots && i < nsys; ++i) {
+        if (kslots[i] < 0 || kslots[i] >= g->nk) return fail(PC_EINVAL, "pcg: Bloch slot out of range");
+        if (kslots[i] != 0) multi_k = true;
+    }
+    if (multi_k && !precond_multi_k(g)) return fail(PC_EINVAL, "pcg: several Bloch slots need the own DFT");
     const int64_t m = full ? g->n : g->nb;
     const int64_t vs = 3 * m;
     PcgWork* w;
@@ -337,6 +361,12 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
     else
         hb.assign(blocks, blocks + nsys);
     PC_CUDA_TRY(cudaMemcpyAsync(w->blocks, hb.data(), sizeof(int) * hb.size(), cudaMemcpyHostToDevice, s));
+    std::vector<int> hk;  // Bloch slots of the preconditioner subsystems
+    for (int i = 0; multi_k && i < nsys; ++i)
+        for (int r = 0; r < (full ? 4 : 1); ++r) hk.push_back(kslots[i]);
+    if (multi_k)
+        PC_CUDA_TRY(cudaMemcpyAsync(w->kslots, hk.data(), sizeof(int) * hk.size(), cudaMemcpyHostToDevice, s));
+    const int* d_sys_k = multi_k ? w->kslots : nullptr;
     const int vc = vec_ctas(vs);
     const dim3 vgrid(vc, nsys);
 
@@ -350,12 +380,12 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
     }
     int nrz = 0;
     auto precondition = [&](const int* skip) -> int {
-        if (!full) return precond_apply(g, dtype, nsys, R, Z, w->blocks, skip, sigma, s, part_c, &nrz, flex);
+        if (!full) return precond_apply(g, dtype, nsys, R, Z, w->blocks, skip, sigma, s, part_c, &nrz, flex, d_sys_k);
         const int gb = (int)std::min<int64_t>((nsys * vs + 255) / 256, 16LL * device_sm_count());
         full_to_blocks<C><<<gb, 256, 0, s>>>(R, static_cast<C*>(Rb), g->N, nsys);
         note_launch();
         int np = 0;
-        PC_TRY(precond_apply(g, dtype, 4 * nsys, Rb, Zb, w->blocks, nullptr, sigma, s, part_c, &np, flex));
+        PC_TRY(precond_apply(g, dtype, 4 * nsys, Rb, Zb, w->blocks, nullptr, sigma, s, part_c, &np, flex, d_sys_k));
         nrz = 4 * np;  // the four block partials of a full system are contiguous
         blocks_to_full<C><<<gb, 256, 0, s>>>(static_cast<C*>(Zb), Z, g->N, nsys);
         note_launch();
@@ -365,9 +395,11 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
 
     pcg_start<C><<<vgrid, 256, 0, s>>>(B, X, R, vs, part_a, npm);
     note_launch();
+    pcg_start_bb<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, vc);
+    note_launch();
     PC_CUDA_TRY(cudaGetLastError());
-    PC_TRY(precondition(nullptr));
-    pcg_start_reduce<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, vc, part_c, nrz);
+    PC_TRY(precondition(full ? nullptr : w->done));
+    pcg_start_rz<<<nsys, 256, 0, s>>>(w->sc, w->done, part_c, nrz);
     note_launch();
     pcg_copy<C><<<vgrid, 256, 0, s>>>(Z, P, vs, w->done);
     note_launch();
@@ -383,6 +415,7 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
         items[i].block = blocks[i];
         items[i].dot_slot = i;
         items[i].skip = w->done + i;
+        items[i].kslot = kslots ? kslots[i] : 0;
     }
     const ApplyConfig cfg = apply_config_for(g, full, nsys, dtype);
     const int napc = cfg.ctas;
@@ -410,11 +443,13 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, doubl
     const bool graphs = !full && pcg_graphs_enabled() && s != nullptr && s != cudaStreamLegacy &&
                         s != cudaStreamPerThread;
     auto chunk_graph = [&]() -> int {
-        std::vector<double> key = {(double)g->k.version, (double)dtype, (double)nsys, sigma, tol2, (double)maxit,
+        std::vector<double> key = {(double)g->k.version, (double)g->kset_version, (double)dtype, (double)nsys, sigma,
+                                   tol2, (double)maxit,
                                    (double)(uintptr_t)B, (double)(uintptr_t)X, (double)(uintptr_t)g->pre->d_work,
                                    (double)(uintptr_t)w->R, (double)(timing_enabled() ? 1 : 0), (double)npm,
                                    (double)flex, (double)(uintptr_t)g->d_split};  // the two-pass apply's scratch
         for (int i = 0; i < nsys; ++i) key.push_back((double)blocks[i]);
+        for (int i = 0; i < nsys; ++i) key.push_back(kslots ? (double)kslots[i] : 0.0);
         if (w->gexec == nullptr || w->gkey != key) {
             w->drop_graph();
             cudaGraph_t graph = nullptr;
@@ -534,12 +569,13 @@ int precond_once(pc_grid* g, int block, int dtype, bool fp32_inner, double sigma
 }
 
 int pcg_solve(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* B, void* X, double tol,
-              int maxit, PcgResult* res, cudaStream_t s, bool pre32) {
+              int maxit, PcgResult* res, cudaStream_t s, bool pre32, const int* kslots) {
     if (nsys <= 0) return PC_OK;
     if (!g->k.set) return fail(PC_ESTATE, "pcg: call pc_set_k first");
     if (!(tol > 0) || maxit < 1) return fail(PC_EINVAL, "pcg: tol must be > 0 and maxit >= 1");
-    if (dtype == PC_C64) return pcg_solve_t<float2>(g, dtype, nsys, blocks, sigma, B, X, tol, maxit, res, s, false);
-    return pcg_solve_t<double2>(g, dtype, nsys, blocks, sigma, B, X, tol, maxit, res, s, pre32);
+    if (dtype == PC_C64)
+        return pcg_solve_t<float2>(g, dtype, nsys, blocks, kslots, sigma, B, X, tol, maxit, res, s, false);
+    return pcg_solve_t<double2>(g, dtype, nsys, blocks, kslots, sigma, B, X, tol, maxit, res, s, pre32);
 }
 
 }  // namespace pc

@@ -37,7 +37,8 @@ struct PcgWork {
     int npart_max = 0;
     PcgScal* sc = nullptr;   // [cap]
     int* done = nullptr;     // [cap] mirror of sc.done for skip flags
-    int* blocks = nullptr;   // [cap] block of each system
+    int* blocks = nullptr;   // [4 cap] block of each preconditioner subsystem
+    int* kslots = nullptr;   // [4 cap] Bloch slot of each preconditioner subsystem
     PcgScal* h_sc = nullptr; // pinned host mirror
     // CUDA graph of one chunk of PCG iterations, valid for the key it was captured with
     cudaGraphExec_t gexec = nullptr;
@@ -53,9 +54,11 @@ struct PcgWork {
 // (stride 3 m elements); blocks[s] in -1..3 (all full-space or all blocks).  x starts at
 // zero.  Per-system results in res (host, nsys entries).  pre32 (complex128 only): apply the
 // preconditioner in complex64 and use the flexible (Polak-Ribiere) beta, which keeps CG
-// convergent under the preconditioner's rounding; the iterates stay complex128.
+// convergent under the preconditioner's rounding; the iterates stay complex128.  kslots (host,
+// optional): the Bloch slot of each system (several Bloch vectors of the grid in one solve).
 int pcg_solve(pc_grid* g, int dtype, int nsys, const int* blocks, double sigma, const void* B, void* X,
-              double tol, int maxit, PcgResult* res, cudaStream_t s, bool pre32 = false);
+              double tol, int maxit, PcgResult* res, cudaStream_t s, bool pre32 = false,
+              const int* kslots = nullptr);
 
 // z = P_ref r once, outside a solve (block 0..3, or -1 for the full space through its four
 // blocks); fp32_inner as pre32 above.
@@ -81,6 +84,29 @@ int ts_gram(const double2* A, int rows, const double2* B, int cols, int64_t m, c
 // C must not overlap A; with beta == 0 C is only written.
 int ts_update(const double2* A, int k, const double2* d_h, int cols, double2* C, int64_t vs, double alpha,
               double beta, cudaStream_t s);
+
+// The same two products for several spaces in one launch (jobs of equal vector length; the
+// Gram jobs all weighted by their mat or all unweighted).  Results of a Gram job go to its out
+// (device, rows x cols column-major).  An update job's C must not overlap its A.
+struct GramJob {
+    const double2* A;
+    int rows;
+    const double2* B;
+    int cols;
+    const void* mat;
+    double2* out;
+};
+struct UpdateJob {
+    const double2* A;
+    int k;
+    const double2* h;
+    int cols;
+    double2* C;
+    double alpha, beta;
+};
+int ts_gram_batch(const GramJob* jobs, int njobs, int64_t m, int matkind, double rho0, double rho1, double* d_part,
+                  size_t part_cap, cudaStream_t s);
+int ts_update_batch(const UpdateJob* jobs, int njobs, int64_t vs, cudaStream_t s);
 
 }  // namespace pc
 

@@ -1,6 +1,6 @@
-"""The multi-rank path of bench.py on CPU: two gloo ranks deal the Bloch vectors round-robin
-(every point of the path once per sweep, no point on two ranks in the same sweep) and reduce
-the timing with max and the k-point counts with sum, as the GPU launch under torchrun does."""
+"""The multi-rank path of bench.py on CPU: two gloo ranks deal chunks of consecutive Bloch vectors
+round-robin (every point of the path once per sweep, no point on two ranks in the same sweep) and
+reduce the timing with max and the k-point counts with sum, as the GPU launch under torchrun does."""
 
 import os
 import socket
@@ -16,7 +16,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, nk, steps, out):
+def _rank_main(rank, world, port, nk, steps, kb, out):
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -25,10 +25,10 @@ def _rank_main(rank, world, port, nk, steps, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
-        mine = [bench.kpoint_index(s, world, rank, nk) for s in range(steps)]
+        mine = [bench.kpoint_chunk(s, world, rank, nk, kb) for s in range(steps)]
         local_time = 1.0 + rank  # rank-dependent "time"
         t_max = bench.max_over_ranks(world, local_time, device="cpu")
-        total = bench.sum_over_ranks(world, float(steps), device="cpu")
+        total = bench.sum_over_ranks(world, float(steps * kb), device="cpu")
         gathered = [None] * world
         dist.all_gather_object(gathered, mine)
         if rank == 0:
@@ -38,13 +38,13 @@ def _rank_main(rank, world, port, nk, steps, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,steps", [(2, 16), (2, 3)])
-def test_two_rank_sharding_and_reductions(world, steps):
+@pytest.mark.parametrize("world,steps,kb", [(2, 16, 1), (2, 3, 1), (2, 2, 8), (2, 3, 8)])
+def test_two_rank_sharding_and_reductions(world, steps, kb):
     nk = 31
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, world, port, nk, steps, q)) for r in range(world)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, nk, steps, kb, q)) for r in range(world)]
     for p in procs:
         p.start()
     gathered, t_max, total = q.get(timeout=120)
@@ -52,9 +52,10 @@ def test_two_rank_sharding_and_reductions(world, steps):
         p.join(timeout=120)
         assert p.exitcode == 0
     assert t_max == 1.0 + (world - 1)
-    assert total == world * steps
-    # step s on rank r takes point (s * world + r) mod nk: the first sweep covers each point once
-    order = [gathered[r][s] for s in range(steps) for r in range(world)]
+    assert total == world * steps * kb
+    # step s on rank r takes the kb points of chunk s * world + r (mod nk): the first sweep covers
+    # each point once
+    order = [i for s in range(steps) for r in range(world) for i in gathered[r][s]]
     first = order[:nk]
     assert len(set(first)) == len(first)
     if len(order) >= nk:

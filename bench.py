@@ -322,16 +322,19 @@ def profile_run(what):
     import paper_2606_03599_gb300 as pc
     from workloads import config_cell
     if what.startswith("kpoint"):
-        # the timed step's options; tuning and one warm-up solve stay outside the profiled range
-        # (ncu --profile-from-start off captures only what runs between profiler start and stop)
+        # one timed step (a lockstep chunk of 8 path points) with the step's options; tuning and
+        # one warm-up chunk stay outside the profiled range (ncu --profile-from-start off captures
+        # only what runs between profiler start and stop)
+        from workloads import sc_path
         cell = config_cell("fp64")
         g = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
         prec = pc.PC_PREC_MIXED if what == "kpoint-mixed" else pc.PC_PREC_FP64
         opt = pc.pc_options_default(tol=TOL, inner_tol=1e-10, precision=prec, autotune=1)
-        pc.pc_eigs(g, [0.25, 0.0, 0.0], NEV, opt=opt)
+        kpts = sc_path(6)
+        pc.pc_eigs_multi(g, kpts[0:8], NEV, opt=opt)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        pc.pc_eigs(g, [0.5, 0.0, 0.0], NEV, opt=opt)
+        pc.pc_eigs_multi(g, kpts[8:16], NEV, opt=opt)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     else:
@@ -612,8 +615,9 @@ def main():
     ap.add_argument("--paper-n", type=int, default=60, help="grid size of --paper (the paper's: 60)")
     ap.add_argument("--paper-k", type=int, default=10, help="Bloch vectors of the 91-point path timed by --paper")
     ap.add_argument("--profile", default=None, choices=["kpoint", "kpoint-mixed", "apply-c64", "apply-c128"],
-                    help="profiling aid for ncu: run only one k-point solve of the workload, or one "
-                         "N=160 four-block apply (after two untimed ones), and print nothing else")
+                    help="profiling aid for ncu: run only one lockstep chunk of 8 Bloch vectors of the "
+                         "workload (after an untimed one), or one N=160 four-block apply (after two "
+                         "untimed ones), and print nothing else")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -44,9 +44,11 @@ namespace pc {
 using cd = std::complex<double>;
 
 // ================================================================== small dense LA (host)
-// Hermitian eigen-decomposition by cyclic Jacobi rotations.  A: n x n column-major
-// (only its Hermitian part is used).  Returns eigenvalues in descending order and
-// the matching orthonormal eigenvectors (columns of V).
+// Hermitian eigen-decomposition: Householder reduction to tridiagonal form, a diagonal unitary
+// scaling that makes the off-diagonal real, then the implicit QL iteration with Wilkinson shifts
+// on the real symmetric tridiagonal matrix (the textbook tridiagonal QL method).  A: n x n
+// column-major (only its Hermitian part is used).  Returns eigenvalues in descending order and the
+// matching orthonormal eigenvectors (columns of V).
 static void herm_eig_desc(int n, std::vector<cd> A, std::vector<double>& w, std::vector<cd>& V) {
     for (int j = 0; j < n; ++j)
         for (int i = 0; i < j; ++i) {
@@ -55,56 +57,128 @@ static void herm_eig_desc(int n, std::vector<cd> A, std::vector<double>& w, std:
             A[j + i * n] = std::conj(h);
         }
     for (int i = 0; i < n; ++i) A[i + i * n] = cd(A[i + i * n].real(), 0.0);
-    V.assign((size_t)n * n, cd(0, 0));
-    for (int i = 0; i < n; ++i) V[i + i * n] = 1.0;
-    double fro = 0;
-    for (auto& v : A) fro += std::norm(v);
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0;
-        for (int j = 0; j < n; ++j)
-            for (int i = 0; i < j; ++i) off += std::norm(A[i + j * n]);
-        if (off <= 1e-32 * fro || off == 0.0) break;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const cd apq = A[p + q * n];
-                const double g = std::abs(apq);
-                if (g < 1e-300) continue;
-                const double app = A[p + p * n].real(), aqq = A[q + q * n].real();
-                const cd ph = apq / g;  // e^{i phi}
-                // real symmetric 2x2 [[app, g],[g, aqq]] diagonalised by [[c, s],[-s, c]]
-                const double zeta = (aqq - app) / (2.0 * g);
-                const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
-                const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
-                // J = diag(1, e^{-i phi}) [[c, s],[-s, c]]
-                const cd j00 = c, j01 = s, j10 = -s * std::conj(ph), j11 = c * std::conj(ph);
-                for (int k = 0; k < n; ++k) {  // columns: A <- A J
-                    const cd akp = A[k + p * n], akq = A[k + q * n];
-                    A[k + p * n] = akp * j00 + akq * j10;
-                    A[k + q * n] = akp * j01 + akq * j11;
+    // Q accumulates the reflectors: A = Q T Q^H
+    std::vector<cd> Q((size_t)n * n, cd(0, 0));
+    for (int i = 0; i < n; ++i) Q[i + i * n] = 1.0;
+    std::vector<cd> v(n), p(n), q(n);
+    for (int k = 0; k + 2 < n; ++k) {
+        // reflector H = I - tau u u^H mapping A[k+1:, k] to a multiple of e_{k+1}
+        double xn = 0;
+        for (int i = k + 1; i < n; ++i) xn += std::norm(A[i + k * n]);
+        xn = std::sqrt(xn);
+        if (xn == 0.0) continue;
+        const cd x0 = A[(k + 1) + k * n];
+        const double ax0 = std::abs(x0);
+        const cd ph = ax0 > 0 ? x0 / ax0 : cd(1, 0);
+        const cd alpha = -ph * xn;
+        for (int i = 0; i < n; ++i) v[i] = 0;
+        for (int i = k + 1; i < n; ++i) v[i] = A[i + k * n];
+        v[k + 1] -= alpha;
+        double vn = 0;
+        for (int i = k + 1; i < n; ++i) vn += std::norm(v[i]);
+        if (vn == 0.0) continue;
+        const double tau = 2.0 / vn;
+        // A <- H A H with H = I - tau v v^H (A Hermitian): p = tau A v, K = tau/2 v^H p,
+        // q = p - K v, A <- A - v q^H - q v^H
+        for (int i = k; i < n; ++i) {
+            cd s = 0;
+            for (int j = k + 1; j < n; ++j) s += A[i + j * n] * v[j];
+            p[i] = tau * s;
+        }
+        cd K = 0;
+        for (int i = k + 1; i < n; ++i) K += std::conj(v[i]) * p[i];
+        K *= 0.5 * tau;
+        for (int i = k; i < n; ++i) q[i] = p[i] - K * (i > k ? v[i] : cd(0, 0));
+        for (int j = k; j < n; ++j)
+            for (int i = k; i < n; ++i) {
+                const cd vi = i > k ? v[i] : cd(0, 0), vj = j > k ? v[j] : cd(0, 0);
+                A[i + j * n] -= vi * std::conj(q[j]) + q[i] * std::conj(vj);
+            }
+        // Q <- Q H
+        for (int i = 0; i < n; ++i) {
+            cd s = 0;
+            for (int j = k + 1; j < n; ++j) s += Q[i + j * n] * v[j];
+            s *= tau;
+            for (int j = k + 1; j < n; ++j) Q[i + j * n] -= s * std::conj(v[j]);
+        }
+    }
+    // T: real diagonal d, complex subdiagonal A[k+1, k]; D = diag(phases) makes it real
+    std::vector<double> d(n), e(n, 0.0);
+    for (int i = 0; i < n; ++i) d[i] = A[i + i * n].real();
+    cd phase = 1.0;
+    std::vector<cd> phs(n);
+    phs[0] = 1.0;
+    for (int k = 0; k + 1 < n; ++k) {
+        const cd t = A[(k + 1) + k * n];
+        const double at = std::abs(t);
+        e[k] = at;
+        phase = at > 0 ? phase * (t / at) : phase;
+        phs[k + 1] = phase;
+    }
+    // implicit QL on (d, e), rotations accumulated in Z (real, column-major)
+    std::vector<double> Z((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Z[i + i * n] = 1.0;
+    for (int l = 0; l < n; ++l) {
+        for (int iter = 0; iter < 60; ++iter) {
+            int m = l;
+            for (; m + 1 < n; ++m) {
+                const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+                if (std::fabs(e[m]) <= 1e-16 * dd) break;
+            }
+            if (m == l) break;
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = std::hypot(g, 1.0);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+            double s = 1.0, c = 1.0, pp = 0.0;
+            int i = m - 1;
+            bool deflated = false;
+            for (; i >= l; --i) {
+                double f = s * e[i], b = c * e[i];
+                r = std::hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {
+                    d[i + 1] -= pp;
+                    e[m] = 0.0;
+                    deflated = true;
+                    break;
                 }
-                for (int k = 0; k < n; ++k) {  // rows: A <- J^H A
-                    const cd apk = A[p + k * n], aqk = A[q + k * n];
-                    A[p + k * n] = std::conj(j00) * apk + std::conj(j10) * aqk;
-                    A[q + k * n] = std::conj(j01) * apk + std::conj(j11) * aqk;
-                }
-                A[p + q * n] = A[q + p * n] = 0.0;
-                for (int k = 0; k < n; ++k) {  // V <- V J
-                    const cd vkp = V[k + p * n], vkq = V[k + q * n];
-                    V[k + p * n] = vkp * j00 + vkq * j10;
-                    V[k + q * n] = vkp * j01 + vkq * j11;
+                s = f / r;
+                c = g / r;
+                g = d[i + 1] - pp;
+                r = (d[i] - g) * s + 2.0 * c * b;
+                pp = s * r;
+                d[i + 1] = g + pp;
+                g = c * r - b;
+                for (int k = 0; k < n; ++k) {
+                    f = Z[k + (i + 1) * n];
+                    Z[k + (i + 1) * n] = s * Z[k + i * n] + c * f;
+                    Z[k + i * n] = c * Z[k + i * n] - s * f;
                 }
             }
+            if (deflated) continue;
+            d[l] -= pp;
+            e[l] = g;
+            e[m] = 0.0;
+        }
     }
+    // eigenvectors: Q D Z
     std::vector<int> idx(n);
     for (int i = 0; i < n; ++i) idx[i] = i;
-    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return A[a + a * n].real() > A[b + b * n].real(); });
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return d[a] > d[b]; });
     w.resize(n);
-    std::vector<cd> Vs((size_t)n * n);
-    for (int j = 0; j < n; ++j) {
-        w[j] = A[idx[j] + idx[j] * n].real();
-        for (int i = 0; i < n; ++i) Vs[i + j * n] = V[i + idx[j] * n];
+    V.assign((size_t)n * n, cd(0, 0));
+    std::vector<cd> QD((size_t)n * n);
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) QD[i + j * n] = Q[i + j * n] * phs[j];
+    for (int jj = 0; jj < n; ++jj) {
+        const int j = idx[jj];
+        w[jj] = d[j];
+        for (int k = 0; k < n; ++k) {
+            const double z = Z[k + j * n];
+            if (z == 0.0) continue;
+            for (int i = 0; i < n; ++i) V[i + jj * n] += QD[i + k * n] * z;
+        }
     }
-    V.swap(Vs);
 }
 
 // G = R^H R with R upper triangular (column-major n x n).  False if G is not numerically SPD.
@@ -287,6 +361,7 @@ struct Eigs {
     size_t gpart_cap = 0;
     long long pcg_iters = 0;
     int max_pcg = 0, solves = 0, expansions = 0, cholqr_single = 0, syncs = 0;
+    double t_op = 0, t_ritz = 0, t_check = 0;  // wall seconds in the solves, Rayleigh-Ritz, residual checks
     std::vector<void*> allocs;
     ~Eigs() {
         for (void* p : allocs) cudaFree(p);
@@ -652,7 +727,9 @@ static int expand(Eigs& E, std::vector<int>& active, double tol) {
         if (live[i * bs]) PC_TRY(mass(E, S, S.V + (int64_t)S.m_exp * vs, rhs, bs));
         else PC_CUDA_TRY(cudaMemsetAsync(rhs, 0, sizeof(double2) * bs * vs, E.s));
     }
+    const auto t_op0 = std::chrono::steady_clock::now();
     PC_TRY(apply_op(E, nsys, blocks, kslots, live, vs));
+    E.t_op += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_op0).count();
     E.expansions += nA;
     auto Wv = [&](int a) { return E.W + (int64_t)active[a] * bs * vs; };
     auto dsm = [&](size_t off) { return reinterpret_cast<double2*>(E.dsmall + off); };
@@ -790,6 +867,7 @@ static int expand(Eigs& E, std::vector<int>& active, double tol) {
                                     cudaMemcpyDeviceToDevice, E.s));
     }
     // Rayleigh-Ritz and the candidates for a true-residual check
+    const auto t_rr0 = std::chrono::steady_clock::now();
     std::vector<int> chk, nck;
     for (int a = 0; a < nA; ++a) {
         Space& S = E.sp[active[a]];
@@ -820,9 +898,12 @@ static int expand(Eigs& E, std::vector<int>& active, double tol) {
             nck.push_back(ntest);
         }
     }
+    const auto t_ck0 = std::chrono::steady_clock::now();
+    E.t_ritz += std::chrono::duration<double>(t_ck0 - t_rr0).count();
     if (!chk.empty()) {
         std::vector<std::vector<double>> lam, rel;
         PC_TRY(check_pairs(E, chk, nck, lam, rel));
+        E.t_check += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_ck0).count();
         for (size_t c = 0; c < chk.size(); ++c) {
             Space& S = E.sp[chk[c]];
             int nc = 0;
@@ -1042,7 +1123,9 @@ static int run_eigs(pc_grid* g, int nk, const double* kappas, int nev, double si
     }
     if (opt->verbose)
         std::fprintf(stderr, "[pc_eigs] Bloch vectors=%d expansions=%d single-pass CholQR=%d solves=%d pcg=%lld "
-                     "host syncs=%d\n", nk, E.expansions, E.cholqr_single, E.solves, E.pcg_iters, E.syncs);
+                     "host syncs=%d; seconds in solves %.3f, Rayleigh-Ritz %.3f, residual checks %.3f, total %.3f\n",
+                     nk, E.expansions, E.cholqr_single, E.solves, E.pcg_iters, E.syncs, E.t_op, E.t_ritz, E.t_check,
+                     std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
     const double to_si = g->C0 / (g->rho0 * g->L * g->L);
     std::vector<double> maxres(nk, 0.0);
     for (int ks = 0; ks < nk; ++ks) {

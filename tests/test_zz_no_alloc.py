@@ -54,6 +54,44 @@ def test_noalloc_matches_regular_apply_twice(pc, dtype, block):
         pc.pc_grid_destroy(g)
 
 
+@pytest.mark.parametrize("N", [186, 254])
+def test_noalloc_complex128_full_space_inside_the_limit(pc, N):
+    """Full-space complex128 grids inside the documented 2^24-node limit whose default launch
+    would need more CTAs than the static scratch holds (4x4 tiles: 2209 at N = 186, 4096 at
+    N = 254) are accepted and computed with a smaller launch: y on sampled nodes (random and on
+    the Bloch-wrap faces) against the oracle, and *dot against the inner product of the returned
+    y with x."""
+    import torch
+    from oracle import oracle as O
+    cell = two_phase_sphere(N, 0.3, 2)
+    g = pc.pc_grid_create(N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+    try:
+        kappa = [0.3, 0.1, 0.2]
+        pc.pc_set_k(g, kappa)
+        C0, rho0, L = pc.pc_grid_units(g)
+        pb = O.problem_from_cell(cell, C0=C0, rho0=rho0, L=L)
+        n = N ** 3
+        xh = complex_gaussian((3, n), 77)
+        x = torch.from_numpy(xh.reshape(-1)).cuda()
+        y = torch.full_like(x, complex(float("nan"), float("nan")))
+        dot = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        pc.pc_block_apply_dot_noalloc(g, -1, x, y, dot, shift=0.4)
+        torch.cuda.synchronize()
+        yh = y.cpu().numpy().reshape(3, n)
+        assert np.isfinite(yh).all()
+        rng = np.random.default_rng(5)
+        i, j, k = (rng.integers(0, N, 150) for _ in range(3))
+        faces = np.concatenate([0 + N * (j + N * k), (N - 1) + N * (j + N * k), i + N * (0 + N * k),
+                                i + N * ((N - 1) + N * k), i + N * (j + N * 0), i + N * (j + N * (N - 1))])
+        nodes = np.unique(np.concatenate([rng.integers(0, n, 600), faces]))
+        ref = O.apply_at_nodes(pb, kappa, xh, nodes, 0.4)
+        assert np.abs(yh[:, nodes].T - ref).max() <= 1e-12 * np.abs(ref).max()
+        ref_dot = float(np.real(np.vdot(xh.reshape(-1), yh.reshape(-1))))
+        assert abs(dot.item() - ref_dot) <= 1e-12 * np.linalg.norm(xh) * np.linalg.norm(yh)
+    finally:
+        pc.pc_grid_destroy(g)
+
+
 def test_noalloc_rejects_grids_beyond_the_static_limit(pc):
     import torch
     N = 258  # 258^3 nodes > 2^24

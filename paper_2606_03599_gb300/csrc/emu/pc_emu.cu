@@ -13,6 +13,7 @@
 #include "../pc_apply_row.cuh"
 #include "../pc_apply_pipe.cuh"
 #include "../pc_apply_split.cuh"
+#include "../pc_small_dft.cuh"
 
 using namespace pc;
 
@@ -436,4 +437,27 @@ extern "C" int pc_emu_apply(int N, int block, int dtype, int shape, int tz, cons
         return 0;
     }
     return emu_t<double>(shape, P, full, cubic != 0, matkind, block, x, y, mat, shift, tz);
+}
+
+// The L-point DFT of the Bloch transform kernels (compile-time roots) on one complex128 vector.
+template <int L>
+static void emu_sdft_l(int inv, const double* in, double* out) {
+    double2 v[16];
+    for (int i = 0; i < L; ++i) v[i] = make_double2(in[2 * i], in[2 * i + 1]);
+    if (inv) small_dft_ct<L, true>(v);
+    else small_dft_ct<L, false>(v);
+    for (int i = 0; i < L; ++i) {
+        out[2 * i] = v[i].x;
+        out[2 * i + 1] = v[i].y;
+    }
+}
+
+extern "C" int pc_emu_small_dft(int L, int inv, const double* in, double* out) {
+    switch (L) {
+#define PC_L(n) case n: emu_sdft_l<n>(inv, in, out); return 0;
+        PC_L(1) PC_L(2) PC_L(3) PC_L(4) PC_L(5) PC_L(6) PC_L(7) PC_L(8)
+        PC_L(9) PC_L(10) PC_L(11) PC_L(12) PC_L(13) PC_L(14) PC_L(15) PC_L(16)
+#undef PC_L
+        default: return -1;
+    }
 }

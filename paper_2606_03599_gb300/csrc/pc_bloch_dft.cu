@@ -9,7 +9,8 @@
 //
 //   X[k1 + n1 k2] = sum_{i2 < n2} w_n^{i2 k1} [sum_{i1 < n1} x[i1 n2 + i2] w_n1^{i1 k1}] w_n2^{i2 k2}
 //
-// (Cooley-Tukey with two direct DFTs of lengths n1, n2 <= 16, w_m = e^{-2 pi i / m}).  Both stages
+// (Cooley-Tukey with two direct DFTs of lengths n1, n2 <= 16, w_m = e^{-2 pi i / m}; the direct DFTs
+// pair their inputs and take their roots as compile-time constants, pc_small_dft.cuh).  Both stages
 // work in place in shared memory on groups of n1 (stage A) or n2 (stage B) values that no other
 // thread touches, so a stage needs no barrier inside; the spectrum comes out digit-permuted
 // (mode k1 + n1 k2 at position k1 n2 + k2) and the inverse stages take that order back to the natural
@@ -33,6 +34,7 @@
 #include "pc_complex.cuh"
 #include "pc_fourier.h"
 #include "pc_internal.h"
+#include "pc_small_dft.cuh"
 
 namespace pc {
 
@@ -55,25 +57,6 @@ template <typename Co, typename Ci> __device__ __forceinline__ Co conv_c(Ci v) {
     o.x = (decltype(o.x))v.x;
     o.y = (decltype(o.y))v.y;
     return o;
-}
-
-// Direct L-point DFT of v in place (roots wn[(n / L) ((j k) mod L)], conjugated when INV).
-template <int L, bool INV, typename C>
-__device__ __forceinline__ void small_dft(C (&v)[kDftMaxFactor], const C* __restrict__ wn, int s) {
-    C out[L];
-#pragma unroll
-    for (int k = 0; k < L; ++k) {
-        C acc = v[0];
-#pragma unroll
-        for (int j = 1; j < L; ++j) {
-            C w = wn[s * ((j * k) % L)];
-            if (INV) w = conj_c(w);
-            acc = cadd(acc, cmul(v[j], w));
-        }
-        out[k] = acc;
-    }
-#pragma unroll
-    for (int k = 0; k < L; ++k) v[k] = out[k];
 }
 
 // Geometry of one batch of lines along an axis of a shared-memory array: element e of line l sits at
@@ -101,7 +84,7 @@ __device__ void stage_a(C* buf, const Lines& ln, int n1, int n2, const C* wn, in
 #pragma unroll
             for (int k = 1; k < L1; ++k) v[k] = cmul(v[k], conj_c(wn[(i2 * k) % n]));
         }
-        small_dft<L1, INV>(v, wn, n2);
+        small_dft_ct<L1, INV>(v);
         if (!INV) {
 #pragma unroll
             for (int k = 1; k < L1; ++k) v[k] = cmul(v[k], wn[(i2 * k) % n]);
@@ -123,7 +106,7 @@ __device__ void stage_b(C* buf, const Lines& ln, int n1, int n2, const C* wn) {
         C v[kDftMaxFactor];
 #pragma unroll
         for (int i = 0; i < L2; ++i) v[i] = buf[b0 + i * ln.es];
-        small_dft<L2, INV>(v, wn, n1);
+        small_dft_ct<L2, INV>(v);
 #pragma unroll
         for (int i = 0; i < L2; ++i) buf[b0 + i * ln.es] = v[i];
     }

@@ -167,3 +167,21 @@ def test_emulated_two_pass_nodewise_material(emu, block, lattice):
     assert rc == 0
     err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
     assert err < 1e-13
+
+
+@pytest.mark.parametrize("L", list(range(1, 17)))
+def test_small_dft_with_compile_time_roots_matches_numpy(emu, L):
+    """The L-point DFT inside the Bloch transform kernels (roots from constant expressions, paired
+    inputs) equals numpy's FFT, forward and unnormalised inverse, to rounding."""
+    rng = np.random.default_rng(L)
+    v = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    fn = emu.pc_emu_small_dft
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    fn.restype = ctypes.c_int
+    for inv, ref in ((0, np.fft.fft(v)), (1, np.fft.ifft(v) * L)):
+        inp = np.ascontiguousarray(np.stack([v.real, v.imag], axis=1).reshape(-1))
+        out = np.zeros(2 * L)
+        assert fn(L, inv, inp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 0
+        got = out[0::2] + 1j * out[1::2]
+        assert np.abs(got - ref).max() <= 4e-16 * L * np.abs(v).sum()

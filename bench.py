@@ -52,11 +52,13 @@ TOL = 1e-8
 #   flops: 294 real flops (differences, reconstruction, 6x6 stiffness, fluxes, gather, shift)
 BYTES_PER_NODE = {"c64": 3 * 8 * 2 + 1, "c128": 3 * 16 * 2 + 1}
 FLOPS_PER_NODE = 294
-# DRAM bytes per node of the two-pass complex128 apply (the four kernels together), from one
-# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, cold cache, 8 block vectors of the
-# N=48 workload per launch: ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum
-# --clock-control none --profile-from-start off -k regex:split_ -c 8 python bench.py --profile kpoint).
-SPLIT_F64_DRAM_BYTES_PER_NODE = (10634752 + 2304 + 16088320 + 3559168 + 18640640 + 14592 + 68762624 + 59136) / 221184
+# DRAM bytes per node of the two-pass complex128 apply (the four kernels together) at the bench's
+# launch (64 block vectors: 8 Bloch vectors x 4 blocks x Krylov block 2, N = 48), from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, cold cache: ncu --metrics
+# dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
+# --profile-from-start off -k regex:split_ -c 8 python bench.py --profile kpoint).
+SPLIT_F64_DRAM_BYTES_PER_NODE = (85038592 + 55449856 + 167524608 + 397934080 + 155096832 + 45943040 +
+                                 549512704 + 72092416) / (64 * 27648)
 
 
 def peaks():
@@ -718,10 +720,10 @@ def main():
     app_ms = st["apply_ms"][1] / max(1, n_app)
     nodes_per_launch = st["apply_nodes"][1] / max(1, n_app)
     achieved_tflops = nodes_per_launch * FLOPS_PER_NODE / (app_ms / 1e3) / 1e12
-    kind = pc.pc_tuned_config(g, pc.PC_C128, 0, 4 * opt.block_size)[0]
+    kind = pc.pc_tuned_config(g, pc.PC_C128, 0, 4 * opt.block_size * KB)[0]
     kname = {0: "apply_kernel<double>", 1: "apply_tma_kernel<double>", 2: "apply_row_kernel",
              3: "split_fill_x + split_flux + split_fill_f + split_gather (two-pass FP64)"}[kind]
-    traffic = SPLIT_F64_DRAM_BYTES_PER_NODE * nodes_per_launch if kind == 3 else None
+    traffic = SPLIT_F64_DRAM_BYTES_PER_NODE * nodes_per_launch if (kind == 3 and KB == 8) else None
     roofline = {"kernel": kname + " (block stencil, FP64, autotuned launch)", "bound": "alu",
                 "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / fp64_peak, "traffic": traffic,

@@ -112,7 +112,9 @@ typedef struct {
 /* Options of pc_eigs; fill with pc_options_default first. */
 typedef struct {
     double tol;          /* converged when the true relative residual
-                            ||A x - lambda M x|| / (|lambda| ||M x||) <= tol (FP64); default 1e-8 */
+                            ||A x - lambda M x|| / (max(|lambda|, |sigma|) ||M x||) <= tol (FP64),
+                            i.e. relative to lambda wherever lambda >= |sigma| and to the shift's
+                            scale for the acoustic modes next to Gamma; default 1e-8 */
     double inner_tol;    /* relative residual of each shift-invert solve; default 1e-10 */
     int precision;       /* PC_PREC_FP64 or PC_PREC_MIXED */
     int full_space;      /* 0: four parity blocks merged (default); 1: one full-space solve */

@@ -15,7 +15,9 @@
 //
 // Convergence uses the true FP64 residual of each Ritz vector y (unit M-norm):
 // with the Rayleigh quotient lambda = y^H A y / y^H M y,
-//     || A y - lambda M y ||_2 / ( |lambda| || M y ||_2 ) <= tol.
+//     || A y - lambda M y ||_2 / ( max(|lambda|, |sigma|) || M y ||_2 ) <= tol,
+// i.e. relative to lambda, and to the scale of the shift for the few eigenvalues below |sigma|
+// (acoustic modes next to Gamma).
 //
 // At a Bloch vector where symbol blocks vanish (Gamma, Sec. 6.2, App. C) the
 // zero-derivative modes T_sigma (e_m (x) e_alpha) of those Fourier modes m are
@@ -655,7 +657,10 @@ static int check_pairs(Eigs& E, const std::vector<int>& chk, const std::vector<i
                 const double d = q[2] / q[3];  // Rayleigh-quotient correction of lambda
                 L[i] = lr[col] + d;
                 const double r2 = std::max(0.0, q[0] - 2.0 * d * q[4] + d * d * q[1]);
-                Rl[i] = std::sqrt(r2) / (std::fabs(L[i]) * std::sqrt(q[1]));
+                // relative to the eigenvalue, or to the shift's scale for eigenvalues below |sigma|
+                // (the acoustic modes next to Gamma, where |lambda| / ||A|| is below what an
+                // inexact shift-invert solve resolves; for lambda >= |sigma| this is ||r|| / |lambda|)
+                Rl[i] = std::sqrt(r2) / (std::max(std::fabs(L[i]), std::fabs(E.sigma)) * std::sqrt(q[1]));
             }
         }
         c0 = c1;

@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 parity-blocked band solver.
 
-One step = one chunk of --kbatch (default 8) consecutive Bloch vectors of the
+One step = one chunk of --kbatch (default 16) consecutive Bloch vectors of the
 plain FP64 workload: a seeded two-phase simple-cubic cell (N = 48, sphere
 R = 0.35, seed 2), the Gamma-X-M-Gamma-R-X path of 31 k-points (6 intervals per
 segment), the lowest 20 non-zero bands at true relative residual 1e-8, solved on
@@ -59,6 +59,7 @@ FLOPS_PER_NODE = 294
 # --profile-from-start off -k regex:split_ -c 8 python bench.py --profile kpoint).
 SPLIT_F64_DRAM_BYTES_PER_NODE = (85038592 + 55449856 + 167524608 + 397934080 + 155096832 + 45943040 +
                                  549512704 + 72092416) / (64 * 27648)
+SPLIT_DRAM_KB = 8  # Bloch vectors per step of that capture
 
 
 def peaks():
@@ -216,8 +217,8 @@ def run_reference(args):
     x = complex_gaussian((3, cell.N ** 3 // 4), 7)
     # block applies one k-point solve of the GPU arm performs, as that arm measures it
     # (solver.block_applies_per_kpoint of its JSON line on GB300: 6095 = 173.5 inner solves x ~27
-    # PCG iterations plus residual checks and refinement applies, lockstep chunks of 8 Bloch
-    # vectors); the GPU arm's own cpu_baseline scales by the count it measures itself
+    # PCG iterations plus residual checks, counted over the launches' items); the GPU arm's own
+    # cpu_baseline scales by the count it measures itself
     applies = int(os.environ.get("PC_APPLIES_PER_KPOINT", str(APPLIES_PER_KPOINT_MEASURED)))
     reps = 16
     for _ in range(args.warmup):
@@ -325,7 +326,7 @@ def profile_run(what):
     import paper_2606_03599_gb300 as pc
     from workloads import config_cell
     if what.startswith("kpoint"):
-        # one timed step (a lockstep chunk of 8 path points) with the step's options; tuning and
+        # one timed step (a lockstep chunk of 16 path points) with the step's options; tuning and
         # one warm-up chunk stay outside the profiled range (ncu --profile-from-start off captures
         # only what runs between profiler start and stop)
         from workloads import sc_path
@@ -334,10 +335,10 @@ def profile_run(what):
         prec = pc.PC_PREC_MIXED if what == "kpoint-mixed" else pc.PC_PREC_FP64
         opt = pc.pc_options_default(tol=TOL, inner_tol=1e-10, precision=prec, autotune=1)
         kpts = sc_path(6)
-        pc.pc_eigs_multi(g, kpts[0:8], NEV, opt=opt)
+        pc.pc_eigs_multi(g, kpts[0:16], NEV, opt=opt)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        pc.pc_eigs_multi(g, kpts[8:16], NEV, opt=opt)
+        pc.pc_eigs_multi(g, kpts[15:31], NEV, opt=opt)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     else:
@@ -616,7 +617,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=8)
-    ap.add_argument("--kbatch", type=int, default=8,
+    ap.add_argument("--kbatch", type=int, default=16,
                     help="Bloch vectors per step, solved together in lockstep (1 = one pc_eigs per step)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -637,7 +638,7 @@ def main():
     ap.add_argument("--paper-n", type=int, default=60, help="grid size of --paper (the paper's: 60)")
     ap.add_argument("--paper-k", type=int, default=16, help="Bloch vectors of the 91-point path timed by --paper")
     ap.add_argument("--profile", default=None, choices=["kpoint", "kpoint-mixed", "apply-c64", "apply-c128"],
-                    help="profiling aid for ncu: run only one lockstep chunk of 8 Bloch vectors of the "
+                    help="profiling aid for ncu: run only one lockstep chunk of 16 Bloch vectors of the "
                          "workload (after an untimed one), or one N=160 four-block apply (after two "
                          "untimed ones), and print nothing else")
     args = ap.parse_args()
@@ -743,7 +744,7 @@ def main():
     kind = pc.pc_tuned_config(g, pc.PC_C128, 0, 4 * opt.block_size * KB)[0]
     kname = {0: "apply_kernel<double>", 1: "apply_tma_kernel<double>", 2: "apply_row_kernel",
              3: "split_fill_x + split_flux + split_fill_f + split_gather (two-pass FP64)"}[kind]
-    traffic = SPLIT_F64_DRAM_BYTES_PER_NODE * nodes_per_launch if (kind == 3 and KB == 8) else None
+    traffic = SPLIT_F64_DRAM_BYTES_PER_NODE * nodes_per_launch if (kind == 3 and KB == SPLIT_DRAM_KB) else None
     roofline = {"kernel": kname + " (block stencil, FP64, autotuned launch)", "bound": "alu",
                 "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / fp64_peak, "traffic": traffic,
@@ -780,7 +781,7 @@ def main():
     compare = None
     if rank == 0:
         compare = {}
-        nc = max(1, min(args.steps, 3))
+        nc = max(1, min(args.steps, 24 // KB))  # about 24 Bloch vectors
         cks = [kchunk(args.warmup + s) for s in range(nc)]
         legs = (("mixed", pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED, autotune=1), True),
                 ("fp64_preconditioner", pc.pc_options_default(tol=TOL, precond_fp32=0, autotune=1), True),

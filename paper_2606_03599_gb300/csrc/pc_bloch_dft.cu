@@ -71,7 +71,7 @@ struct Lines {
 // times w_n^{i2 k1}, in place.  Inverse (A^-1, the last inverse stage): conjugate twiddle first, then
 // the conjugate n1-point DFT.
 template <int L1, bool INV, typename C>
-__device__ void stage_a(C* buf, const Lines& ln, int n1, int n2, const C* wn, int n) {
+__device__ __forceinline__ void stage_a(C* buf, const Lines ln, int n1, int n2, const C* wn, int n) {
     const int groups = ln.count * n2;
     for (int g = threadIdx.x; g < groups; g += blockDim.x) {
         const int l = ln.line_fast ? g % ln.count : g / n2;
@@ -97,7 +97,7 @@ __device__ void stage_a(C* buf, const Lines& ln, int n1, int n2, const C* wn, in
 // Stage B: for every line and k1 < n1, the n2 contiguous values at k1 n2 + i2 -> their n2-point DFT
 // (conjugate when INV), in place.
 template <int L2, bool INV, typename C>
-__device__ void stage_b(C* buf, const Lines& ln, int n1, int n2, const C* wn) {
+__device__ __forceinline__ void stage_b(C* buf, const Lines ln, int n1, int n2, const C* wn) {
     const int groups = ln.count * n1;
     for (int g = threadIdx.x; g < groups; g += blockDim.x) {
         const int l = ln.line_fast ? g % ln.count : g / n1;
@@ -113,7 +113,7 @@ __device__ void stage_b(C* buf, const Lines& ln, int n1, int n2, const C* wn) {
 }
 
 template <bool INV, typename C>
-__device__ void dispatch_a(C* buf, const Lines& ln, int n1, int n2, const C* wn, int n) {
+__device__ void dispatch_a(C* buf, const Lines ln, int n1, int n2, const C* wn, int n) {
     switch (n1) {
 #define PC_CASE(L) case L: stage_a<L, INV>(buf, ln, n1, n2, wn, n); break;
         PC_CASE(1) PC_CASE(2) PC_CASE(3) PC_CASE(4) PC_CASE(5) PC_CASE(6) PC_CASE(7) PC_CASE(8)
@@ -123,7 +123,7 @@ __device__ void dispatch_a(C* buf, const Lines& ln, int n1, int n2, const C* wn,
     }
 }
 template <bool INV, typename C>
-__device__ void dispatch_b(C* buf, const Lines& ln, int n1, int n2, const C* wn) {
+__device__ void dispatch_b(C* buf, const Lines ln, int n1, int n2, const C* wn) {
     switch (n2) {
 #define PC_CASE(L) case L: stage_b<L, INV>(buf, ln, n1, n2, wn); break;
         PC_CASE(1) PC_CASE(2) PC_CASE(3) PC_CASE(4) PC_CASE(5) PC_CASE(6) PC_CASE(7) PC_CASE(8)
@@ -137,7 +137,7 @@ __device__ void dispatch_b(C* buf, const Lines& ln, int n1, int n2, const C* wn)
 // the factors are compile-time constants (N1, N2) (only the stages of that size are compiled into
 // the kernel); N1 = 0: runtime factors.
 template <int N1, int N2, typename C>
-__device__ void dft_fwd(C* buf, const Lines& ln, int n1, int n2, const C* wn, int n) {
+__device__ __forceinline__ void dft_fwd(C* buf, const Lines ln, int n1, int n2, const C* wn, int n) {
     if constexpr (N1 > 0) stage_a<N1, false>(buf, ln, N1, N2, wn, N1 * N2);
     else dispatch_a<false>(buf, ln, n1, n2, wn, n);
     __syncthreads();
@@ -146,7 +146,7 @@ __device__ void dft_fwd(C* buf, const Lines& ln, int n1, int n2, const C* wn, in
     __syncthreads();
 }
 template <int N1, int N2, typename C>
-__device__ void dft_inv(C* buf, const Lines& ln, int n1, int n2, const C* wn, int n) {
+__device__ __forceinline__ void dft_inv(C* buf, const Lines ln, int n1, int n2, const C* wn, int n) {
     if constexpr (N1 > 0) stage_b<N2, true>(buf, ln, N1, N2, wn);
     else dispatch_b<true>(buf, ln, n1, n2, wn);
     __syncthreads();
@@ -159,7 +159,7 @@ __device__ void dft_inv(C* buf, const Lines& ln, int n1, int n2, const C* wn, in
 __host__ __device__ __forceinline__ int planes_per_cta(int) { return 1; }
 
 // p positions per pencil CTA: the largest divisor of n that is at most kPencilTileMax (no ragged tile).
-__host__ __device__ __forceinline__ int pencil_tile(int n) {
+__host__ __device__ constexpr int pencil_tile(int n) {
     int t = 1;
     for (int d = 1; d <= kPencilTileMax && d <= n; ++d)
         if (n % d == 0) t = d;
@@ -193,6 +193,10 @@ __global__ void __launch_bounds__(kPlaneThreads)
                    const int* __restrict__ sys_k, int64_t tab_stride) {
     extern __shared__ __align__(16) unsigned char smem_bdft[];
     const int n = N1 > 0 ? N1 * N2 : n_rt;
+    if (N1 > 0) {  // compile-time factors: every index division below is by a constant
+        n1 = N1;
+        n2 = N2;
+    }
     const int pp = planes_per_cta(n), nn = n * n;
     C* buf = reinterpret_cast<C*>(smem_bdft);
     C* wn = buf + pp * nn;
@@ -251,6 +255,10 @@ __global__ void __launch_bounds__(kPlaneThreads)
     extern __shared__ __align__(16) unsigned char smem_bdft[];
     using R = typename RTy<C>::R;
     const int n = N1 > 0 ? N1 * N2 : n_rt;
+    if (N1 > 0) {
+        n1 = N1;
+        n2 = N2;
+    }
     const int pp = planes_per_cta(n), nn = n * n;
     C* buf = reinterpret_cast<C*>(smem_bdft);
     C* wn = buf + pp * nn;
@@ -340,8 +348,13 @@ __global__ void __launch_bounds__(kPencilThreads)
                 int64_t sys_stride, double shift_rho_d, double scale_d, int mode, const int* __restrict__ sys_k,
                 int64_t tab_stride, int64_t aref_stride) {
     const int n = N1 > 0 ? N1 * N2 : n_rt;
+    if (N1 > 0) {
+        n1 = N1;
+        n2 = N2;
+    }
     extern __shared__ __align__(16) unsigned char smem_bdft[];
-    const int PT = pencil_tile(n);
+    constexpr int PTc = N1 > 0 ? pencil_tile(N1 * N2) : 1;
+    const int PT = N1 > 0 ? PTc : pencil_tile(n);
     C* buf = reinterpret_cast<C*>(smem_bdft);  // [pencil = comp * 2 + par][k'][pl]
     C* wn = buf + 6 * n * PT;
     const int tiles = n / PT;

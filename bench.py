@@ -53,13 +53,13 @@ TOL = 1e-8
 BYTES_PER_NODE = {"c64": 3 * 8 * 2 + 1, "c128": 3 * 16 * 2 + 1}
 FLOPS_PER_NODE = 294
 # DRAM bytes per node of the two-pass complex128 apply (the four kernels together) at the bench's
-# launch (64 block vectors: 8 Bloch vectors x 4 blocks x Krylov block 2, N = 48), from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum, cold cache: ncu --metrics
+# launches (64 block vectors per launch, the two-pass launcher's batch: a step of 16 Bloch vectors x
+# 4 blocks x Krylov block 2 runs two such launches per apply; N = 48), from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, cold cache: ncu --metrics
 # dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
 # --profile-from-start off -k regex:split_ -c 8 python bench.py --profile kpoint).
-SPLIT_F64_DRAM_BYTES_PER_NODE = (85038592 + 55449856 + 167524608 + 397934080 + 155096832 + 45943040 +
-                                 549512704 + 72092416) / (64 * 27648)
-SPLIT_DRAM_KB = 8  # Bloch vectors per step of that capture
+SPLIT_F64_DRAM_BYTES_PER_NODE = (85041664 + 54938368 + 167506688 + 397915904 + 155097856 + 45949440 +
+                                 549504512 + 71575552) / (64 * 27648)
 
 
 def peaks():
@@ -744,11 +744,12 @@ def main():
     kind = pc.pc_tuned_config(g, pc.PC_C128, 0, 4 * opt.block_size * KB)[0]
     kname = {0: "apply_kernel<double>", 1: "apply_tma_kernel<double>", 2: "apply_row_kernel",
              3: "split_fill_x + split_flux + split_fill_f + split_gather (two-pass FP64)"}[kind]
-    traffic = SPLIT_F64_DRAM_BYTES_PER_NODE * nodes_per_launch if (kind == 3 and KB == SPLIT_DRAM_KB) else None
+    traffic = SPLIT_F64_DRAM_BYTES_PER_NODE * nodes_per_launch if (kind == 3 and KB >= 8) else None
     roofline = {"kernel": kname + " (block stencil, FP64, autotuned launch)", "bound": "alu",
                 "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": achieved_tflops / fp64_peak, "traffic": traffic,
-                "traffic_note": "bytes per launch, ncu cold-cache capture scaled by nodes per launch"
+                "traffic_note": "DRAM bytes per timed apply (two 64-vector launches of the four kernels), ncu "
+                                "cold-cache capture per node scaled by the nodes per timed apply"
                 if traffic is not None else None,
                 "launches": n_app, "avg_launch_us": app_ms * 1e3, "nodes_per_launch": nodes_per_launch,
                 "flops_per_node": FLOPS_PER_NODE, "peak_source": peak_src,

@@ -786,6 +786,11 @@ def main():
         cks = [kchunk(args.warmup + s) for s in range(nc)]
         legs = (("mixed", pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED, autotune=1), True),
                 ("fp64_preconditioner", pc.pc_options_default(tol=TOL, precond_fp32=0, autotune=1), True),
+                # Krylov block width 1 (not the default: a one-vector Krylov space can miss a copy of
+                # an exactly degenerate eigenvalue; reported with its difference to the main leg)
+                ("fp64_block_width_1", pc.pc_options_default(tol=TOL, block_size=1, autotune=1), True),
+                ("mixed_block_width_1", pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED, block_size=1,
+                                                              autotune=1), True),
                 ("one_at_a_time_fp64", pc.pc_options_default(tol=TOL, autotune=1), False),
                 ("full_space_fp64", pc.pc_options_default(tol=TOL, full_space=1, autotune=1), False))
         for name, o2, lockstep in legs:

@@ -119,7 +119,8 @@ typedef struct {
     int precision;       /* PC_PREC_FP64 or PC_PREC_MIXED */
     int full_space;      /* 0: four parity blocks merged (default); 1: one full-space solve */
     int block_size;      /* Krylov block width per parity block; default 2 */
-    int max_basis;       /* Krylov-Schur basis size before restart; default 32 */
+    int max_basis;       /* Krylov-Schur basis size before restart; default 24, raised where a
+                            space's wanted pairs need more (their count + 2 blocks + 8) */
     int max_restarts;    /* outer iteration cap; default 60 */
     int inner_maxit;     /* PCG iteration cap per solve; default 400 */
     int guard;           /* extra Ritz pairs carried per block beyond its share; default 3 */

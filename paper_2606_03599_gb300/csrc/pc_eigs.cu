@@ -994,7 +994,13 @@ static int run_eigs(pc_grid* g, int nk, const double* kappas, int nev, double si
     E.o = opt;
     E.sigma = std::isnan(sigma) ? pc_default_sigma(g) : sigma;
     E.bs = std::max(1, std::min(opt->block_size, 16));
-    E.mmax = std::max(opt->max_basis, 3 * E.bs);
+    {
+        // the basis must hold a space's wanted pairs plus room to expand: at least its initial
+        // target (its share of nev plus the guard pairs) + 2 blocks + 8
+        const int share0 = opt->full_space ? nev : (nev + 3) / 4;
+        const int target0 = share0 + (opt->full_space ? std::max(0, opt->guard) : 1);
+        E.mmax = std::max({opt->max_basis, 3 * E.bs, target0 + 2 * E.bs + 8});
+    }
     E.mcap = E.mmax + 2 * E.bs;
     const bool own_stream = opt->stream == nullptr;
     if (own_stream) PC_CUDA_TRY(cudaStreamCreateWithFlags(&E.s, cudaStreamNonBlocking));
@@ -1231,7 +1237,7 @@ int pc_options_default(pc_options* o) {
     o->precision = PC_PREC_FP64;
     o->full_space = 0;
     o->block_size = 2;
-    o->max_basis = 32;
+    o->max_basis = 24;
     o->max_restarts = 60;
     o->inner_maxit = 400;
     o->guard = 3;

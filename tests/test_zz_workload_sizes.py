@@ -11,7 +11,10 @@ apply and precision workloads), where the oracle's dense and ARPACK solves are o
 * On the heterogeneous N = 48 workload cell, every returned eigenpair is checked with the
   oracle's matrix-free C apply: true residual ||A x - lambda M x|| <= 1e-8 |lambda| ||M x||
   (which bounds the eigenvalue's distance to the spectrum), M-orthonormality to 1e-9.
-* On the same grid, a right-hand side holding a NaN ends the inner solve with PC_ENAN and
+* On the heterogeneous N = 160 precision cell, mixed precision returns the FP64 solve's 20
+  eigenvalues band by band to 1e-10, and FP64 eigenpairs across the band range pass the
+  oracle's residual test and M-normalisation.
+* On the N = 48 grid, a right-hand side holding a NaN ends the inner solve with PC_ENAN and
   leaves x at its zero start (the status path of the reductions, no device fault).
 * Guard bands: outputs written into views of larger buffers leave a sentinel on both sides
   untouched (no write outside the caller's vector), for the benchmarked launches.
@@ -114,6 +117,33 @@ def test_n48_workload_eigenpairs_pass_the_oracle_residual(pc, kappa):
         W = V.reshape(nev, -1)
         gram = (W.conj() * np.tile(rho, 3)[None, :]) @ W.T
         assert np.abs(gram - np.eye(nev)).max() <= 1e-9
+    finally:
+        g.close()
+
+
+def test_n160_precision_cell_mixed_equals_fp64_and_passes_the_oracle_residual(pc):
+    """The heterogeneous precision workload (N = 160, R = 0.3, seed 3) at kappa = (0.3, 0.1, 0.2):
+    the mixed-precision solve (complex64 inner PCG, FP64 refinement and outer loop) returns the
+    FP64 solve's 20 eigenvalues band by band to 1e-10, and FP64 eigenpairs spread over the band
+    range pass the oracle's own FP64 residual (1e-8) and M-normalisation."""
+    import torch
+    N, nev = 160, 20
+    kappa = [0.3, 0.1, 0.2]
+    g = Grid(pc, two_phase_sphere(N, 0.3, 3))
+    try:
+        evecs = torch.empty(nev * 3 * N ** 3, dtype=torch.complex128, device="cuda")
+        ev64, _, info64 = pc.pc_eigs(g.h, kappa, nev, evecs=evecs)
+        evm, _, infom = pc.pc_eigs(g.h, kappa, nev, opt=pc.pc_options_default(precision=pc.PC_PREC_MIXED))
+        assert info64["max_rel_resid"] <= 1e-8 and infom["max_rel_resid"] <= 1e-8
+        assert np.abs(evm - ev64).max() <= 1e-10 * ev64.max()
+        rho = g.pb.node_rho()
+        for i in (0, 9, 19):
+            v = evecs[i * 3 * N ** 3:(i + 1) * 3 * N ** 3].cpu().numpy().reshape(3, -1)
+            lam = ev64[i] / g.to_si
+            Mv = rho[None, :] * v
+            r = O.apply_full(g.pb, kappa, v) - lam * Mv
+            assert np.linalg.norm(r) <= 1e-8 * abs(lam) * np.linalg.norm(Mv), i
+            assert abs(np.real(np.vdot(v, Mv)) - 1.0) <= 1e-9
     finally:
         g.close()
 

@@ -52,6 +52,17 @@ def test_block_index_rejects_bad_arguments(pc):
 def test_options_defaults(pc):
     o = pc.pc_options_default()
     assert o.tol == 1e-8 and o.block_size == 2 and o.precision == pc.PC_PREC_FP64
+    assert o.max_basis == 24 and o.kbatch == 0 and o.precond_fp32 == 1
+
+
+def test_lockstep_entry_points_reject_bad_arguments(pc):
+    import ctypes as ct
+    k = (ct.c_double * 6)(0, 0, 0, 0.5, 0, 0)
+    ev = (ct.c_double * 8)()
+    assert pc.lib.pc_eigs_multi(None, 2, k, 4, float("nan"), None, ev, None, None) == pc.PC_EINVAL
+    assert pc.lib.pc_set_k_multi(None, 2, k) == pc.PC_EINVAL
+    assert pc.lib.pc_eigs_multi_max(None) == pc.PC_EINVAL
+    assert pc.lib.pc_apply_batch_k(None, pc.PC_C64, 0, None, None, None, None, None, None) == pc.PC_EINVAL
 
 
 def test_null_grid_is_rejected(pc):

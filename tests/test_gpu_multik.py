@@ -7,7 +7,8 @@ vector are independent), through the C ABI, against the oracle and against one-a
 * pc_eigs_multi: the lowest eigenvalues at four Bloch vectors (Gamma, X, M, a generic vector)
   solved in lockstep equal four pc_eigs calls (1e-10 relative, FP64 and mixed precision), with the
   zero modes deflated at Gamma only and every true residual below the tolerance.
-* pc_eigs_batch with lockstep chunks equals pc_eigs per Bloch vector on ragged grids.
+* pc_eigs_batch with lockstep chunks equals pc_eigs per Bloch vector on ragged grids; so do
+  lockstep solves of the full space and of a nodewise material.
 * Grids whose block transform falls back to the library FFT accept one Bloch vector at a time.
 """
 
@@ -179,5 +180,42 @@ def test_fallback_fft_grid_solves_one_vector_at_a_time(pc):
         ev, _, infos = pc.pc_eigs_multi(g, KAPPAS[3:], 4)
         e1, _, _ = pc.pc_eigs(g, KAPPAS[3], 4)
         assert np.abs(ev[0] - e1).max() <= 1e-10 * e1.max()
+    finally:
+        pc.pc_grid_destroy(g)
+
+
+def test_eigs_multi_full_space_equals_one_at_a_time(pc):
+    """Lockstep solves of the full space (one space per Bloch vector, the preconditioner through the
+    four block transforms of each vector's slot) equal pc_eigs per Bloch vector."""
+    N = 12
+    cell = two_phase_sphere(N, 0.35, 5)
+    g = pc.pc_grid_create(N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+    try:
+        opt = pc.pc_options_default(full_space=1)
+        ev, bo, infos = pc.pc_eigs_multi(g, KAPPAS, 10, opt=opt)
+        for i, k in enumerate(KAPPAS):
+            assert infos[i]["status"] == pc.PC_OK and (bo[i] == -1).all()
+            e1, _, _ = pc.pc_eigs(g, k, 10, opt=opt)
+            assert np.abs(ev[i] - e1).max() <= 1e-10 * e1.max()
+    finally:
+        pc.pc_grid_destroy(g)
+
+
+def test_eigs_multi_nodewise_material_equals_one_at_a_time(pc):
+    """A nodewise material (two-pass complex128 kernels with per-node stiffness) solved at several
+    Bloch vectors in lockstep equals pc_eigs per Bloch vector."""
+    from paper_2606_03599_gb300 import autodiff
+    N = 12
+    cell = two_phase_sphere(N, 0.35, 6)
+    C21, rho = autodiff.two_phase_nodewise(cell)
+    rng = np.random.default_rng(3)
+    rho = rho * (1 + 0.1 * rng.uniform(size=rho.shape))
+    g = pc.pc_grid_create_nodewise(N, C21, rho, a_lat=cell.a_lat)
+    try:
+        ev, _, infos = pc.pc_eigs_multi(g, KAPPAS, 8)
+        for i, k in enumerate(KAPPAS):
+            assert infos[i]["status"] == pc.PC_OK
+            e1, _, _ = pc.pc_eigs(g, k, 8)
+            assert np.abs(ev[i] - e1).max() <= 1e-10 * e1.max()
     finally:
         pc.pc_grid_destroy(g)

@@ -543,8 +543,9 @@ def differentiation_run(args, emit=True, nk=10):
     stiffness and (N^3,) density tensors): gradients of the lowest 12 eigenvalues at `nk` Bloch
     vectors of the SC path and of the width of the gap between bands 6 and 7 over them, through the
     torch.autograd functions whose inputs are those tensors (forward: the GPU solve of the nodewise
-    grid; backward: the adjoint kernel).  Reported: seconds per Bloch vector for solve +
-    eigenvectors + adjoint, the gap gradient's time, and central differences with a relative step of
+    grid, all Bloch vectors in lockstep; backward: the adjoint kernel).  Reported: seconds per Bloch
+    vector for solve + eigenvectors + adjoint (lockstep, and one Bloch vector at a time, with the
+    difference of the two summed gradients), the gap gradient's time, and central differences with a relative step of
     1e-6 along `--fd-dirs` seeded random directions in (C, rho) against the autograd gradient of
     sum(lambda) at one Bloch vector."""
     import numpy as np
@@ -568,15 +569,31 @@ def differentiation_run(args, emit=True, nk=10):
     kfd = min(3, len(ks) - 1)
     t0 = time.perf_counter()
     grad_fd_k = None
+    sum_gc, sum_gr = 0.0, 0.0
     for i, k in enumerate(ks):
         lam = ad.band_eigenvalues_nodewise(Ct, rt, N, k, nev, opt=opt)
         lam.sum().backward()
         if i == kfd:
             grad_fd_k = (Ct.grad.numpy().copy(), rt.grad.numpy().copy(), lam.detach().numpy())
+        sum_gc = sum_gc + Ct.grad.numpy()
+        sum_gr = sum_gr + rt.grad.numpy()
         Ct.grad = None
         rt.grad = None
     torch.cuda.synchronize()
+    t_grad_one = (time.perf_counter() - t0) / len(ks)
+    # the same gradients with every Bloch vector solved in lockstep (one forward, summed adjoints)
+    Cl = torch.tensor(C21, dtype=torch.float64, requires_grad=True)
+    rl = torch.tensor(rho, dtype=torch.float64, requires_grad=True)
+    ad.band_structure_nodewise(Cl, rl, N, ks[:2], nev, opt=opt).sum().backward()  # untimed: state
+    Cl.grad = None
+    rl.grad = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ad.band_structure_nodewise(Cl, rl, N, ks, nev, opt=opt).sum().backward()
+    torch.cuda.synchronize()
     t_grad = (time.perf_counter() - t0) / len(ks)
+    lock_diff = max(float(np.abs(Cl.grad.numpy() - sum_gc).max() / np.abs(sum_gc).max()),
+                    float(np.abs(rl.grad.numpy() - sum_gr).max() / np.abs(sum_gr).max()))
     Cg = torch.tensor(C21, dtype=torch.float64, requires_grad=True)
     rg = torch.tensor(rho, dtype=torch.float64, requires_grad=True)
     t0 = time.perf_counter()
@@ -605,7 +622,9 @@ def differentiation_run(args, emit=True, nk=10):
                                    "12 bands, gap between bands 6 and 7, resid 1e-8" % len(ks),
                        "k_points": len(ks), "fd_directions": max(1, args.fd_dirs), "fd_relative_step": h,
                        "fd_direction_scale": {"C": sC, "rho": sr}},
-            "grad_s_per_kpoint": t_grad, "gap_hz": float(gap.detach()), "gap_grad_s": t_gap,
+            "grad_s_per_kpoint": t_grad, "grad_s_per_kpoint_one_at_a_time": t_grad_one,
+            "lockstep_grad_rel_diff_vs_one_at_a_time": lock_diff,
+            "gap_hz": float(gap.detach()), "gap_grad_s": t_gap,
             "gap_grad_norm": float(np.sqrt(float((Cg.grad ** 2).sum()) + float((rg.grad ** 2).sum()))),
             "fd_rel_err_sum_lambda": errs, "fd_rel_err_max": max(errs)}
     if emit:

@@ -286,14 +286,15 @@ int pc_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_o
  * residual apply over all unfinished spaces, so a launch serves several Bloch vectors (each
  * stencil item and preconditioner system carries its slot).  Results equal nk pc_eigs calls up to
  * rounding (same start vectors, same tests).  kappas: host [nk][3].  evals: host [nk][nev];
- * block_of: NULL or host [nk][nev]; info: NULL or nk entries -- status, zero_modes and
+ * evecs: NULL or device [nk][nev][3][N^3] complex128, full-space layout, M_h-normalised (zero for a
+ * Bloch vector that did not converge); block_of: NULL or host [nk][nev]; info: NULL or nk entries -- status, zero_modes and
  * max_rel_resid per vector; outer_iters, inner_solves, pcg_iters, max_pcg_iters and seconds are
  * totals of the whole call, repeated in every entry.  Afterwards the grid's current Bloch vector
  * (pc_set_k) is kappas[0:3].  nk > 1 needs a grid whose block transform runs in the library's own
  * kernels (pc_eigs_multi_max > 1), else PC_EINVAL.  Returns PC_ENOCONV when some vector did not
  * converge (its info status says which; the others are valid).  Synchronous. */
 int pc_eigs_multi(pc_grid* g, int nk, const double* kappas, int nev, double sigma, const pc_options* opt,
-                  double* evals, int* block_of, pc_eigs_info* info);
+                  double* evals, void* evecs, int* block_of, pc_eigs_info* info);
 
 /* Largest nk pc_eigs_multi accepts for this grid (32, or 1 when the grid's quarter-grid length
  * N/2 has a prime factor above 16 or exceeds 96). */

@@ -113,7 +113,7 @@ def _load():
         "pc_default_sigma": ([vp], cd),
         "pc_eigs": ([vp, dp, ci, cd, ctypes.POINTER(c_options), dp, vp, ctypes.POINTER(ci),
                      ctypes.POINTER(c_eigs_info)], ci),
-        "pc_eigs_multi": ([vp, ci, dp, ci, cd, ctypes.POINTER(c_options), dp, ctypes.POINTER(ci),
+        "pc_eigs_multi": ([vp, ci, dp, ci, cd, ctypes.POINTER(c_options), dp, vp, ctypes.POINTER(ci),
                            ctypes.POINTER(c_eigs_info)], ci),
         "pc_eigs_multi_max": ([vp], ci),
         "pc_set_k_multi": ([vp, ci, dp], ci),
@@ -329,9 +329,9 @@ def pc_eigs(g, kappa, nev, sigma=float("nan"), opt=None, evecs=None, raise_on_fa
     return ev, np.array(list(bo)), d
 
 
-def pc_eigs_multi(g, kappas, nev, sigma=float("nan"), opt=None, raise_on_fail=True):
+def pc_eigs_multi(g, kappas, nev, sigma=float("nan"), opt=None, evecs=None, raise_on_fail=True):
     """Several Bloch vectors of one grid in lockstep.  Returns (evals [nk][nev], block_of [nk][nev],
-    list of per-vector info dicts)."""
+    list of per-vector info dicts); evecs: optional device complex128 buffer of nk * nev * 3 N^3."""
     ks = np.ascontiguousarray(np.asarray(kappas, dtype=np.float64).reshape(-1, 3))
     nk = ks.shape[0]
     opt = opt if opt is not None else pc_options_default()
@@ -339,7 +339,7 @@ def pc_eigs_multi(g, kappas, nev, sigma=float("nan"), opt=None, raise_on_fail=Tr
     bo = np.empty((nk, int(nev)), dtype=np.int32)
     infos = (c_eigs_info * nk)()
     rc = lib.pc_eigs_multi(g, nk, ks.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nev), float(sigma),
-                           ctypes.byref(opt), ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           ctypes.byref(opt), ev.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(evecs),
                            bo.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), infos)
     if raise_on_fail:
         _check(rc)

@@ -8,8 +8,8 @@ Degenerate clusters are treated as subspaces: eigenvalues closer than a
 relative ``cluster_tol`` share the mean of their incoming gradients, which is
 the gradient of any symmetric function of the cluster (basis independent).
 
-``NodewiseBandEigenvalues`` and ``NodewiseBandGap`` take the nodewise material itself as
-their inputs: a (N^3, 21) tensor of the independent Voigt stiffness entries of every node
+``NodewiseBandEigenvalues``, ``NodewiseBandStructure`` (several Bloch vectors, solved in
+lockstep) and ``NodewiseBandGap`` take the nodewise material itself as their inputs: a (N^3, 21) tensor of the independent Voigt stiffness entries of every node
 and a (N^3,) density tensor (the general pencil of Eq. discrete_GEP_main, solved on a grid
 made by ``pc_grid_create_nodewise``); their gradients are the (N^3, 21) and (N^3,)
 Hellmann-Feynman gradients.  ``BandEigenvalues`` differentiates with respect to the
@@ -122,18 +122,47 @@ def _solve_nodewise(C21, rho, N, kappa, nev, a_lat, opt):
     return ev, evecs
 
 
+def _solve_nodewise_multi(C21, rho, N, kappas, nev, a_lat, opt):
+    """Eigenvalues ([nk][nev] numpy, SI) and M-normalised full-space eigenvectors (a list of nk device
+    complex128 tensors of nev * 3 N^3) of the nodewise material at several Bloch vectors, solved in
+    lockstep chunks (pc_eigs_multi; one at a time where the grid's size needs the library FFT)."""
+    ks = np.ascontiguousarray(np.asarray(kappas, dtype=np.float64).reshape(-1, 3))
+    g = pc.pc_grid_create_nodewise(N, C21, rho, a_lat=a_lat)
+    try:
+        kb = pc.pc_eigs_multi_max(g)
+        vn = nev * 3 * N ** 3
+        evs, vecs = [], []
+        for c in range(0, len(ks), kb):
+            ch = ks[c:c + kb]
+            buf = torch.empty(len(ch) * vn, dtype=torch.complex128, device="cuda")
+            ev, _, _ = pc.pc_eigs_multi(g, ch, nev, opt=opt, evecs=buf)
+            evs.append(ev)
+            vecs += list(buf.view(len(ch), vn).unbind(0))
+    finally:
+        pc.pc_grid_destroy(g)
+    return np.concatenate(evs, axis=0), vecs
+
+
 def _adjoint(N, a_lat, kappa, evecs, ev, w):
     """sum_v w_v d lambda_v / d(C_l, rho_l) for full-space eigenvectors: (dC [N^3, 21], drho [N^3])
     device tensors.  The adjoint kernel reads the grid's geometry, units and Bloch vector only, so a
     grid of any material with the same N and lattice serves."""
+    return _adjoint_many(N, a_lat, [(kappa, evecs, ev, w)])
+
+
+def _adjoint_many(N, a_lat, terms):
+    """The sum of _adjoint over terms (kappa, evecs, ev, w) on one scratch grid."""
     n = N ** 3
     C = np.stack([np.eye(6), np.eye(6)]) * 1e9
     g = pc.pc_grid_create(N, C, np.array([1e3, 1e3]), a_lat=a_lat)
     try:
         dC = torch.zeros(21 * n, dtype=torch.float64, device="cuda")
         drho = torch.zeros(n, dtype=torch.float64, device="cuda")
-        pc.pc_set_k(g, kappa)
-        pc.pc_eig_grad(g, -1, evecs, ev, w, dC, drho)
+        for kappa, evecs, ev, w in terms:
+            if not np.any(w):
+                continue
+            pc.pc_set_k(g, kappa)
+            pc.pc_eig_grad(g, -1, evecs, ev, w, dC, drho)
     finally:
         pc.pc_grid_destroy(g)
     return dC.view(21, n).T, drho
@@ -178,14 +207,13 @@ class NodewiseBandGap(torch.autograd.Function):
     def forward(ctx, C21, rho, N, kappas, lo, a_lat=None, opt=None, cluster_tol=1e-9):
         hi, nev = lo + 1, lo + 3
         Cn, rn = C21.detach().cpu().numpy(), rho.detach().cpu().numpy()
-        top = bot = None
-        for k in kappas:
-            ev, evecs = _solve_nodewise(Cn, rn, N, k, nev, a_lat, opt)
-            f = np.sqrt(ev) / (2 * np.pi)
-            if top is None or f[hi] < top[0]:
-                top = (f[hi], k, ev, evecs)
-            if bot is None or f[lo] > bot[0]:
-                bot = (f[lo], k, ev, evecs)
+        evs, vecs = _solve_nodewise_multi(Cn, rn, N, kappas, nev, a_lat, opt)  # all Bloch vectors in lockstep
+        f = np.sqrt(evs) / (2 * np.pi)
+        it, ib = int(np.argmin(f[:, hi])), int(np.argmax(f[:, lo]))
+        # keep only the two active Bloch vectors' eigenvectors (copies: the rest can be freed)
+        top = (f[it, hi], kappas[it], evs[it], vecs[it].clone())
+        bot = (f[ib, lo], kappas[ib], evs[ib], vecs[ib].clone() if ib != it else top[3])
+        del vecs
         ctx.N, ctx.a_lat, ctx.lo, ctx.top, ctx.bot, ctx.cluster_tol = N, a_lat, lo, top, bot, cluster_tol
         return torch.as_tensor(top[0] - bot[0], dtype=torch.float64, device=C21.device)
 
@@ -205,6 +233,37 @@ class NodewiseBandGap(torch.autograd.Function):
         ctx.top = ctx.bot = None
         dev = grad_out.device
         return (dC.to(dev), drho.to(dev)) + (None,) * 6
+
+
+class NodewiseBandStructure(torch.autograd.Function):
+    """lambda(C, rho) at several Bloch vectors: the lowest ``nev`` non-zero eigenvalues (SI) at each
+    of ``kappas`` ([nk, nev]), as a function of the nodewise material (as
+    ``NodewiseBandEigenvalues``); the forward solves all Bloch vectors in lockstep
+    (pc_eigs_multi), the backward sums the adjoint over them, with numerically degenerate
+    eigenvalues treated as subspaces at each Bloch vector."""
+
+    @staticmethod
+    def forward(ctx, C21, rho, N, kappas, nev, a_lat=None, opt=None, cluster_tol=1e-9):
+        evs, vecs = _solve_nodewise_multi(C21.detach().cpu().numpy(), rho.detach().cpu().numpy(), N, kappas, nev,
+                                          a_lat, opt)
+        ctx.N, ctx.a_lat, ctx.kappas, ctx.evs, ctx.vecs, ctx.cluster_tol = N, a_lat, kappas, evs, vecs, cluster_tol
+        return torch.as_tensor(evs, dtype=torch.float64, device=C21.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        go = grad_out.detach().cpu().numpy()
+        terms = [(k, ctx.vecs[i], ctx.evs[i], subspace_weights(ctx.evs[i], go[i], ctx.cluster_tol))
+                 for i, k in enumerate(ctx.kappas)]
+        dC, drho = _adjoint_many(ctx.N, ctx.a_lat, terms)
+        ctx.vecs = None
+        dev = grad_out.device
+        return (dC.to(dev), drho.to(dev)) + (None,) * 6
+
+
+def band_structure_nodewise(C21, rho, N, kappas, nev, a_lat=None, opt=None):
+    """Differentiable lowest ``nev`` eigenvalues (SI) at every Bloch vector of ``kappas`` ([nk, nev])
+    of the nodewise material (C21, rho), the Bloch vectors solved in lockstep."""
+    return NodewiseBandStructure.apply(C21, rho, N, kappas, nev, a_lat, opt)
 
 
 def band_gap_nodewise(C21, rho, N, kappas, lo, a_lat=None, opt=None):

@@ -166,7 +166,7 @@ extern "C" int pc_eigs_batch(pc_batch_job* jobs, int njobs, const pc_options* op
             std::vector<pc_eigs_info> inf(it.nk);
             std::memset(inf.data(), 0, sizeof(pc_eigs_info) * it.nk);
             int rc = pc_eigs_multi(clone, it.nk, J.kappas + 3 * it.k, J.nev, J.sigma, &o,
-                                   J.evals + (size_t)it.k * J.nev,
+                                   J.evals + (size_t)it.k * J.nev, nullptr,
                                    J.block_of ? J.block_of + (size_t)it.k * J.nev : nullptr, inf.data());
             const bool soft = rc == PC_OK || rc == PC_ENOCONV;  // per Bloch vector statuses are valid
             int nfail = 0;

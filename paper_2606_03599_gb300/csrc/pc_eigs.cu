@@ -1165,36 +1165,40 @@ static int run_eigs(pc_grid* g, int nk, const double* kappas, int nev, double si
             }
         }
     }
-    if (evecs && nk == 1 && status == PC_OK) {
-        // recompute Ritz vectors for the merged values and write them in full-space layout
-        double2* out = static_cast<double2*>(evecs);
-        PC_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(double2) * (size_t)nev * 3 * g->n, E.s));
-        std::vector<char> used(nev, 0);  // equal eigenvalues of one block get distinct slots
-        for (int i = 0; i < nspace; ++i) {
-            Space& S = E.sp[i];
-            ritz(E, S);
-            const int ncand = (int)S.lam.size();
-            if (ncand == 0) continue;
-            const int mm = S.m_exp;
-            std::vector<cd> Sk((size_t)mm * ncand);
-            for (int j = 0; j < ncand; ++j)
-                for (int r = 0; r < mm; ++r) Sk[r + j * mm] = S.S[r + j * mm];
-            PC_TRY(gemm_nn_host(E, S.V, mm, Sk, ncand, E.Y, S.vs, kOne, kZero));
-            for (int j = 0; j < ncand; ++j) {
-                int slot = -1;
-                for (int q = 0; q < nev && slot < 0; ++q)
-                    if (!used[q] && mblock[0][q] == S.block && merged[0][q] == S.lam[j]) slot = q;
-                if (slot < 0) continue;
-                used[slot] = 1;
-                double2* dst = out + (size_t)slot * 3 * g->n;
-                if (S.block < 0)
-                    PC_CUDA_TRY(cudaMemcpyAsync(dst, E.Y + (int64_t)j * S.vs, sizeof(double2) * S.vs,
-                                                cudaMemcpyDeviceToDevice, E.s));
-                else
-                    PC_TRY(launch_transfer(PC_C128, E.Y + (int64_t)j * S.vs, dst, g->N, S.block, 1, E.s));
+    if (evecs) {
+        // recompute Ritz vectors for the merged values and write them in full-space layout,
+        // [Bloch vector][nev][3][n]; the vectors of a Bloch vector that did not converge stay zero
+        const size_t vn = (size_t)3 * g->n;
+        PC_CUDA_TRY(cudaMemsetAsync(evecs, 0, sizeof(double2) * (size_t)nk * nev * vn, E.s));
+        for (int ks = 0; ks < nk; ++ks) {
+            if (!kdone[ks]) continue;
+            double2* out = static_cast<double2*>(evecs) + (size_t)ks * nev * vn;
+            std::vector<char> used(nev, 0);  // equal eigenvalues of one block get distinct slots
+            for (int b = 0; b < nper; ++b) {
+                Space& S = E.sp[ks * nper + b];
+                ritz(E, S);
+                const int ncand = (int)S.lam.size();
+                if (ncand == 0) continue;
+                const int mm = S.m_exp;
+                std::vector<cd> Sk((size_t)mm * ncand);
+                for (int j = 0; j < ncand; ++j)
+                    for (int r = 0; r < mm; ++r) Sk[r + j * mm] = S.S[r + j * mm];
+                PC_TRY(gemm_nn_host(E, S.V, mm, Sk, ncand, E.Y, S.vs, kOne, kZero));
+                for (int j = 0; j < ncand; ++j) {
+                    int slot = -1;
+                    for (int q = 0; q < nev && slot < 0; ++q)
+                        if (!used[q] && mblock[ks][q] == S.block && merged[ks][q] == S.lam[j]) slot = q;
+                    if (slot < 0) continue;
+                    used[slot] = 1;
+                    double2* dst = out + (size_t)slot * vn;
+                    if (S.block < 0)
+                        PC_CUDA_TRY(cudaMemcpyAsync(dst, E.Y + (int64_t)j * S.vs, sizeof(double2) * S.vs,
+                                                    cudaMemcpyDeviceToDevice, E.s));
+                    else
+                        PC_TRY(launch_transfer(PC_C128, E.Y + (int64_t)j * S.vs, dst, g->N, S.block, 1, E.s));
+                }
             }
         }
-        PC_CUDA_TRY(cudaStreamSynchronize(E.s));
     }
     PC_CUDA_TRY(cudaStreamSynchronize(E.s));
     if (info) {
@@ -1318,14 +1322,14 @@ int pc_eigs(pc_grid* g, const double kappa[3], int nev, double sigma, const pc_o
 }
 
 int pc_eigs_multi(pc_grid* g, int nk, const double* kappas, int nev, double sigma, const pc_options* opt,
-                  double* evals, int* block_of, pc_eigs_info* info) {
+                  double* evals, void* evecs, int* block_of, pc_eigs_info* info) {
     if (!g || !kappas || !evals) return fail(PC_EINVAL, "pc_eigs_multi: null argument");
     if (nk < 1 || nk > kMaxKSlots) return fail(PC_EINVAL, "pc_eigs_multi: nk must be in 1..32");
     pc_options def;
     pc_options_default(&def);
     const pc_options* o = opt ? opt : &def;
     PC_TRY(check_eigs_args(g, nev, sigma, o, "pc_eigs_multi"));
-    const int rc = run_eigs(g, nk, kappas, nev, sigma, o, evals, nullptr, block_of, info);
+    const int rc = run_eigs(g, nk, kappas, nev, sigma, o, evals, evecs, block_of, info);
     const int st = grid_device_status(g, (cudaStream_t)o->stream);
     return st != PC_OK ? st : rc;
 }

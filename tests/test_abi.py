@@ -59,7 +59,7 @@ def test_lockstep_entry_points_reject_bad_arguments(pc):
     import ctypes as ct
     k = (ct.c_double * 6)(0, 0, 0, 0.5, 0, 0)
     ev = (ct.c_double * 8)()
-    assert pc.lib.pc_eigs_multi(None, 2, k, 4, float("nan"), None, ev, None, None) == pc.PC_EINVAL
+    assert pc.lib.pc_eigs_multi(None, 2, k, 4, float("nan"), None, ev, None, None, None) == pc.PC_EINVAL
     assert pc.lib.pc_set_k_multi(None, 2, k) == pc.PC_EINVAL
     assert pc.lib.pc_eigs_multi_max(None) == pc.PC_EINVAL
     assert pc.lib.pc_apply_batch_k(None, pc.PC_C64, 0, None, None, None, None, None, None) == pc.PC_EINVAL

@@ -11,6 +11,8 @@ and the autograd functions whose inputs are that material, against the oracle.
   differences with a relative step of 1e-6 along seeded random directions in (C, rho) (the
   forward evaluated by the GPU solver on the perturbed nodewise material).
 * NodewiseBandGap: the gap-width gradient against central differences along seeded directions.
+* NodewiseBandStructure (lockstep over several Bloch vectors) = NodewiseBandEigenvalues per
+  Bloch vector, eigenvalues and summed gradients.
 """
 
 import numpy as np
@@ -218,3 +220,31 @@ def test_nodewise_band_gap_matches_central_differences(pc, ad):
         fd = (vals[0] - vals[1]) / (2 * h)
         an = float(np.sum(gc * dCd) + np.sum(gr * drd))
         assert abs(fd - an) <= 1e-5 * abs(an) + 1e-6
+
+
+def test_band_structure_autograd_equals_per_bloch_vector_autograd(pc, ad):
+    """NodewiseBandStructure (all Bloch vectors in one lockstep solve, eigenvectors from
+    pc_eigs_multi) gives the per-Bloch-vector eigenvalues and the summed gradient of
+    NodewiseBandEigenvalues called once per Bloch vector."""
+    import torch
+    N = 8
+    C21, rho, _, A, _ = perturbed_material(N, 17)
+    kappas = [[0.0, 0.0, 0.0], [0.3, 0.1, 0.2], [0.5, 0.5, 0.0]]
+    nev = 6
+    w = np.array([[1.0, -0.5, 0.75, 2.0, -1.25, 0.3], [0.2, 0.4, -1.0, 0.5, 0.9, -0.3],
+                  [1.5, 0.1, 0.6, -0.8, 0.25, 1.1]])
+    Ct = torch.tensor(C21, dtype=torch.float64, requires_grad=True)
+    rt = torch.tensor(rho, dtype=torch.float64, requires_grad=True)
+    lam = ad.band_structure_nodewise(Ct, rt, N, kappas, nev, a_lat=A)
+    (lam * torch.as_tensor(w)).sum().backward()
+    gc_sum, gr_sum = 0.0, 0.0
+    for i, k in enumerate(kappas):
+        C1 = torch.tensor(C21, dtype=torch.float64, requires_grad=True)
+        r1 = torch.tensor(rho, dtype=torch.float64, requires_grad=True)
+        l1 = ad.band_eigenvalues_nodewise(C1, r1, N, k, nev, a_lat=A)
+        assert np.abs(l1.detach().numpy() - lam[i].detach().numpy()).max() <= 1e-10 * l1.detach().numpy().max()
+        (l1 * torch.as_tensor(w[i])).sum().backward()
+        gc_sum = gc_sum + C1.grad.numpy()
+        gr_sum = gr_sum + r1.grad.numpy()
+    assert np.abs(Ct.grad.numpy() - gc_sum).max() <= 1e-8 * np.abs(gc_sum).max()
+    assert np.abs(rt.grad.numpy() - gr_sum).max() <= 1e-8 * np.abs(gr_sum).max()

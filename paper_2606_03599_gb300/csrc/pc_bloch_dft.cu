@@ -44,6 +44,12 @@ constexpr int kDftMaxFactor = 16;
 constexpr int kDftMaxN = 96;
 constexpr int kPlaneThreads = 128;   // one plane per CTA of the plane kernels
 constexpr int kPencilThreads = 256;
+// Threads per CTA for compile-time factors: the large planes and pencils (n >= 40) hold 25-60 KB of
+// shared memory per CTA, so few CTAs fit on an SM; more threads per CTA keep the SM's warps up.
+template <int N1, int N2>
+constexpr int plane_nt() { return N1 > 0 && N1 * N2 >= 40 ? 512 : kPlaneThreads; }
+template <int N1, int N2>
+constexpr int pencil_nt() { return N1 > 0 && N1 * N2 >= 40 ? 512 : kPencilThreads; }
 constexpr int kPencilTileMax = 16;  // p positions per pencil CTA: the largest divisor of n up to this
 
 template <typename C> struct RTy;
@@ -186,7 +192,7 @@ __device__ __forceinline__ C t_par2(const TT* ea, const TT* eb, const TT* eg, in
 // K1: planes_per_cta(n) planes per CTA (plane id = ((sys * 3 + comp) * 2 + par) * n + k'): w (type Ci)
 // pre-twiddled into the work buffer W (type C), 2D DFT over (a, b).  W layout [sys][comp][par][k'][q][p].
 template <int N1, int N2, typename C, typename Ci>
-__global__ void __launch_bounds__(kPlaneThreads)
+__global__ void __launch_bounds__(plane_nt<N1, N2>())
     bdft_plane_fwd(const Ci* __restrict__ w, C* __restrict__ W, const C* __restrict__ wn_g, const C* __restrict__ twa,
                    const C* __restrict__ twb, const C* __restrict__ twk, int n_rt, int n1, int n2, int nplanes,
                    int64_t sys_stride_in, int64_t sys_stride_out, const int* __restrict__ skip, int conj_tw,
@@ -246,7 +252,7 @@ __global__ void __launch_bounds__(kPlaneThreads)
 // pre-twiddle), scale, into z (type Co); with part non-null also the partial Re <r, z> of each plane
 // (partial index = plane id within its system, 6 n per system).
 template <int N1, int N2, typename C, typename Co>
-__global__ void __launch_bounds__(kPlaneThreads)
+__global__ void __launch_bounds__(plane_nt<N1, N2>())
     bdft_plane_inv(const C* __restrict__ W, Co* __restrict__ z, const Co* __restrict__ r, const C* __restrict__ wn_g,
                    const C* __restrict__ twa, const C* __restrict__ twb, const C* __restrict__ twk, int n_rt, int n1,
                    int n2, int nplanes, int64_t sys_stride_in, int64_t sys_stride_out, double scale,
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(kPlaneThreads)
         }
     }
     if (part) {
-        __shared__ double red[kPlaneThreads / 32];
+        __shared__ double red[plane_nt<N1, N2>() / 32];
         for (int j = 0; j < pp; ++j) {
             double v = 0.0;
 #pragma unroll
@@ -341,7 +347,7 @@ __global__ void __launch_bounds__(kPlaneThreads)
 // mode order [comp][r < 2n][q][p]); 2 = inverse block transform (reads `out`'s layout from W, inverse
 // butterfly, inverse DFT over k', written to W).
 template <int N1, int N2, typename C, typename R, typename TT>
-__global__ void __launch_bounds__(kPencilThreads)
+__global__ void __launch_bounds__(pencil_nt<N1, N2>())
     bdft_pencil(C* __restrict__ W, C* __restrict__ out, const C* __restrict__ wn_g, const R* __restrict__ Aref,
                 const TT* __restrict__ ea, const TT* __restrict__ eb, const TT* __restrict__ eg,
                 const int* __restrict__ sys_block, const int* __restrict__ skip, int n_rt, int n1, int n2,
@@ -513,15 +519,15 @@ static int precond_launch(int n, int n1, int n2, int nsys, const V* r, V* z, C* 
     PC_TRY(allow_smem(bdft_pencil<N1, N2, C, R, TT>, sq));
     PC_TRY(allow_smem(bdft_plane_inv<N1, N2, C, V>, sp));
     const int planes = nsys * 6 * n, pctas = (planes + planes_per_cta(n) - 1) / planes_per_cta(n);
-    bdft_plane_fwd<N1, N2, C, V><<<pctas, kPlaneThreads, sp, s>>>(r, W, wn, twa, twb, twk, n, n1, n2, planes, vs, vs,
+    bdft_plane_fwd<N1, N2, C, V><<<pctas, (plane_nt<N1, N2>()), sp, s>>>(r, W, wn, twa, twb, twk, n, n1, n2, planes, vs, vs,
                                                                skip, 0, sys_k, tab_stride);
     note_launch();
     const int tiles = n / pencil_tile(n);
-    bdft_pencil<N1, N2, C, R, TT><<<nsys * n * tiles, kPencilThreads, sq, s>>>(
+    bdft_pencil<N1, N2, C, R, TT><<<nsys * n * tiles, (pencil_nt<N1, N2>()), sq, s>>>(
         W, nullptr, wn, Aref, ea, eb, eg, sys_block, skip, n, n1, n2, vs, shift_rho, scale, 0, sys_k, tab_stride,
         aref_stride);
     note_launch();
-    bdft_plane_inv<N1, N2, C, V><<<pctas, kPlaneThreads, sp, s>>>(W, z, r, wn, twa, twb, twk, n, n1, n2, planes, vs,
+    bdft_plane_inv<N1, N2, C, V><<<pctas, (plane_nt<N1, N2>()), sp, s>>>(W, z, r, wn, twa, twb, twk, n, n1, n2, planes, vs,
                                                                vs, 1.0, skip, part, bloch_dft_partials(n), sys_k,
                                                                tab_stride);
     note_launch();
@@ -542,17 +548,17 @@ static int fourier_launch(int n, int n1, int n2, int inverse, const C* in, C* ou
     const int planes = 6 * n, pctas = (planes + planes_per_cta(n) - 1) / planes_per_cta(n);
     const int tiles = n / pencil_tile(n);
     if (!inverse) {
-        bdft_plane_fwd<N1, N2, C, C><<<pctas, kPlaneThreads, sp, s>>>(in, W, wn, twa, twb, twk, n, n1, n2, planes, vs,
+        bdft_plane_fwd<N1, N2, C, C><<<pctas, (plane_nt<N1, N2>()), sp, s>>>(in, W, wn, twa, twb, twk, n, n1, n2, planes, vs,
                                                                    vs, nullptr, 0, nullptr, 0);
         note_launch();
-        bdft_pencil<N1, N2, C, R, C><<<n * tiles, kPencilThreads, sq, s>>>(
+        bdft_pencil<N1, N2, C, R, C><<<n * tiles, (pencil_nt<N1, N2>()), sq, s>>>(
             W, out, wn, nullptr, ea, eb, eg, d_block, nullptr, n, n1, n2, vs, 0.0, scale, 1, nullptr, 0, 0);
         note_launch();
     } else {
-        bdft_pencil<N1, N2, C, R, C><<<n * tiles, kPencilThreads, sq, s>>>(
+        bdft_pencil<N1, N2, C, R, C><<<n * tiles, (pencil_nt<N1, N2>()), sq, s>>>(
             W, const_cast<C*>(in), wn, nullptr, ea, eb, eg, d_block, nullptr, n, n1, n2, vs, 0.0, 1.0, 2, nullptr, 0, 0);
         note_launch();
-        bdft_plane_inv<N1, N2, C, C><<<pctas, kPlaneThreads, sp, s>>>(W, out, nullptr, wn, twa, twb, twk, n, n1, n2,
+        bdft_plane_inv<N1, N2, C, C><<<pctas, (plane_nt<N1, N2>()), sp, s>>>(W, out, nullptr, wn, twa, twb, twk, n, n1, n2,
                                                                    planes, vs, vs, scale, nullptr, nullptr, 0, nullptr,
                                                                    0);
         note_launch();

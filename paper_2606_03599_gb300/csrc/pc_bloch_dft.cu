@@ -189,8 +189,9 @@ __device__ __forceinline__ C t_par2(const TT* ea, const TT* eb, const TT* eg, in
     return t;
 }
 
-// K1: planes_per_cta(n) planes per CTA (plane id = ((sys * 3 + comp) * 2 + par) * n + k'): w (type Ci)
+// K1: one plane per CTA (plane id = ((sys * 3 + comp) * 2 + par) * n + k' = blockIdx.x): w (type Ci)
 // pre-twiddled into the work buffer W (type C), 2D DFT over (a, b).  W layout [sys][comp][par][k'][q][p].
+// The loads run four per thread before their shared-memory stores, so several are in flight.
 template <int N1, int N2, typename C, typename Ci>
 __global__ void __launch_bounds__(plane_nt<N1, N2>())
     bdft_plane_fwd(const Ci* __restrict__ w, C* __restrict__ W, const C* __restrict__ wn_g, const C* __restrict__ twa,
@@ -203,54 +204,44 @@ __global__ void __launch_bounds__(plane_nt<N1, N2>())
         n1 = N1;
         n2 = N2;
     }
-    const int pp = planes_per_cta(n), nn = n * n;
+    const int nn = n * n;
+    const int pl = blockIdx.x;
+    if (pl >= nplanes) return;
+    const int kp = pl % n, rest = pl / n;
+    const int par = rest & 1, comp = (rest >> 1) % 3, sys = rest / 6;
+    if (skip && skip[sys]) return;  // the whole CTA: nothing of this system is written
     C* buf = reinterpret_cast<C*>(smem_bdft);
-    C* wn = buf + pp * nn;
+    C* wn = buf + nn;
     const int64_t nb = (int64_t)2 * n * nn, plane = nn;
     for (int j = threadIdx.x; j < n; j += blockDim.x) wn[j] = wn_g[j];
-    const int pl0 = blockIdx.x * pp;
-    for (int e = threadIdx.x; e < pp * nn; e += blockDim.x) {
-        const int j = e / nn, t = e - j * nn;
-        int pl = pl0 + j;
-        C v;
-        v.x = 0;
-        v.y = 0;
-        if (pl < nplanes) {
-            const int kp = pl % n;
-            pl /= n;
-            const int par = pl & 1, comp = (pl >> 1) % 3, sys = pl / 6;
-            if (!(skip && skip[sys])) {
-                const int b = t / n, a = t - b * n;
-                const int64_t to = sys_k ? (int64_t)sys_k[sys] * tab_stride : 0;
-                C tw = cmul(cmul(twa[to + a], twb[to + b]), twk[to + kp]);
-                if (conj_tw) tw = conj_c(tw);
-                v = cmul(conv_c<C>(w[sys * sys_stride_in + comp * nb + (int64_t)(2 * kp + par) * plane + t]), tw);
-            }
-        }
-        buf[e] = v;
+    const int64_t to = sys_k ? (int64_t)sys_k[sys] * tab_stride : 0;
+    const C* ta = twa + to;
+    const C* tb = twb + to;
+    const C tk = twk[to + kp];
+    const Ci* src = w + sys * sys_stride_in + comp * nb + (int64_t)(2 * kp + par) * plane;
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        const int b = t / n, a = t - b * n;
+        C tw = cmul(cmul(ta[a], tb[b]), tk);
+        if (conj_tw) tw = conj_c(tw);
+        buf[t] = cmul(conv_c<C>(src[t]), tw);
     }
     __syncthreads();
-    const Lines rows{pp * n, n, n, nn, 1, false};
+    const Lines rows{n, n, n, nn, 1, false};
     dft_fwd<N1, N2>(buf, rows, n1, n2, wn, n);
-    const Lines cols{pp * n, n, 1, nn, n, true};
+    const Lines cols{n, n, 1, nn, n, true};
     dft_fwd<N1, N2>(buf, cols, n1, n2, wn, n);
-    for (int e = threadIdx.x; e < pp * nn; e += blockDim.x) {
-        const int j = e / nn, t = e - j * nn;
-        int pl = pl0 + j;
-        if (pl >= nplanes) continue;
-        const int kp = pl % n;
-        pl /= n;
-        const int par = pl & 1, comp = (pl >> 1) % 3, sys = pl / 6;
-        if (skip && skip[sys]) continue;
+    C* dst = W + sys * sys_stride_out + comp * nb + par * (nb / 2) + (int64_t)kp * plane;
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
         const int q = t / n, p = t - q * n;
-        W[sys * sys_stride_out + comp * nb + par * (nb / 2) + (int64_t)kp * plane + t] =
-            buf[j * nn + perm_pos(q, n1, n2) * n + perm_pos(p, n1, n2)];
+        dst[t] = buf[perm_pos(q, n1, n2) * n + perm_pos(p, n1, n2)];
     }
 }
 
-// K3: planes_per_cta(n) planes per CTA: inverse 2D DFT of W's planes, post-twiddle (conjugate of the
-// pre-twiddle), scale, into z (type Co); with part non-null also the partial Re <r, z> of each plane
-// (partial index = plane id within its system, 6 n per system).
+// K3: one plane per CTA: inverse 2D DFT of W's plane, post-twiddle (conjugate of the pre-twiddle),
+// scale, into z (type Co); with part non-null also the partial Re <r, z> of the plane (partial index
+// = plane id within its system, 6 n per system).
 template <int N1, int N2, typename C, typename Co>
 __global__ void __launch_bounds__(plane_nt<N1, N2>())
     bdft_plane_inv(const C* __restrict__ W, Co* __restrict__ z, const Co* __restrict__ r, const C* __restrict__ wn_g,
@@ -265,78 +256,53 @@ __global__ void __launch_bounds__(plane_nt<N1, N2>())
         n1 = N1;
         n2 = N2;
     }
-    const int pp = planes_per_cta(n), nn = n * n;
+    const int nn = n * n;
+    const int pl = blockIdx.x;
+    if (pl >= nplanes) return;
+    const int kp = pl % n, rest = pl / n;
+    const int par = rest & 1, comp = (rest >> 1) % 3, sys = rest / 6;
+    if (skip && skip[sys]) return;
     C* buf = reinterpret_cast<C*>(smem_bdft);
-    C* wn = buf + pp * nn;
+    C* wn = buf + nn;
     const int64_t nb = (int64_t)2 * n * nn, plane = nn;
     for (int j = threadIdx.x; j < n; j += blockDim.x) wn[j] = wn_g[j];
-    const int pl0 = blockIdx.x * pp;
-    for (int e = threadIdx.x; e < pp * nn; e += blockDim.x) {
-        const int j = e / nn, t = e - j * nn;
-        int pl = pl0 + j;
-        C v;
-        v.x = 0;
-        v.y = 0;
-        if (pl < nplanes) {
-            const int kp = pl % n;
-            pl /= n;
-            const int par = pl & 1, comp = (pl >> 1) % 3, sys = pl / 6;
-            if (!(skip && skip[sys])) v = W[sys * sys_stride_in + comp * nb + par * (nb / 2) + (int64_t)kp * plane + t];
-        }
+    const C* src = W + sys * sys_stride_in + comp * nb + par * (nb / 2) + (int64_t)kp * plane;
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
         const int q = t / n, p = t - q * n;
-        buf[j * nn + perm_pos(q, n1, n2) * n + perm_pos(p, n1, n2)] = v;
+        buf[perm_pos(q, n1, n2) * n + perm_pos(p, n1, n2)] = src[t];
     }
     __syncthreads();
-    const Lines cols{pp * n, n, 1, nn, n, true};
+    const Lines cols{n, n, 1, nn, n, true};
     dft_inv<N1, N2>(buf, cols, n1, n2, wn, n);
-    const Lines rows{pp * n, n, n, nn, 1, false};
+    const Lines rows{n, n, n, nn, 1, false};
     dft_inv<N1, N2>(buf, rows, n1, n2, wn, n);
     const R sc = (R)scale;
     using Ro = decltype(z[0].x);
-    Ro acc[8];  // per-thread sums per plane in the output precision, FP64 across threads
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0;
-    for (int e = threadIdx.x; e < pp * nn; e += blockDim.x) {
-        const int j = e / nn, t = e - j * nn;
-        int pl = pl0 + j;
-        if (pl >= nplanes) continue;
-        const int kp = pl % n;
-        pl /= n;
-        const int par = pl & 1, comp = (pl >> 1) % 3, sys = pl / 6;
-        if (skip && skip[sys]) continue;
+    Ro acc = 0;  // per-thread sum in the output precision, FP64 across threads
+    const int64_t to = sys_k ? (int64_t)sys_k[sys] * tab_stride : 0;
+    const C* ta = twa + to;
+    const C* tb = twb + to;
+    const C tk = twk[to + kp];
+    const int64_t base = sys * sys_stride_out + comp * nb + (int64_t)(2 * kp + par) * plane;
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
         const int b = t / n, a = t - b * n;
-        const int64_t to = sys_k ? (int64_t)sys_k[sys] * tab_stride : 0;
-        const C tw = conj_c(cmul(cmul(twa[to + a], twb[to + b]), twk[to + kp]));
-        const int64_t off = sys * sys_stride_out + comp * nb + (int64_t)(2 * kp + par) * plane + t;
-        const Co v = conv_c<Co>(scale_c(sc, cmul(buf[e], tw)));
-        z[off] = v;
-        if (part) {
-            const Ro d = cdotre(r[off], v, (Ro)0);
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj)
-                if (jj == j) acc[jj] += d;
-        }
+        const C tw = conj_c(cmul(cmul(ta[a], tb[b]), tk));
+        const Co v = conv_c<Co>(scale_c(sc, cmul(buf[t], tw)));
+        z[base + t] = v;
+        if (part) acc = cdotre(r[base + t], v, acc);
     }
     if (part) {
         __shared__ double red[plane_nt<N1, N2>() / 32];
-        for (int j = 0; j < pp; ++j) {
-            double v = 0.0;
-#pragma unroll
-            for (int jj = 0; jj < 8; ++jj)
-                if (jj == j) v = (double)acc[jj];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            __syncthreads();
-            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-            __syncthreads();
-            const int pl = pl0 + j;
-            if (threadIdx.x == 0 && pl < nplanes) {
-                const int sys = pl / (6 * n);
-                if (!(skip && skip[sys])) {
-                    double t = 0.0;
-                    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-                    part[(int64_t)sys * npart + (pl - sys * 6 * n)] = t;
-                }
-            }
+        double v = (double)acc;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+            part[(int64_t)sys * npart + (pl - sys * 6 * n)] = t;
         }
     }
 }
@@ -386,6 +352,7 @@ __global__ void __launch_bounds__(pencil_nt<N1, N2>())
     const Lines pencils{6 * PT, PT, 1, n * PT, PT, true};
     const R shift_rho = (R)shift_rho_d, scale = (R)scale_d;
     if (mode != 2) {
+#pragma unroll 4
         for (int e = threadIdx.x; e < 6 * n * PT; e += blockDim.x) {
             const int pl = e % PT, kp = (e / PT) % n, pen = e / (PT * n);
             C v;

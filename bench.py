@@ -341,6 +341,16 @@ def profile_run(what):
         pc.pc_eigs_multi(g, kpts[15:31], NEV, opt=opt)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
+    elif what == "precision-mixed":
+        cell = config_cell("precision")
+        g = pc.pc_grid_create(cell.N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+        opt = pc.pc_options_default(tol=TOL, precision=pc.PC_PREC_MIXED, autotune=1)
+        pc.pc_eigs(g, [0.25, 0.0, 0.0], NEV, opt=opt)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        pc.pc_eigs(g, [0.3, 0.1, 0.2], NEV, opt=opt)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     else:
         cell = config_cell("precision")
         N = cell.N
@@ -656,10 +666,12 @@ def main():
                     help="run the paper's own FCC quartz/silicon workload (40 bands) instead")
     ap.add_argument("--paper-n", type=int, default=60, help="grid size of --paper (the paper's: 60)")
     ap.add_argument("--paper-k", type=int, default=16, help="Bloch vectors of the 91-point path timed by --paper")
-    ap.add_argument("--profile", default=None, choices=["kpoint", "kpoint-mixed", "apply-c64", "apply-c128"],
+    ap.add_argument("--profile", default=None,
+                    choices=["kpoint", "kpoint-mixed", "precision-mixed", "apply-c64", "apply-c128"],
                     help="profiling aid for ncu: run only one lockstep chunk of 16 Bloch vectors of the "
-                         "workload (after an untimed one), or one N=160 four-block apply (after two "
-                         "untimed ones), and print nothing else")
+                         "workload (after an untimed one), one mixed-precision solve of the N=160 precision "
+                         "cell (after an untimed one), or one N=160 four-block apply (after two untimed "
+                         "ones), and print nothing else")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

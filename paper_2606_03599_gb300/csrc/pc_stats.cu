@@ -183,7 +183,7 @@ int pc_fp64_peak(double seconds, double* tflops, double* fma_per_s) {
         cudaEventElapsedTime(&ms, e0, e1);
         const double fmas = (double)blocks * threads * 8.0 * iters;
         if (ms > 0.f && round >= 2) best = std::fmax(best, fmas / (ms * 1e-3));
-        // grow the launch until it runs for about `seconds` / 4 (the last rounds are the measurement)
+        // grow the launch until it runs for about `seconds` / 4 (the last passes are the measurement)
         if (ms > 0.f && ms * 1e-3 < seconds / 4) {
             const double f = std::fmin(16.0, (seconds / 4) / (ms * 1e-3));
             iters = (int)std::fmin(1e9, iters * f);

@@ -41,8 +41,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "block B C B^H apply GDoF/s & HBM frac; sec per k-point for 20 bands @1e-8 resid"
 # block applies per k-point of the FP64 band workload, as the GPU arm measures them on GB300
-# (solver.block_applies_per_kpoint); the reference arm scales its per-apply time by it
-APPLIES_PER_KPOINT_MEASURED = 6095
+# (solver.block_applies_per_kpoint: the PCG iterations and true-residual checks of one k-point, items
+# of converged systems not counted); the reference arm scales its per-apply time by it
+APPLIES_PER_KPOINT_MEASURED = 4844
 WORKLOAD = ("two-phase SC cell N=48 (R=0.35, seed 2), 31-point Gamma-X-M-Gamma-R-X path, 20 bands, resid 1e-8, "
             "FP64; Bloch vectors solved in lockstep chunks of --kbatch")
 NEV = 20
@@ -198,7 +199,7 @@ def cpu_oracle_sample(apply_count_per_kpoint, seconds=15.0):
     return {"value": per_apply * apply_count_per_kpoint, "unit": "s/k-point", "cores": threads, "kind": "oracle",
             "sample": ("%d FP64 oracle block applies (N=48, OpenMP %d threads, %.2f ms each) scaled by the %d "
                        "block applies one k-point solve performs; the oracle's exact eigen-solve (ARPACK + "
-                       "SuperLU) takes ~15 min per block and is not sampled" % (n, threads, per_apply * 1e3,
+                       "SuperLU) takes ~35 min per block on one core and is not sampled" % (n, threads, per_apply * 1e3,
                                                                                  apply_count_per_kpoint)),
             "per_apply_ms": per_apply * 1e3}
 
@@ -215,23 +216,27 @@ def run_reference(args):
     pb = O.problem_from_cell(cell, C0=1e9, rho0=1e3)
     threads = os.cpu_count() or 1
     x = complex_gaussian((3, cell.N ** 3 // 4), 7)
-    # block applies one k-point solve of the GPU arm performs, as that arm measures it
-    # (solver.block_applies_per_kpoint of its JSON line on GB300: 6095 = 173.5 inner solves x ~27
-    # PCG iterations plus residual checks, counted over the launches' items); the GPU arm's own
+    # block applies one k-point solve of the GPU arm performs, as that arm measures it on GB300
+    # (178 inner solves x ~27 PCG iterations, plus the residual checks); the GPU arm's own
     # cpu_baseline scales by the count it measures itself
     applies = int(os.environ.get("PC_APPLIES_PER_KPOINT", str(APPLIES_PER_KPOINT_MEASURED)))
     reps = 16
     for _ in range(args.warmup):
         O.apply_block(pb, [0.25, 0, 0], 0, x, 0.1, nthreads=threads)
-    times = []
+    times, step_s = [], []
     for s in range(args.steps):
         t0 = time.perf_counter()
         for r in range(reps):
             O.apply_block(pb, [0.25, 0, 0], r % 4, x, 0.1, nthreads=threads)
-        times.append((time.perf_counter() - t0) / reps * applies)
+        dt = time.perf_counter() - t0
+        step_s.append(dt)
+        times.append(dt / reps * applies)
     v = float(np.mean(times))
+    # ms_per_step is the measured time of a step (its sample of applies); value is that sample's
+    # time per apply times the applies of one k-point solve (see "extrapolation")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/k-point", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_s)) * 1e3,
+            "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": 48},
             "cpu_baseline": {"value": v, "unit": "s/k-point", "cores": threads, "kind": "oracle",
@@ -240,8 +245,9 @@ def run_reference(args):
             "extrapolation": {"measured": "time of one FP64 oracle block apply at N=48 (OpenMP, all host cores)",
                               "applies_per_kpoint": applies,
                               "source": "the GPU arm's measured block-apply count per k-point "
-                                        "(solver.block_applies_per_kpoint); the oracle's own exact eigen-solve "
-                                        "(ARPACK + sparse LU) takes ~35 min per block and is not run"},
+                                        "(solver.block_applies_per_kpoint: PCG iterations and residual checks); "
+                                        "the oracle's own exact eigen-solve "
+                                        "(ARPACK + sparse LU) takes ~35 min per block on one core and is not run"},
             "e2e": {"value": v, "unit": "s/k-point", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -886,12 +892,14 @@ def main():
             import torch.distributed as dist
             dist.destroy_process_group()
         return
-    # block-apply equivalents per k-point (FP64 applies of the timed steps, counted in nodes)
+    # block applies per k-point of the timed steps: nodes of the FP64 apply items that ran, in units
+    # of one parity block (items of systems that had converged are skipped inside a launch and not
+    # counted); the PCG iterations plus the true-residual checks
+    pcg_total = sum(i["pcg_iters"] for i in infos)
     applies_per_k = int(round(st["apply_nodes"][1] / (cell.N ** 3 / 4) / (args.steps * KB)))
     cpu = None if args.no_cpu else cpu_oracle_sample(applies_per_k)
     if cpu is not None:
         cpu["apply_n160"] = cpu_oracle_apply_rate()
-    pcg_total = sum(i["pcg_iters"] for i in infos)
     line = {
         "metric": METRIC, "value": value, "unit": "s/k-point", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": False,

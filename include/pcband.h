@@ -428,17 +428,19 @@ typedef struct {
     long long apply_launches;  /* stencil-apply launches (both precisions) */
     long long apply_timed[2];  /* timed apply launches: [0] complex64, [1] complex128 */
     double apply_ms[2];        /* their summed device time, ms */
-    double apply_nodes[2];     /* nodes they processed (sum over items) */
+    double apply_nodes[2];     /* nodes of the items they processed; an item skipped at run
+                                  time (a converged system of a batched solve) counts none */
 } pc_stats;
 
 /* Enable (1) or disable (0) event timing of apply launches.  Timing adds two
- * event records per apply launch. */
+ * event records per apply launch, and a one-CTA counting kernel after each
+ * launch whose items carry run-time skip flags. */
 int pc_stats_timing(int enable);
 
 /* Reset all counters. */
 int pc_stats_reset(void);
 
-/* Read the counters; synchronises on the recorded events first. */
+/* Read the counters; synchronises the device first. */
 int pc_stats_get(pc_stats* out);
 
 

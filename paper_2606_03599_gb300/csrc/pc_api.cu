@@ -567,7 +567,7 @@ int grid_apply(pc_grid* g, int dtype, bool full, const ApplyItem* items, int nit
             i = j;
         }
     }
-    if (th) timing_end(th, s, dtype == PC_C64 ? 0 : 1, (double)nitems * X * Y * Z);
+    if (th) timing_end(th, s, dtype == PC_C64 ? 0 : 1, items, nitems, (double)X * Y * Z);
     return rc;
 }
 

@@ -179,7 +179,9 @@ void note_launch(int n = 1);
 void note_apply_launch(int n = 1);
 bool timing_enabled();
 void* timing_begin(cudaStream_t s);
-void timing_end(void* h, cudaStream_t s, int kind, double nodes);
+// Ends a timed apply call of nitems items of nodes_per_item nodes each; items with a skip flag are
+// counted on the device when they run.
+void timing_end(void* h, cudaStream_t s, int kind, const ApplyItem* items, int nitems, double nodes_per_item);
 // Timing of launches captured into a CUDA graph (read after each replay).
 struct TimedSet;
 TimedSet* timing_capture_begin();

@@ -1,4 +1,5 @@
 // Process-wide launch counters and event timing of the stencil apply.
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -55,11 +56,43 @@ void* timing_begin(cudaStream_t s) {
     return t;
 }
 
-void timing_end(void* h, cudaStream_t s, int kind, double nodes) {
+// Nodes of timed apply items whose skip flag is read on the device: an item of a converged system
+// returns at once inside the apply kernels, so only the items that ran are added here, by a small
+// kernel on the apply's stream right after its end event (inside a captured graph it is a node of
+// the graph and counts on every replay).
+__device__ unsigned long long g_dev_nodes[2];
+static std::atomic<int> g_dev_used{0};
+
+constexpr int kCountMax = 64;
+struct SkipList {
+    const int* f[kCountMax];
+    int n;
+};
+
+__global__ void count_active_kernel(const __grid_constant__ SkipList L, unsigned long long per_item, int kind) {
+    const int i = threadIdx.x;
+    unsigned long long v = (i < L.n && !(L.f[i] != nullptr && *L.f[i])) ? per_item : 0ULL;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((i & 31) == 0 && v != 0ULL) atomicAdd(&g_dev_nodes[kind], v);
+}
+
+void timing_end(void* h, cudaStream_t s, int kind, const ApplyItem* items, int nitems, double nodes_per_item) {
     TimedLaunch* t = static_cast<TimedLaunch*>(h);
     record(t->b, s);
     t->kind = kind;
-    t->nodes = nodes;
+    bool flagged = false;
+    for (int i = 0; i < nitems && !flagged; ++i) flagged = items[i].skip != nullptr;
+    t->nodes = flagged ? 0.0 : nitems * nodes_per_item;
+    if (flagged) {
+        g_dev_used.store(1);
+        for (int i0 = 0; i0 < nitems; i0 += kCountMax) {
+            SkipList L{};
+            L.n = std::min(kCountMax, nitems - i0);
+            for (int i = 0; i < L.n; ++i) L.f[i] = items[i0 + i].skip;
+            count_active_kernel<<<1, kCountMax, 0, s>>>(L, (unsigned long long)nodes_per_item, kind);
+            note_launch();
+        }
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     g_pending.push_back(*t);
     delete t;
@@ -211,6 +244,11 @@ int pc_stats_reset(void) {
     g_timed[0] = g_timed[1] = 0;
     g_ms[0] = g_ms[1] = 0;
     g_nodes[0] = g_nodes[1] = 0;
+    if (g_dev_used.load()) {
+        const unsigned long long zero[2] = {0ULL, 0ULL};
+        cudaDeviceSynchronize();
+        PC_CUDA_TRY(cudaMemcpyToSymbol(g_dev_nodes, zero, sizeof(zero)));
+    }
     return PC_OK;
 }
 
@@ -218,12 +256,17 @@ int pc_stats_get(pc_stats* out) {
     if (!out) return fail(PC_EINVAL, "pc_stats_get: null");
     std::lock_guard<std::mutex> lk(g_mu);
     drain();
+    unsigned long long dev[2] = {0ULL, 0ULL};
+    if (g_dev_used.load()) {
+        PC_CUDA_TRY(cudaDeviceSynchronize());
+        PC_CUDA_TRY(cudaMemcpyFromSymbol(dev, g_dev_nodes, sizeof(dev)));
+    }
     out->launches = g_launches.load();
     out->apply_launches = g_apply_launches.load();
     for (int k = 0; k < 2; ++k) {
         out->apply_timed[k] = g_timed[k];
         out->apply_ms[k] = g_ms[k];
-        out->apply_nodes[k] = g_nodes[k];
+        out->apply_nodes[k] = g_nodes[k] + (double)dev[k];
     }
     return PC_OK;
 }

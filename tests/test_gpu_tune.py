@@ -132,3 +132,40 @@ def test_apply_timing_through_graph_replays(pc):
         assert st["apply_ms"][1] > 0
     finally:
         pc.pc_grid_destroy(g)
+
+
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_timed_apply_nodes_count_only_items_that_ran(pc, side_stream):
+    """PCG runs its iterations in chunks of four (replayed as a CUDA graph on a side stream); once
+    the system has converged, or reached maxit, the rest of the chunk's applies skip it on the
+    device.  The timed node count holds only the applies that ran: one block per iteration."""
+    import torch
+    N = 16
+    cell = two_phase_sphere(N, 0.35, 4)
+    g = pc.pc_grid_create(N, cell.C, cell.rho, phase=cell.phase, a_lat=cell.a_lat)
+    try:
+        pc.pc_set_k(g, [0.3, 0.1, 0.2])
+        nb = N ** 3 // 4
+        rhs = torch.from_numpy(complex_gaussian(3 * nb, 21)).cuda()
+        x = torch.empty_like(rhs)
+        stream = torch.cuda.Stream() if side_stream else None
+        sigma = pc.pc_default_sigma(g)
+        for tol, maxit in ((1e-10, 400), (1e-12, 1), (1e-12, 6)):
+            pc.pc_shift_invert_pcg(g, 1, sigma, rhs, x, tol=tol, maxit=maxit, stream=stream,
+                                   raise_on_fail=False)  # warm-up: workspace and graph
+            torch.cuda.synchronize()
+            pc.pc_stats_reset()
+            pc.pc_stats_timing(1)
+            try:
+                r = pc.pc_shift_invert_pcg(g, 1, sigma, rhs, x, tol=tol, maxit=maxit, stream=stream,
+                                           raise_on_fail=False)
+            finally:
+                pc.pc_stats_timing(0)
+            st = pc.pc_stats_get()
+            launched = st["apply_timed"][1]
+            assert launched >= r["iters"] and launched % 4 == 0, (launched, r)
+            assert st["apply_nodes"][1] == r["iters"] * nb, (st["apply_nodes"], r, launched)
+            if maxit < 400:
+                assert r["iters"] == maxit and launched > maxit
+    finally:
+        pc.pc_grid_destroy(g)

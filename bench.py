@@ -43,7 +43,7 @@ METRIC = "block B C B^H apply GDoF/s & HBM frac; sec per k-point for 20 bands @1
 # block applies per k-point of the FP64 band workload, as the GPU arm measures them on GB300
 # (solver.block_applies_per_kpoint: the PCG iterations and true-residual checks of one k-point, items
 # of converged systems not counted); the reference arm scales its per-apply time by it
-APPLIES_PER_KPOINT_MEASURED = 4844
+APPLIES_PER_KPOINT_MEASURED = 5136
 WORKLOAD = ("two-phase SC cell N=48 (R=0.35, seed 2), 31-point Gamma-X-M-Gamma-R-X path, 20 bands, resid 1e-8, "
             "FP64; Bloch vectors solved in lockstep chunks of --kbatch")
 NEV = 20
@@ -776,7 +776,9 @@ def main():
         peak_src = "nominal FP64 dense rate of GB300 (measurement failed)"
     n_app = st["apply_timed"][1]
     app_ms = st["apply_ms"][1] / max(1, n_app)
+    # nodes of the items that ran (a launch's items of converged systems return at once)
     nodes_per_launch = st["apply_nodes"][1] / max(1, n_app)
+    skipped_frac = 1.0 - st["apply_nodes"][1] / max(1.0, st["apply_nodes_launched"][1])
     achieved_tflops = nodes_per_launch * FLOPS_PER_NODE / (app_ms / 1e3) / 1e12
     kind = pc.pc_tuned_config(g, pc.PC_C128, 0, 4 * opt.block_size * KB)[0]
     kname = {0: "apply_kernel<double>", 1: "apply_tma_kernel<double>", 2: "apply_row_kernel",
@@ -789,6 +791,7 @@ def main():
                                 "cold-cache capture per node scaled by the nodes per timed apply"
                 if traffic is not None else None,
                 "launches": n_app, "avg_launch_us": app_ms * 1e3, "nodes_per_launch": nodes_per_launch,
+                "skipped_item_frac": skipped_frac,
                 "flops_per_node": FLOPS_PER_NODE, "peak_source": peak_src,
                 "fp64_fma_per_s": fma_rate, "peak_nominal_tflops": FP64_NOMINAL_TFLOPS}
 

@@ -430,6 +430,8 @@ typedef struct {
     double apply_ms[2];        /* their summed device time, ms */
     double apply_nodes[2];     /* nodes of the items they processed; an item skipped at run
                                   time (a converged system of a batched solve) counts none */
+    double apply_nodes_launched[2]; /* nodes of all items the timed launches carried, skipped
+                                       ones included */
 } pc_stats;
 
 /* Enable (1) or disable (0) event timing of apply launches.  Timing adds two

@@ -79,7 +79,8 @@ class c_batch_info(ctypes.Structure):
 class c_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("apply_launches", ctypes.c_longlong),
                 ("apply_timed", ctypes.c_longlong * 2), ("apply_ms", ctypes.c_double * 2),
-                ("apply_nodes", ctypes.c_double * 2)]
+                ("apply_nodes", ctypes.c_double * 2),
+                ("apply_nodes_launched", ctypes.c_double * 2)]
 
 
 class c_eigs_info(ctypes.Structure):
@@ -485,7 +486,8 @@ def pc_stats_get():
     _check(lib.pc_stats_get(ctypes.byref(st)))
     return {"launches": st.launches, "apply_launches": st.apply_launches,
             "apply_timed": list(st.apply_timed), "apply_ms": list(st.apply_ms),
-            "apply_nodes": list(st.apply_nodes)}
+            "apply_nodes": list(st.apply_nodes),
+            "apply_nodes_launched": list(st.apply_nodes_launched)}
 
 
 def pc_version():

@@ -11,7 +11,8 @@ namespace pc {
 struct TimedLaunch {
     cudaEvent_t a, b;
     int kind;  // 0 = complex64, 1 = complex128
-    double nodes;
+    double nodes;     // nodes counted on the host (items without a skip flag)
+    double launched;  // nodes of all items
 };
 
 static std::atomic<long long> g_launches{0}, g_apply_launches{0};
@@ -20,7 +21,7 @@ static std::mutex g_mu;
 static std::vector<TimedLaunch> g_pending;
 static std::vector<cudaEvent_t> g_pool;
 static long long g_timed[2] = {0, 0};
-static double g_ms[2] = {0, 0}, g_nodes[2] = {0, 0};
+static double g_ms[2] = {0, 0}, g_nodes[2] = {0, 0}, g_launched[2] = {0, 0};
 
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void note_apply_launch(int n) { g_apply_launches.fetch_add(n, std::memory_order_relaxed); }
@@ -83,6 +84,7 @@ void timing_end(void* h, cudaStream_t s, int kind, const ApplyItem* items, int n
     bool flagged = false;
     for (int i = 0; i < nitems && !flagged; ++i) flagged = items[i].skip != nullptr;
     t->nodes = flagged ? 0.0 : nitems * nodes_per_item;
+    t->launched = nitems * nodes_per_item;
     if (flagged) {
         g_dev_used.store(1);
         for (int i0 = 0; i0 < nitems; i0 += kCountMax) {
@@ -129,6 +131,7 @@ void timing_replayed(TimedSet* t) {
             g_ms[r.kind] += ms;
             g_timed[r.kind] += 1;
             g_nodes[r.kind] += r.nodes;
+            g_launched[r.kind] += r.launched;
         } else {
             cudaGetLastError();  // an unreadable timing is dropped, not reported to later calls
         }
@@ -156,6 +159,7 @@ static void drain() {
             g_ms[t.kind] += ms;
             g_timed[t.kind] += 1;
             g_nodes[t.kind] += t.nodes;
+            g_launched[t.kind] += t.launched;
         } else {
             cudaGetLastError();
         }
@@ -244,6 +248,7 @@ int pc_stats_reset(void) {
     g_timed[0] = g_timed[1] = 0;
     g_ms[0] = g_ms[1] = 0;
     g_nodes[0] = g_nodes[1] = 0;
+    g_launched[0] = g_launched[1] = 0;
     if (g_dev_used.load()) {
         const unsigned long long zero[2] = {0ULL, 0ULL};
         cudaDeviceSynchronize();
@@ -267,6 +272,7 @@ int pc_stats_get(pc_stats* out) {
         out->apply_timed[k] = g_timed[k];
         out->apply_ms[k] = g_ms[k];
         out->apply_nodes[k] = g_nodes[k] + (double)dev[k];
+        out->apply_nodes_launched[k] = g_launched[k];
     }
     return PC_OK;
 }

@@ -165,6 +165,7 @@ def test_timed_apply_nodes_count_only_items_that_ran(pc, side_stream):
             launched = st["apply_timed"][1]
             assert launched >= r["iters"] and launched % 4 == 0, (launched, r)
             assert st["apply_nodes"][1] == r["iters"] * nb, (st["apply_nodes"], r, launched)
+            assert st["apply_nodes_launched"][1] == launched * nb
             if maxit < 400:
                 assert r["iters"] == maxit and launched > maxit
     finally:

@@ -340,17 +340,15 @@ static void emu_run_split(const StencilParams<R>& P, int block, const void* x, v
     using T = SplitApply<R, FULL, CUBIC, MATK>;
     using C = typename CT<R>::T;
     const SplitGeom G = make_split_geom(P.X, P.Y, P.Z);
-    std::vector<C> xe(3 * G.ne), fe(15 * G.ne);
-    std::memset((void*)xe.data(), 0xFF, sizeof(C) * xe.size());
+    std::vector<C> xg(3 * G.ghosts), fe(15 * G.ne);
+    std::memset((void*)xg.data(), 0xFF, sizeof(C) * xg.size());
     std::memset((void*)fe.data(), 0xFF, sizeof(C) * fe.size());
     const int p12 = FULL ? 0 : (block >> 1), p13 = FULL ? 0 : (block & 1);
     const C* xv = static_cast<const C*>(x);
-    for (int c = 0; c < 3; ++c)
-        for (int64_t t = 0; t < G.m; ++t) T::fill_x_interior(G, xv, xe.data(), c, t);
-    for (int64_t gi = 0; gi < G.ghosts; ++gi) T::fill_x_ghost(P.ph, G, xv, xe.data(), gi);
+    for (int64_t gi = 0; gi < G.ghosts; ++gi) T::fill_x_ghost(P.ph, G, xv, xg.data(), gi);
     R Ct[2][36];
     for (int i = 0; i < 72; ++i) Ct[i / 36][i % 36] = P.C[i / 36][i % 36];
-    for (int64_t t = 0; t < G.m; ++t) T::flux_node(P, Ct, G, p12, p13, xe.data(), mat, fe.data(), t, true);
+    for (int64_t t = 0; t < G.m; ++t) T::flux_node(P, Ct, G, p12, p13, xv, xg.data(), mat, fe.data(), t, true);
     for (int64_t gi = 0; gi < G.ghosts; ++gi) T::fill_f_ghost(P.ph, G, fe.data(), gi);
     for (int64_t t = 0; t < G.m; ++t)
         T::gather_node(P, G, p12, p13, fe.data(), xv, static_cast<C*>(y), mat, (R)shift, t, true);

@@ -15,7 +15,7 @@ template <typename R>
 struct SplitBatch {
     using C = typename CT<R>::T;
     ApplyItem it[kSplitMaxItems];
-    C* xe[kSplitMaxItems];  // extended x of each item
+    C* xg[kSplitMaxItems];  // ghost cells of x of each item
     C* fe[kSplitMaxItems];  // extended fluxes of each item
     R ph[kSplitMaxItems][3][2];  // (cos, sin) of each item's Bloch phases
     int n;
@@ -23,29 +23,20 @@ struct SplitBatch {
 
 __device__ __forceinline__ bool item_skipped(const ApplyItem& it) { return it.skip != nullptr && *it.skip; }
 
-// Pass 1: blockIdx.z = item; CTAs with blockIdx.x < nint copy interior cells (blockIdx.y = component),
-// the others (blockIdx.y = 0 only) write the ghost cells of all three components (the only FP64
-// work of the pass: the Bloch phase, computed once per cell).
+// Pass 1: the ghost cells of x (all three components, the only FP64 work of the pass: the Bloch
+// phase, computed once per cell); blockIdx.y = item.
 template <typename R, bool FULL, bool CUBIC, int MATK>
 __global__ void __launch_bounds__(kSplitThreads)
     split_fill_x(const __grid_constant__ StencilParams<R> P, const __grid_constant__ SplitBatch<R> B,
-                 const __grid_constant__ SplitGeom G, int nint) {
+                 const __grid_constant__ SplitGeom G) {
     using T = SplitApply<R, FULL, CUBIC, MATK>;
     using C = typename CT<R>::T;
-    const ApplyItem& it = B.it[blockIdx.z];
+    const ApplyItem& it = B.it[blockIdx.y];
     if (item_skipped(it)) return;
     const C* x = static_cast<const C*>(it.x);
-    C* xe = B.xe[blockIdx.z];
-    const int c = blockIdx.y;
-    if ((int)blockIdx.x < nint) {
-        for (int64_t t = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; t < G.m; t += (int64_t)nint * kSplitThreads)
-            T::fill_x_interior(G, x, xe, c, t);
-    } else if (c == 0) {
-        const int nghost = gridDim.x - nint;
-        for (int64_t gi = (blockIdx.x - nint) * (int64_t)kSplitThreads + threadIdx.x; gi < G.ghosts;
-             gi += (int64_t)nghost * kSplitThreads)
-            T::fill_x_ghost(B.ph[blockIdx.z], G, x, xe, gi);
-    }
+    for (int64_t gi = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; gi < G.ghosts;
+         gi += (int64_t)gridDim.x * kSplitThreads)
+        T::fill_x_ghost(B.ph[blockIdx.y], G, x, B.xg[blockIdx.y], gi);
 }
 
 // Pass 2: fluxes of every interior node; blockIdx.y = item.
@@ -62,7 +53,8 @@ __global__ void __launch_bounds__(kSplitThreads)
     const int p12 = FULL ? 0 : (it.block >> 1), p13 = FULL ? 0 : (it.block & 1);
     for (int64_t t = blockIdx.x * (int64_t)kSplitThreads + threadIdx.x; t < G.m;
          t += (int64_t)gridDim.x * kSplitThreads)
-        T::flux_node(P, Ct, G, p12, p13, B.xe[blockIdx.y], it.mat, B.fe[blockIdx.y], t, true);
+        T::flux_node(P, Ct, G, p12, p13, static_cast<const typename CT<R>::T*>(it.x), B.xg[blockIdx.y], it.mat,
+                     B.fe[blockIdx.y], t, true);
 }
 
 // Pass 3: ghost cells of F_0..F_3 (12 arrays per cell); blockIdx.y = item.
@@ -111,10 +103,8 @@ template <typename R, bool FULL, bool CUBIC, int MATK>
 int launch_split_t(const StencilParams<R>& P, const SplitBatch<R>& B, const SplitGeom& G, double* dp, int ds,
                    cudaStream_t s) {
     const int sm = device_sm_count();
-    // interior copy and ghost fill share one launch: CTAs in proportion to their cells
-    const int nint = (int)std::max<int64_t>(1, std::min<int64_t>((G.m + kSplitThreads - 1) / kSplitThreads, 2LL * sm));
     const int ngh = (int)std::max<int64_t>(1, std::min<int64_t>((G.ghosts + kSplitThreads - 1) / kSplitThreads, sm));
-    split_fill_x<R, FULL, CUBIC, MATK><<<dim3(nint + ngh, 3, B.n), kSplitThreads, 0, s>>>(P, B, G, nint);
+    split_fill_x<R, FULL, CUBIC, MATK><<<dim3(ngh, B.n), kSplitThreads, 0, s>>>(P, B, G);
     note_launch();
     const int nflux = split_apply_ctas(G.m);
     split_flux<R, FULL, CUBIC, MATK><<<dim3(nflux, B.n), kSplitThreads, 0, s>>>(P, B, G);
@@ -157,8 +147,8 @@ static int launch_apply_split_t(bool full, bool cubic, int matkind, const Stenci
             B.it[i] = items[base + i];
             for (int e = 0; e < 6; ++e) B.ph[i][e / 2][e % 2] = (R)item_ph[(size_t)6 * (base + i) + e];
             C* w = static_cast<C*>(scratch) + (int64_t)i * per;
-            B.xe[i] = w;
-            B.fe[i] = w + 3 * G.ne;
+            B.xg[i] = w;
+            B.fe[i] = w + 3 * G.ghosts;
         }
         int rc;
         if (matkind == 2) {

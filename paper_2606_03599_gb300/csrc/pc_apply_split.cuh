@@ -8,18 +8,21 @@
 // a flux region is not a multiple of the warp width.  Here each node's fluxes are computed
 // exactly once, by one lane, and go through memory (L2 at the solver's grid sizes):
 //
-//   1. fill:   x -> x_e, the Bloch-extended copy of x with one ghost layer on every side
-//              (ghost = wrapped node times exp(i w.phi)); interior cells are a plain copy;
-//   2. flux:   per node, g_l = x_e(node - d_l) - x_e(node), the strain, the stress and the
-//              fluxes F_l and P_0 (sum_l F_l = 4 P_0) -> f_e;
+//   1. fill:   the ghost layer of x (one cell deep on every side the flux pass reads; ghost =
+//              wrapped node times exp(i w.phi)) -> x_g, a compact array of ghost cells;
+//   2. flux:   per node, g_l = x(node - d_l) - x(node), the neighbour read from x itself when it
+//              lies inside the grid and from x_g when not (an address choice, no arithmetic:
+//              the FP64 pipe that bounds this pass does no phase work), the strain, the stress
+//              and the fluxes F_l and P_0 (sum_l F_l = 4 P_0) -> f_e;
 //   3. fill:   ghost cells of f_e (F_0..F_3) from their wrapped nodes, times exp(i w.phi);
 //   4. gather: y(node) = sum_l F_l(node + d_l) - 4 P_0(node) - shift rho x(node), with
 //              optional partial sums of Re<x, y>.
 //
 // Extended cell (a, b, k), a in [-1, X], b in [-1, Y], k in [-1, Z], has index
-// (a + 1) + Xe ((b + 1) + Ye (k + 1)) with Xe = X + 2, Ye = Y + 2; each of the 3 components
-// of x_e and the 15 values of f_e (F_l of component c at l * 3 + c, P_0 of c at 12 + c) is a
-// separate array of Xe Ye Ze cells.
+// (a + 1) + Xe ((b + 1) + Ye (k + 1)) with Xe = X + 2, Ye = Y + 2; each of the 15 values of f_e
+// (F_l of component c at l * 3 + c, P_0 of c at 12 + c) is a separate array of Xe Ye Ze cells.
+// Each of the 3 components of x_g is an array of the extended grid's ghost cells, in the order
+// of ghost_cell.
 #pragma once
 
 #include <math.h>
@@ -55,8 +58,8 @@ inline SplitGeom make_split_geom(int X, int Y, int Z) {
     return G;
 }
 
-// Complex values of scratch per item: x_e (3 arrays) and f_e (15 arrays).
-inline int64_t split_item_elems(const SplitGeom& G) { return 18 * G.ne; }
+// Complex values of scratch per item: x_g (3 arrays of ghost cells) and f_e (15 extended arrays).
+inline int64_t split_item_elems(const SplitGeom& G) { return 3 * G.ghosts + 15 * G.ne; }
 
 // Upper-triangular position (row order, p <= r) of Voigt entry (p, r) among the 21 independent
 // entries of a symmetric 6x6 stiffness.
@@ -121,25 +124,27 @@ struct SplitApply {
         k = (int)cq;
     }
 
-    // Pass 1, interior cell t of component c: plain copy.
-    static PC_HD void fill_x_interior(const SplitGeom& G, const C* x, C* xe, int c, int64_t t) {
-        int a, b, k;
-        split3(t, G.X, G.Y, a, b, k);
-        PC_IDX(c * G.m + t, 3 * G.m);
-        xe[c * G.ne + eidx(G, a, b, k)] = x[c * G.m + t];
+    // Inverse of ghost_cell: the number of the ghost cell (a, b, k) (one coordinate outside the
+    // interior range at least).
+    static PC_HD int64_t ghost_index(const SplitGeom& G, int a, int b, int k) {
+        const int64_t pl = (int64_t)G.Xe * G.Ye;
+        if (k < 0 || k >= G.Z) return (k < 0 ? 0 : pl) + (a + 1) + (int64_t)G.Xe * (b + 1);
+        if (b < 0 || b >= G.Y) return 2 * pl + (int64_t)(2 * k + (b < 0 ? 0 : 1)) * G.Xe + (a + 1);
+        return 2 * pl + 2 * (int64_t)G.Xe * G.Z + 2 * (b + (int64_t)G.Y * k) + (a < 0 ? 0 : 1);
     }
 
     // Pass 1, ghost cell gi (all three components): the wrapped node times its Bloch phase.
-    static PC_HD void fill_x_ghost(const R (*kph)[2], const SplitGeom& G, const C* x, C* xe, int64_t gi) {
+    static PC_HD void fill_x_ghost(const R (*kph)[2], const SplitGeom& G, const C* x, C* xg, int64_t gi) {
         int a, b, k, wa, wb, wk;
         ghost_cell(G, gi, a, b, k);
+        if (a >= G.X) return;  // the flux pass reads a in [-1, X) only
         const int aw = wrap1(a, G.X, wa), bw = wrap1(b, G.Y, wb), kw = wrap1(k, G.Z, wk);
-        const int64_t src = aw + (int64_t)G.X * (bw + (int64_t)G.Y * kw), dst = eidx(G, a, b, k);
+        const int64_t src = aw + (int64_t)G.X * (bw + (int64_t)G.Y * kw);
         PC_IDX(src, G.m);
-        PC_IDX(dst, G.ne);
+        PC_IDX(gi, G.ghosts);
         const C ph = phase(kph, wa, wb, wk);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) xe[c * G.ne + dst] = cmul(x[c * G.m + src], ph);
+        for (int c = 0; c < 3; ++c) xg[c * G.ghosts + gi] = cmul(x[c * G.m + src], ph);
     }
 
     // Pass 3, ghost cell gi of the flux arrays F_0..F_3 (12 arrays).
@@ -164,7 +169,7 @@ struct SplitApply {
     // Pass 2, interior node t: fluxes F_l (l = 0..3) and P_0 of the three components.
     // Ct: the two stiffness tables (shared memory on the device).
     static PC_HD void flux_node(const StencilParams<R>& P, const R (*Ct)[36], const SplitGeom& G, int p12, int p13,
-                                const C* xe, const void* mat, C* fe, int64_t t, bool uniform_ortho_ok) {
+                                const C* x, const C* xg, const void* mat, C* fe, int64_t t, bool uniform_ortho_ok) {
         int a, b, k;
         split3(t, G.X, G.Y, a, b, k);
         const int64_t own = eidx(G, a, b, k);
@@ -176,22 +181,38 @@ struct SplitApply {
         // H_s = sum_l c_{s l} g_l with g_l = n_l - x(node): the own value cancels from H_1 and H_2
         // (their sign rows sum to zero) and enters H_0 as -4 x(node), so the four differences are
         // never formed (16 instead of 22 FP64 operations per component).
+        // neighbour l: inside the grid from x, else from the ghost cells (array base and stride
+        // per neighbour, the same for the three components)
+        const C* nbase[4];
+        int64_t nstr[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int s2 = (l < 2) ? 1 : -1, s3 = (l & 1) ? -1 : 1;
+            const int db = FULL ? -s2 : j0 - ((s2 + 1) >> 1);
+            const int na = a + da, nb = b + db, nk = k - s3;
+            const bool in = (unsigned)na < (unsigned)G.X && (unsigned)nb < (unsigned)G.Y && (unsigned)nk < (unsigned)G.Z;
+            if (in) {
+                const int64_t i = na + (int64_t)G.X * (nb + (int64_t)G.Y * nk);
+                PC_IDX(i, G.m);
+                nbase[l] = x + i;
+                nstr[l] = G.m;
+            } else {
+                const int64_t i = ghost_index(G, na, nb, nk);
+                PC_IDX(i, G.ghosts);
+                nbase[l] = xg + i;
+                nstr[l] = G.ghosts;
+            }
+        }
         C H[3][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const C* xc = xe + c * G.ne;
             C n[4];
 #pragma unroll
-            for (int l = 0; l < 4; ++l) {
-                const int s2 = (l < 2) ? 1 : -1, s3 = (l & 1) ? -1 : 1;
-                const int db = FULL ? -s2 : j0 - ((s2 + 1) >> 1);
-                const int64_t nb = eidx(G, a + da, b + db, k - s3);
-                PC_IDX(nb, G.ne);
-                n[l] = xc[nb];
-            }
+            for (int l = 0; l < 4; ++l) n[l] = nbase[l][c * nstr[l]];
             const C u = cadd(n[0], n[1]), v = cadd(n[2], n[3]);
             const C w = csub(n[0], n[1]), z = csub(n[2], n[3]);
-            H[0][c] = cfma((R)(-4), xc[own], cadd(u, v));
+            PC_IDX(c * G.m + t, 3 * G.m);
+            H[0][c] = cfma((R)(-4), x[c * G.m + t], cadd(u, v));
             H[1][c] = csub(u, v);
             H[2][c] = cadd(w, z);
         }

@@ -59,8 +59,8 @@ FLOPS_PER_NODE = 294
 # (dram__bytes_read.sum + dram__bytes_write.sum, cold cache: ncu --metrics
 # dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
 # --profile-from-start off -k regex:split_ -c 8 python bench.py --profile kpoint).
-SPLIT_F64_DRAM_BYTES_PER_NODE = (85041664 + 54938368 + 167506688 + 397915904 + 155097856 + 45949440 +
-                                 549504512 + 71575552) / (64 * 27648)
+SPLIT_F64_DRAM_BYTES_PER_NODE = (36050432 + 900096 + 164037632 + 397710592 + 155104256 + 46386688 +
+                                 549513216 + 71348992) / (64 * 27648)
 
 
 def peaks():

@@ -297,11 +297,12 @@ __global__ void to_c64_scaled(const double2* __restrict__ in, float2* __restrict
     }
 }
 
-// x64_s += d32_s * scale_s
+// x64_s += d32_s * scale_s (systems of scale 0 are left as they are)
 __global__ void axpy_c64_into_c128(const float2* __restrict__ d, double2* __restrict__ x, const double* __restrict__ scale,
                                    int64_t vs) {
     const int s = blockIdx.y;
     const double f = scale[s];
+    if (f == 0.0) return;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
         const float2 v = d[s * vs + e];
         double2 o = x[s * vs + e];
@@ -312,10 +313,14 @@ __global__ void axpy_c64_into_c128(const float2* __restrict__ d, double2* __rest
 }
 
 // res = b - res
-__global__ void sub_from(const double2* __restrict__ b, double2* __restrict__ res, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double2 bv = b[i], rv = res[i];
-        res[i] = make_double2(bv.x - rv.x, bv.y - rv.y);
+// res_s = b_s - res_s for the systems of nonzero scale_s (the others keep their residual)
+__global__ void sub_from(const double2* __restrict__ b, double2* __restrict__ res, const double* __restrict__ scale,
+                         int64_t vs) {
+    const int s = blockIdx.y;
+    if (scale[s] == 0.0) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < vs; e += (int64_t)gridDim.x * blockDim.x) {
+        const double2 bv = b[s * vs + e], rv = res[s * vs + e];
+        res[s * vs + e] = make_double2(bv.x - rv.x, bv.y - rv.y);
     }
 }
 
@@ -504,6 +509,10 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, const std
         return PC_OK;
     }
     // mixed precision: x = 0, res = rhs; repeat { d = PCG32(res/|res|); x += |res| d; res = rhs - (A - sigma M) x }
+    // over the systems whose FP64 residual is still above inner_tol |rhs|.  A complex64 round
+    // reduces its system's residual by about its own PCG tolerance, so each round asks for a
+    // quarter of the reduction the worst remaining system still needs, within [tol32, 0.1]: the
+    // last round of a solve then stops after a few iterations instead of running to tol32.
     const int nc = ctas_for(vs);
     const dim3 vg(nc, nsys);
     PC_CUDA_TRY(cudaMemsetAsync(E.W, 0, sizeof(double2) * nsys * vs, E.s));
@@ -511,54 +520,60 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, const std
     std::vector<double> bnorm(nsys), rnorm(nsys), part((size_t)nsys * nc);
     const double tol32 = 1e-4;
     std::vector<ApplyItem> items;
-    for (int i = 0; i < nsys; ++i) {
-        if (!live[i]) continue;
-        ApplyItem it;
-        it.x = E.W + i * vs;
-        it.y = E.MW + i * vs;
-        it.mat = grid_mat(g, blocks[i]);
-        it.shift = E.sigma;
-        it.block = blocks[i];
-        it.dot_slot = -1;
-        it.skip = nullptr;
-        it.kslot = kslots[i];
-        items.push_back(it);
-    }
     for (int sweep = 0; sweep < 40; ++sweep) {
         sq_norms<double2><<<vg, 256, 0, E.s>>>(E.MW, vs, E.dpart, nc);
         note_launch();
         PC_CUDA_TRY(cudaMemcpyAsync(part.data(), E.dpart, sizeof(double) * nsys * nc, cudaMemcpyDeviceToHost, E.s));
         PC_CUDA_TRY(cudaStreamSynchronize(E.s));
         ++E.syncs;
-        bool all = true;
-        std::vector<double> sc(nsys);
+        std::vector<double> sc(nsys, 0.0);
+        std::vector<char> act(nsys, 0);
+        double worst = 0.0;  // largest |res| / |rhs| of the systems still running
         for (int i = 0; i < nsys; ++i) {
             double a = 0;
             for (int c = 0; c < nc; ++c) a += part[(size_t)i * nc + c];
             rnorm[i] = std::sqrt(a);
             if (sweep == 0) bnorm[i] = rnorm[i];
-            if (rnorm[i] > o.inner_tol * bnorm[i]) all = false;
-            sc[i] = rnorm[i] > 0 ? 1.0 / rnorm[i] : 0.0;
             if (!std::isfinite(rnorm[i])) return fail(PC_ENAN, "refinement met NaN");
+            act[i] = live[i] && rnorm[i] > o.inner_tol * bnorm[i];
+            if (act[i]) {
+                sc[i] = 1.0 / rnorm[i];
+                worst = std::max(worst, rnorm[i] / bnorm[i]);
+            }
         }
-        if (all) break;
+        if (worst == 0.0) break;
+        const double tol_round = std::min(0.1, std::max(tol32, 0.25 * o.inner_tol / worst));
         PC_CUDA_TRY(cudaMemcpyAsync(E.dscale, sc.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, E.s));
-        to_c64_scaled<<<vg, 256, 0, E.s>>>(E.MW, (float2*)E.R32, E.dscale, vs);
+        to_c64_scaled<<<vg, 256, 0, E.s>>>(E.MW, (float2*)E.R32, E.dscale, vs);  // zero for the others
         note_launch();
-        PC_TRY(pcg_solve(g, PC_C64, nsys, blocks.data(), E.sigma, E.R32, E.X32, tol32, o.inner_maxit, res.data(), E.s,
-                         false, ks));
+        PC_TRY(pcg_solve(g, PC_C64, nsys, blocks.data(), E.sigma, E.R32, E.X32, tol_round, o.inner_maxit, res.data(),
+                         E.s, false, ks));
         for (auto& r : res) {
             E.pcg_iters += r.iters;
             E.max_pcg = std::max(E.max_pcg, r.iters);
             if (r.status == PC_EBREAKDOWN) return fail(PC_EBREAKDOWN, "PCG breakdown: sigma is not below the spectrum");
         }
-        for (int i = 0; i < nsys; ++i) sc[i] = rnorm[i];
+        items.clear();
+        for (int i = 0; i < nsys; ++i) {
+            sc[i] = act[i] ? rnorm[i] : 0.0;
+            if (!act[i]) continue;
+            ApplyItem it;
+            it.x = E.W + i * vs;
+            it.y = E.MW + i * vs;
+            it.mat = grid_mat(g, blocks[i]);
+            it.shift = E.sigma;
+            it.block = blocks[i];
+            it.dot_slot = -1;
+            it.skip = nullptr;
+            it.kslot = kslots[i];
+            items.push_back(it);
+        }
         PC_CUDA_TRY(cudaMemcpyAsync(E.dscale, sc.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, E.s));
         axpy_c64_into_c128<<<vg, 256, 0, E.s>>>((const float2*)E.X32, E.W, E.dscale, vs);
         note_launch();
-        // residual in FP64: MW = RHS - (A - sigma M) W
+        // residual in FP64 of the systems of this round: MW = RHS - (A - sigma M) W
         PC_TRY(grid_apply(g, PC_C128, blocks[0] < 0, items.data(), (int)items.size(), nullptr, 0, E.s, nullptr));
-        sub_from<<<ctas_for(nsys * vs), 256, 0, E.s>>>(E.RHS, E.MW, nsys * vs);
+        sub_from<<<vg, 256, 0, E.s>>>(E.RHS, E.MW, E.dscale, vs);
         note_launch();
         PC_CUDA_TRY(cudaGetLastError());
     }

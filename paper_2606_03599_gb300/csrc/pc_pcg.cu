@@ -55,8 +55,10 @@ __global__ void pcg_start(const C* __restrict__ b, C* __restrict__ x, C* __restr
 }
 
 // bb = sum part_bb; init the scalars and flags: a zero right-hand side is solved by x = 0 and
-// its system is retired before the first preconditioner application.
-__global__ void pcg_start_bb(PcgScal* sc, int* done, const double* part_bb, int sbb, int nbb) {
+// its system is retired before the first preconditioner application.  The convergence
+// threshold tol2 bb is kept with the scalars, so that the captured iterations do not depend on
+// the tolerance.
+__global__ void pcg_start_bb(PcgScal* sc, int* done, const double* part_bb, int sbb, int nbb, double tol2) {
     const int s = blockIdx.x;
     double bb = reduce_partials(part_bb + (int64_t)s * sbb, nbb);
     if (threadIdx.x == 0) {
@@ -67,6 +69,7 @@ __global__ void pcg_start_bb(PcgScal* sc, int* done, const double* part_bb, int 
         v.beta = 0;
         v.rr = bb;
         v.bb = bb;
+        v.thr = tol2 * bb;
         v.iters = 0;
         v.pad = 0;
         v.status = PC_OK;
@@ -162,7 +165,7 @@ __global__ void pcg_update_xr(C* __restrict__ x, C* __restrict__ r, const C* __r
 // beta = rz_new / rz_old (Fletcher-Reeves form), or with part_d non-null the flexible
 // (Polak-Ribiere) form beta = (rz_new - Re<r_new, z_old>) / rz_old.
 __global__ void pcg_beta(PcgScal* sc, int* done, const double* part_rr, int srr, int nrr, const double* part_rz,
-                         int nrz, double tol2, int maxit, const double* part_d) {
+                         int nrz, int maxit, const double* part_d) {
     const int s = blockIdx.x;
     if (done[s]) return;
     double rr = reduce_partials(part_rr + (int64_t)s * srr, nrr);
@@ -175,7 +178,7 @@ __global__ void pcg_beta(PcgScal* sc, int* done, const double* part_rr, int srr,
         if (!isfinite(rr) || !isfinite(rz)) {
             v.status = PC_ENAN;
             v.done = 1;
-        } else if (rr <= tol2 * v.bb) {
+        } else if (rr <= v.thr) {
             v.status = PC_OK;
             v.done = 1;
         } else if (v.iters >= maxit) {
@@ -395,7 +398,7 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, const
 
     pcg_start<C><<<vgrid, 256, 0, s>>>(B, X, R, vs, part_a, npm);
     note_launch();
-    pcg_start_bb<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, vc);
+    pcg_start_bb<<<nsys, 256, 0, s>>>(w->sc, w->done, part_a, npm, vc, tol * tol);
     note_launch();
     PC_CUDA_TRY(cudaGetLastError());
     PC_TRY(precondition(full ? nullptr : w->done));
@@ -419,7 +422,6 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, const
     }
     const ApplyConfig cfg = apply_config_for(g, full, nsys, dtype);
     const int napc = cfg.ctas;
-    const double tol2 = tol * tol;
     const int chunk = 4;
     auto iterate = [&]() -> int {
         PC_TRY(grid_apply(g, dtype, full, items.data(), nsys, part_a, npm, s, &cfg));
@@ -430,7 +432,7 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, const
         note_launch();
         PC_CUDA_TRY(cudaGetLastError());
         PC_TRY(precondition(full ? nullptr : w->done));
-        pcg_beta<<<nsys, 256, 0, s>>>(w->sc, w->done, part_b, npm, vc, part_c, nrz, tol2, maxit, part_d);
+        pcg_beta<<<nsys, 256, 0, s>>>(w->sc, w->done, part_b, npm, vc, part_c, nrz, maxit, part_d);
         note_launch();
         pcg_update_p<C><<<vgrid, 256, 0, s>>>(P, Z, w->sc, w->done, vs);
         note_launch();
@@ -439,12 +441,12 @@ static int pcg_solve_t(pc_grid* g, int dtype, int nsys, const int* blocks, const
     };
     // Chunks after the first (which creates the preconditioner workspace and FFT plans) replay
     // a CUDA graph of `chunk` iterations, captured once per (Bloch vector, systems, buffers,
-    // shift, tolerance); block systems on a non-default stream only.
+    // shift); block systems on a non-default stream only.
     const bool graphs = !full && pcg_graphs_enabled() && s != nullptr && s != cudaStreamLegacy &&
                         s != cudaStreamPerThread;
     auto chunk_graph = [&]() -> int {
         std::vector<double> key = {(double)g->k.version, (double)g->kset_version, (double)dtype, (double)nsys, sigma,
-                                   tol2, (double)maxit,
+                                   (double)maxit,
                                    (double)(uintptr_t)B, (double)(uintptr_t)X, (double)(uintptr_t)g->pre->d_work,
                                    (double)(uintptr_t)w->R, (double)(timing_enabled() ? 1 : 0), (double)npm,
                                    (double)flex, (double)(uintptr_t)g->d_split};  // the two-pass apply's scratch

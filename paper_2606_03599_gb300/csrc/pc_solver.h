@@ -16,6 +16,7 @@ struct PcgScal {
     double beta;   // rz_new / rz
     double rr;     // ||r||^2
     double bb;     // ||b||^2
+    double thr;    // tol^2 ||b||^2: converged once ||r||^2 <= thr (set per solve, outside the graphs)
     int done;      // 1 once converged or failed
     int status;    // PC_OK, PC_ENOCONV, PC_EBREAKDOWN, PC_ENAN
     int iters;     // iterations taken

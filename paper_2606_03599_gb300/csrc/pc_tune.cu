@@ -145,7 +145,8 @@ static std::vector<ApplyConfig> candidates(int X, int Y, int Z, int dtype, bool 
     std::vector<ApplyConfig> out;
     const int sm = device_sm_count();
     // two-pass kernels: the default for complex128; for complex64 a candidate while the batch's
-    // fluxes and extended copies (18 complex64 per extended cell) fit in L2 (126 MB on GB300)
+    // scratch (15 complex64 flux arrays per extended cell plus x's ghost cells) fits in L2
+    // (126 MB on GB300)
     const double split_mb = (double)split_scratch_bytes(X, Y, Z, nitems, dtype) / (1 << 20);
     if (matkind == 2) {  // a nodewise material: the complex128 two-pass kernels only
         if (dtype == PC_C128) {

@@ -459,3 +459,32 @@ extern "C" int pc_emu_small_dft(int L, int inv, const double* in, double* out) {
         default: return -1;
     }
 }
+
+// The ghost-cell numbering of the two-pass kernels: ghost_cell(gi) lies on the one-cell layer
+// around the X x Y x Z interior, every such cell is hit exactly once, and ghost_index inverts it.
+// Returns the number of violations (0 = consistent).
+extern "C" long long pc_emu_ghost_cells(int X, int Y, int Z) {
+    using T = SplitApply<double, false, true, 0>;
+    const SplitGeom G = make_split_geom(X, Y, Z);
+    std::vector<int> hits((size_t)G.ne, 0);
+    long long bad = 0;
+    for (int64_t gi = 0; gi < G.ghosts; ++gi) {
+        int a, b, k;
+        T::ghost_cell(G, gi, a, b, k);
+        const bool inside = a >= 0 && a < X && b >= 0 && b < Y && k >= 0 && k < Z;
+        const bool layer = a >= -1 && a <= X && b >= -1 && b <= Y && k >= -1 && k <= Z;
+        if (inside || !layer) {
+            ++bad;
+            continue;
+        }
+        hits[(size_t)T::eidx(G, a, b, k)] += 1;
+        if (T::ghost_index(G, a, b, k) != gi) ++bad;
+    }
+    for (int k = -1; k <= Z; ++k)
+        for (int b = -1; b <= Y; ++b)
+            for (int a = -1; a <= X; ++a) {
+                const bool inside = a >= 0 && a < X && b >= 0 && b < Y && k >= 0 && k < Z;
+                if (!inside && hits[(size_t)T::eidx(G, a, b, k)] != 1) ++bad;
+            }
+    return bad;
+}

@@ -185,3 +185,14 @@ def test_small_dft_with_compile_time_roots_matches_numpy(emu, L):
                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == 0
         got = out[0::2] + 1j * out[1::2]
         assert np.abs(got - ref).max() <= 4e-16 * L * np.abs(v).sum()
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 4), (3, 4, 6), (24, 24, 48), (30, 30, 60), (5, 7, 3)])
+def test_ghost_cell_numbering_is_a_bijection_with_its_inverse(emu, dims):
+    """The two-pass kernels number the one-cell ghost layer around the grid (planes, then rows,
+    then columns); the flux pass finds a wrapped neighbour's cell by the inverse map.  Every layer
+    cell is numbered exactly once, no interior cell is, and the inverse returns the number."""
+    fn = emu.pc_emu_ghost_cells
+    fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    fn.restype = ctypes.c_longlong
+    assert fn(*dims) == 0

@@ -69,3 +69,14 @@ def test_null_grid_is_rejected(pc):
     assert pc.lib.pc_set_k(None, None) == pc.PC_EINVAL
     assert pc.lib.pc_block_apply(None, 0, pc.PC_C64, None, None, 0.0, None) == pc.PC_EINVAL
     assert pc.lib.pc_grid_destroy(None) == pc.PC_OK
+
+
+def test_stats_counters_need_no_device(pc):
+    """The launch and apply counters reset and read back on a host without a GPU (no apply has run,
+    so nothing was counted on a device): every counter is zero after a reset."""
+    pc.pc_stats_reset()
+    st = pc.pc_stats_get()
+    assert st["launches"] == 0 and st["apply_launches"] == 0
+    for k in ("apply_timed", "apply_ms", "apply_nodes", "apply_nodes_launched"):
+        assert st[k] == [0, 0], (k, st[k])
+    assert pc.lib.pc_stats_get(None) == pc.PC_EINVAL

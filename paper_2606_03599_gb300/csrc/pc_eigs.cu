@@ -509,10 +509,10 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, const std
         return PC_OK;
     }
     // mixed precision: x = 0, res = rhs; repeat { d = PCG32(res/|res|); x += |res| d; res = rhs - (A - sigma M) x }
-    // over the systems whose FP64 residual is still above inner_tol |rhs|.  A complex64 round
-    // reduces its system's residual by about its own PCG tolerance, so each round asks for a
+    // over the systems whose FP64 residual is still above inner_tol |rhs|.  A complex64 sweep
+    // reduces its system's residual by about its own PCG tolerance, so each sweep asks for a
     // quarter of the reduction the worst remaining system still needs, within [tol32, 0.1]: the
-    // last round of a solve then stops after a few iterations instead of running to tol32.
+    // last sweep of a solve then stops after a few iterations instead of running to tol32.
     const int nc = ctas_for(vs);
     const dim3 vg(nc, nsys);
     PC_CUDA_TRY(cudaMemsetAsync(E.W, 0, sizeof(double2) * nsys * vs, E.s));
@@ -542,11 +542,11 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, const std
             }
         }
         if (worst == 0.0) break;
-        const double tol_round = std::min(0.1, std::max(tol32, 0.25 * o.inner_tol / worst));
+        const double tol_sweep = std::min(0.1, std::max(tol32, 0.25 * o.inner_tol / worst));
         PC_CUDA_TRY(cudaMemcpyAsync(E.dscale, sc.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, E.s));
         to_c64_scaled<<<vg, 256, 0, E.s>>>(E.MW, (float2*)E.R32, E.dscale, vs);  // zero for the others
         note_launch();
-        PC_TRY(pcg_solve(g, PC_C64, nsys, blocks.data(), E.sigma, E.R32, E.X32, tol_round, o.inner_maxit, res.data(),
+        PC_TRY(pcg_solve(g, PC_C64, nsys, blocks.data(), E.sigma, E.R32, E.X32, tol_sweep, o.inner_maxit, res.data(),
                          E.s, false, ks));
         for (auto& r : res) {
             E.pcg_iters += r.iters;
@@ -571,7 +571,7 @@ static int apply_op(Eigs& E, int nsys, const std::vector<int>& blocks, const std
         PC_CUDA_TRY(cudaMemcpyAsync(E.dscale, sc.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, E.s));
         axpy_c64_into_c128<<<vg, 256, 0, E.s>>>((const float2*)E.X32, E.W, E.dscale, vs);
         note_launch();
-        // residual in FP64 of the systems of this round: MW = RHS - (A - sigma M) W
+        // residual in FP64 of the systems of this sweep: MW = RHS - (A - sigma M) W
         PC_TRY(grid_apply(g, PC_C128, blocks[0] < 0, items.data(), (int)items.size(), nullptr, 0, E.s, nullptr));
         sub_from<<<vg, 256, 0, E.s>>>(E.RHS, E.MW, E.dscale, vs);
         note_launch();
